@@ -1,0 +1,432 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle is pinned to things other than itself: published test vectors,
+closed forms of the paper's distributions and tables, the brute-force
+definition of the signature (Eq. def_new_exp + Eq. signature_def), the paper's
+own equivalence claims (ProbMinHash1 = 1a, 3 = 3a), invariants (element order,
+weight scale), the exponential-race marginals, the estimator's variance
+(Eq. jaccard_variance and the MSE variance in Sec. Verification) and the
+SuperMinHash improvement factor (Eq. improvement_factor).
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_1911_00675_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+VARS = ["1", "1a", "2", "3", "3a", "4"]
+
+
+def _mix_py(z):
+    m = (1 << 64) - 1
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31)
+
+
+# ---------------------------------------------------------------- stream --
+def test_splitmix64_reference_values():
+    with open(os.path.join(GOLDEN, "splitmix64.txt")) as f:
+        rows = [ln.split(";") for ln in f if ln.strip() and not ln.startswith("#")]
+    for j, hx in rows:
+        assert oracle.word(0, int(j)) == int(hx, 16)
+
+
+def test_uniform_range_and_resolution():
+    assert oracle.unif(0) == 0.0
+    assert oracle.unif((1 << 64) - 1) == 1.0 - 2.0**-53
+    assert oracle.unif(1 << 11) == 2.0**-53
+    assert oracle.exp1(0) == 0.0
+    assert math.isfinite(oracle.exp1((1 << 64) - 1))
+
+
+def _words(n, seed=1):
+    k = oracle.key(12345, seed)
+    return [oracle.word(k, j) for j in range(n)]
+
+
+def test_exp1_distribution():
+    e = np.array([oracle.exp1(w) for w in _words(20000)])
+    assert stats.kstest(e, "expon").pvalue > 1e-4
+    assert abs(e.mean() - 1.0) < 0.05
+
+
+@pytest.mark.parametrize("m", [2, 3, 64, 1024])
+def test_truncated_exp_distribution(m):
+    lam = math.log1p(1.0 / (m - 1))
+    c, inv = math.expm1(-lam), 1.0 / lam
+    x = np.array([oracle.texp(w, c, inv) for w in _words(20000, seed=m)])
+    assert x.min() >= 0.0 and x.max() < 1.0
+    cdf = lambda t: (1.0 - np.exp(-lam * t)) / (1.0 - math.exp(-lam))   # Exp(lambda;0,1)
+    assert stats.kstest(x, cdf).pvalue > 1e-4
+
+
+def test_uniform_int_range_and_balance():
+    for r in (1, 2, 3, 7, 1000, 4096):
+        ks = np.array([oracle.uint(w, r) for w in _words(6000, seed=r)])
+        assert ks.min() >= 0 and ks.max() < r
+        if 1 < r <= 8:
+            cnt = np.bincount(ks, minlength=r)
+            assert stats.chisquare(cnt).pvalue > 1e-4
+    assert oracle.uint((1 << 64) - 1, 4096) == 4095
+    assert oracle.uint(0, 4096) == 0
+
+
+def test_key_depends_on_id_and_seed():
+    assert oracle.key(1, 0) != oracle.key(2, 0)
+    assert oracle.key(1, 0) != oracle.key(1, 1)
+    assert oracle.key(5, 9) == _mix_py(5 ^ _mix_py(9))
+
+
+# ---------------------------------------------------------------- tables --
+@pytest.mark.parametrize("m", [2, 3, 5, 256, 4096])
+def test_tables_closed_forms(m):
+    beta, gamma, dgamma, lam, (lam3, c3, inv3, delta) = oracle.tables(m)
+    assert gamma[0] == 0.0 and gamma[1] == 1.0                 # gamma_1 = lambda_1/lambda_1
+    assert lam3 == pytest.approx(math.log(m / (m - 1)), rel=1e-14)
+    assert delta == pytest.approx(1.0 / lam3, rel=1e-15)
+    for i in range(1, m + 1):
+        assert beta[i] == pytest.approx(m / (m - i + 1), rel=1e-15)
+    for i in range(1, m):
+        # boundaries of the correlated generation: gamma_i = log(m/(m-i))/lambda_1
+        assert gamma[i] == pytest.approx(math.log(m / (m - i)) / lam3, rel=1e-12)
+        # every interval [gamma_{i-1}, gamma_i) carries probability 1/m under Exp(lambda_1)
+        p = math.exp(-lam3 * gamma[i - 1]) - math.exp(-lam3 * gamma[i])
+        assert p == pytest.approx(1.0 / m, rel=1e-9)
+        # rate of the i-th truncated exponential: lambda_1 * (gamma_i - gamma_{i-1}) = lambda_i
+        assert lam3 * dgamma[i] == pytest.approx(lam[i], rel=1e-9)
+
+
+@pytest.mark.parametrize("m", [2, 16, 1024])
+def test_pmh3_intervals_match_first_occurrence_law(m):
+    # With replacement the i-th label is the first k with probability (1/m)(1-1/m)^(i-1)
+    # (Eq. correlated_probabilities, r -> inf); the interval [i-1, i) carries exactly that
+    # mass under Exp(lambda) with lambda = log(1 + 1/(m-1)).
+    lam = oracle.tables(m)[4][0]
+    for i in (1, 2, 5, 50):
+        p_int = math.exp(-lam * (i - 1)) - math.exp(-lam * i)
+        assert p_int == pytest.approx((1 / m) * (1 - 1 / m) ** (i - 1), rel=1e-9)
+
+
+# ------------------------------------------------------------ track_max --
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 7, 8, 16, 33, 100])
+def test_track_max_matches_linear_max(m):
+    rng = np.random.default_rng(m)
+    cnt = 40 * m
+    leaves = rng.integers(0, m, size=cnt)
+    vals = rng.exponential(1.0, size=cnt)
+    roots = oracle.track_max_run(m, vals, leaves)
+    q = np.full(m, np.inf)
+    for t in range(cnt):
+        q[leaves[t]] = min(q[leaves[t]], vals[t])
+        assert roots[t] == q.max()
+
+
+def test_ties_keep_smallest_id_in_any_order():
+    # Reading of the tie rule: lexicographic (value, id) minimum per component.
+    vals = [2.0, 1.0, 1.0, 1.0, 3.0]
+    ids = [50, 40, 30, 35, 10]
+    for perm in ([0, 1, 2, 3, 4], [4, 3, 2, 1, 0], [2, 0, 4, 1, 3]):
+        q, z = oracle.offer_run(1, [vals[i] for i in perm], [ids[i] for i in perm], [0] * 5)
+        assert q[0] == 1.0 and z[0] == 30
+
+
+# ---------------------------------------------------------- permutation --
+@pytest.mark.parametrize("m", [1, 2, 5, 64, 300])
+def test_lazy_permutation_is_fisher_yates(m):
+    for e in range(20):
+        k = oracle.key(e, 77)
+        lab = oracle.perm_labels(m, k, m)
+        assert sorted(lab.tolist()) == list(range(m))
+        # eager Fisher-Yates with the same draws
+        p = list(range(m))
+        ref = []
+        for t in range(m):
+            r = t + oracle.uint(oracle.word(k, 2 * t + 1), m - t)
+            ref.append(p[r])
+            p[r], p[t] = p[t], p[r]
+        assert lab.tolist() == ref
+
+
+def test_lazy_permutation_first_label_uniform():
+    m = 6
+    first = [int(oracle.perm_labels(m, oracle.key(e, 3), 1)[0]) for e in range(6000)]
+    assert stats.chisquare(np.bincount(first, minlength=m)).pvalue > 1e-4
+
+
+# ---------------------------------------------- definition & invariants --
+def _rand_set(rng, n, weight="uniform"):
+    ids = W.distinct_ids(int(rng.integers(0, 2**40)), n, int(rng.integers(0, 2**32)))
+    if weight == "uniform":
+        w = 1.0 - rng.random(n)
+    elif weight == "pareto":
+        w = (1.0 - rng.random(n)) ** (-1 / 1.5)
+    elif weight == "lognormal":
+        w = rng.lognormal(0, 2, n)
+    else:
+        w = np.ones(n)
+    return ids, w
+
+
+@pytest.mark.parametrize("variant", VARS)
+def test_early_stop_equals_brute_force(variant):
+    rng = np.random.default_rng(100 + VARS.index(variant))
+    for trial in range(40):
+        n = int(rng.integers(1, 80))
+        m = int(rng.integers(2, 70))
+        ids, w = _rand_set(rng, n, ["uniform", "pareto", "lognormal", "unit"][trial % 4])
+        q, z, _ = oracle.sketch(variant, ids, w, m, seed=trial)
+        qb, zb, _ = oracle.sketch(variant, ids, w, m, seed=trial, brute=True)
+        assert np.array_equal(z, zb) and np.array_equal(q, qb)
+
+
+@pytest.mark.parametrize("pair", [("1", "1a"), ("3", "3a")])
+def test_interleaved_equals_sequential(pair):
+    rng = np.random.default_rng(7)
+    for trial in range(30):
+        n = int(rng.integers(1, 3000))
+        m = int(rng.choice([2, 16, 128, 256]))
+        ids, w = _rand_set(rng, n, ["uniform", "pareto", "lognormal"][trial % 3])
+        qa, za, _ = oracle.sketch(pair[0], ids, w, m, seed=trial)
+        qb, zb, _ = oracle.sketch(pair[1], ids, w, m, seed=trial)
+        assert np.array_equal(za, zb) and np.array_equal(qa, qb)
+
+
+@pytest.mark.parametrize("variant", VARS)
+def test_order_independence(variant):
+    rng = np.random.default_rng(11)
+    for trial in range(10):
+        n = int(rng.integers(1, 500))
+        ids, w = _rand_set(rng, n)
+        q, z, _ = oracle.sketch(variant, ids, w, 64, seed=3)
+        perm = rng.permutation(n)
+        q2, z2, _ = oracle.sketch(variant, ids[perm], w[perm], 64, seed=3)
+        assert np.array_equal(z, z2) and np.array_equal(q, q2)
+
+
+@pytest.mark.parametrize("variant", VARS)
+def test_scale_invariance(variant):
+    rng = np.random.default_rng(12)
+    for trial in range(8):
+        ids, w = _rand_set(rng, int(rng.integers(1, 400)), "lognormal")
+        q, z, _ = oracle.sketch(variant, ids, w, 64, seed=5)
+        q2, z2, _ = oracle.sketch(variant, ids, w * 8.0, 64, seed=5)      # exact power-of-two scaling
+        assert np.array_equal(z, z2) and np.array_equal(q2, q / 8.0)
+        q3, z3, _ = oracle.sketch(variant, ids, w * 3.7, 64, seed=5)      # general factor
+        assert np.array_equal(z, z3)
+
+
+@pytest.mark.parametrize("variant", VARS)
+def test_single_element(variant):
+    for m in (2, 17, 256):
+        q, z, st = oracle.sketch(variant, np.array([42], dtype=np.uint64), np.array([0.3]), m, seed=1)
+        assert (z == 42).all() and np.isfinite(q).all()
+        if variant == "2":
+            assert st["points"] == m          # exactly m points when n = 1
+        if variant == "4":
+            assert st["points"] <= m
+
+
+def test_zero_weights_skipped_and_empty_sets():
+    ids = np.array([1, 2, 3], dtype=np.uint64)
+    for v in VARS:
+        q, z, _ = oracle.sketch(v, ids, np.array([0.0, 1.0, 0.0]), 8, seed=0)
+        assert (z == 2).all()
+        q, z, _ = oracle.sketch(v, ids, np.zeros(3), 8, seed=0)
+        assert (z == 0).all() and np.isinf(q).all()
+        q, z, _ = oracle.sketch(v, ids[:0], np.zeros(0), 8, seed=0)
+        assert (z == 0).all() and np.isinf(q).all()
+
+
+def test_error_codes():
+    ids = np.array([1, 2], dtype=np.uint64)
+    for bad in (-1.0, np.nan, np.inf, 1e-320):
+        assert oracle.sketch_status("1", ids, np.array([1.0, bad]), 8) == oracle.ERR_BAD_WEIGHT
+    for v in ("3", "3a", "4"):
+        assert oracle.sketch_status(v, ids, np.array([1.0, 2.0]), 1) == oracle.ERR_INVALID_ARG
+    for v in ("1", "1a", "2"):
+        assert oracle.sketch_status(v, ids, np.array([1.0, 2.0]), 1) == oracle.OK
+
+
+# ------------------------------------------------------------- marginals --
+@pytest.mark.parametrize("variant", VARS)
+def test_marginals_exponential_race(variant):
+    # P(z_k = d) = w(d) / sum(w): the exponential race behind Eq. def_hash_jp.
+    ids = np.array([11, 22, 33, 44], dtype=np.uint64)
+    w = np.array([1.0, 2.0, 3.0, 4.0])
+    m = 32
+    counts = np.zeros(4)
+    for seed in range(400):
+        _, z, _ = oracle.sketch(variant, ids, w, m, seed=seed)
+        for j, d in enumerate(ids):
+            counts[j] += np.count_nonzero(z == d)
+    expected = w / w.sum() * counts.sum()
+    # components within one signature are dependent for 3/3a/4; use a wide acceptance
+    assert stats.chisquare(counts, expected).pvalue > 1e-6
+
+
+@pytest.mark.parametrize("variant", VARS)
+def test_hash_values_are_exponential(variant):
+    # h_k(d) ~ Exp(lambda * w(d)) with lambda = 1/m (ProbMinHash1/2) or log(1+1/(m-1)) (3/4).
+    m, w = 16, 2.5
+    lam = 1.0 / m if variant in ("1", "1a", "2") else math.log1p(1.0 / (m - 1))
+    vals = []
+    for seed in range(3000):
+        q, _, _ = oracle.sketch(variant, np.array([9], dtype=np.uint64), np.array([w]), m, seed=seed)
+        vals.append(q[seed % m] * lam * w)
+    assert stats.kstest(vals, "expon").pvalue > 1e-4
+
+
+# ----------------------------------------------------------------- J_P --
+def _golden_jp():
+    rows = []
+    with open(os.path.join(GOLDEN, "jp_examples.txt")) as f:
+        for ln in f:
+            if not ln.strip() or ln.startswith("#"):
+                continue
+            pairs, frac = ln.split(";")
+            ws = [tuple(float(x) for x in p.split(",")) for p in pairs.split()]
+            rows.append((ws, Fraction(frac.strip())))
+    return rows
+
+
+def test_jp_golden_examples():
+    rng = np.random.default_rng(0)
+    for ws, frac in _golden_jp():
+        a, wa, b, wb = W.pair_from_weight_pairs(rng, ws)
+        assert oracle.jp(a, wa, b, wb) == pytest.approx(float(frac), rel=1e-14)
+        assert oracle.jp(b, wb, a, wa) == pytest.approx(float(frac), rel=1e-14)
+
+
+def test_jp_properties():
+    rng = np.random.default_rng(1)
+    for t in range(20):
+        a, wa, b, wb, p = W.constructed_pair(rng, t / 19.0, n_total=int(rng.integers(10, 300)))
+        closed = p["w_s"] / (p["w_s"] + p["a"] + p["b"] / p["c"]) if p["w_s"] > 0 else 0.0
+        assert oracle.jp(a, wa, b, wb) == pytest.approx(closed, rel=1e-12, abs=1e-15)
+        assert oracle.jp(a, wa * 3.0, b, wb) == pytest.approx(closed, rel=1e-12, abs=1e-15)
+    ids, w = _rand_set(rng, 50, "lognormal")
+    assert oracle.jp(ids, w, ids, w) == pytest.approx(1.0, rel=1e-14)
+    ids2, w2 = _rand_set(rng, 30)
+    assert oracle.jp(ids, w, ids2, w2) == 0.0
+    # binary weights: J_P equals the Jaccard similarity
+    u = W.distinct_ids(0, 40, 9)
+    a, b = u[:25], u[10:]
+    assert oracle.jp(a, np.ones(25), b, np.ones(30)) == pytest.approx(15 / 40, rel=1e-14)
+
+
+# ---------------------------------------------------- estimator & error --
+def _mse_zscore(est, jp, m):
+    c = len(est)
+    mse = float(np.mean((np.asarray(est) - jp) ** 2))
+    mean = jp * (1 - jp) / m
+    var = (jp**2 * (1 - jp) ** 2 / (m**2 * c)) * (2 - 6 / m) + jp * (1 - jp) / (m**3 * c)
+    return mse / mean, (mse - mean) / math.sqrt(var)
+
+
+@pytest.mark.parametrize("example", [[(3, 20), (30, 7)], [(0, 1), (1, 0), (1, 1)]])
+def test_relative_mse_on_paper_examples(example):
+    # Sec. Verification: relative MSE ~ 1 for the uncorrelated variants (independent
+    # components, Eq. jaccard_variance) and <= 1 for the correlated ones; z-score of the
+    # empirical MSE from the variance formula printed there.
+    m, c = 32, 1500
+    rng = np.random.default_rng(2)
+    pairs = [W.pair_from_weight_pairs(rng, example) for _ in range(c)]
+    jp = oracle.jp(*pairs[0])
+    for variant in ("1", "2", "3", "4"):
+        est = []
+        for t, (a, wa, b, wb) in enumerate(pairs):
+            _, za, _ = oracle.sketch(variant, a, wa, m, seed=t)
+            _, zb, _ = oracle.sketch(variant, b, wb, m, seed=t)
+            est.append(oracle.count_equal(za, zb) / m)
+        rel, z = _mse_zscore(est, jp, m)
+        if variant in ("1", "2"):
+            assert abs(z) < 4.5, (variant, rel, z)
+        else:
+            # correlated generation: the error is significantly reduced for n < m
+            assert rel < 0.9 and z < -3.0, (variant, rel, z)
+    # P-MinHash reference
+    est = []
+    for t, (a, wa, b, wb) in enumerate(pairs):
+        _, za = oracle.pminhash(a, wa, m, seed=t)
+        _, zb = oracle.pminhash(b, wb, m, seed=t)
+        est.append(oracle.count_equal(za, zb) / m)
+    assert abs(_mse_zscore(est, jp, m)[1]) < 4.5
+
+
+def _alpha(m, u):
+    """SuperMinHash improvement factor, Eq. improvement_factor (exact rational)."""
+    s = sum(Fraction(l) ** u * ((l + 1) ** u + (l - 1) ** u - 2 * l**u) for l in range(1, m))
+    return 1 - s / (Fraction(m - 1) ** (u - 1) * Fraction(m) ** u * (u - 1))
+
+
+def test_pmh4_unit_weights_matches_superminhash_variance():
+    # With binary weights ProbMinHash4 is logically SuperMinHash (Sec. Conventional Jaccard
+    # Similarity); its estimator variance is alpha(m,u) J(1-J)/m (Eq. superminhash_variance).
+    m, c = 16, 4000
+    u_ids = W.distinct_ids(0, 4, 5)
+    rng = np.random.default_rng(3)
+    a_idx, b_idx = [0, 1, 2], [1, 2, 3]     # J = 2/4, u = 4
+    jp = 0.5
+    alpha = float(_alpha(m, 4))
+    est = []
+    for t in range(c):
+        ids = W.distinct_ids(int(rng.integers(0, 2**40)), 4, t)
+        _, za, _ = oracle.sketch("4", ids[a_idx], np.ones(3), m, seed=t)
+        _, zb, _ = oracle.sketch("4", ids[b_idx], np.ones(3), m, seed=t)
+        est.append(oracle.count_equal(za, zb) / m)
+    mse = float(np.mean((np.array(est) - jp) ** 2))
+    predicted = alpha * jp * (1 - jp) / m
+    assert mse / predicted == pytest.approx(1.0, abs=0.12)
+    assert alpha < 0.8       # the improvement is real at u < m
+
+
+def test_count_equal_and_allpairs():
+    rng = np.random.default_rng(4)
+    sig = rng.integers(0, 5, size=(7, 64)).astype(np.uint64)
+    cnt = oracle.count_allpairs(sig)
+    ref = (sig[:, None, :] == sig[None, :, :]).sum(-1)
+    assert np.array_equal(cnt, ref)
+    assert oracle.count_equal(sig[0], sig[1]) == ref[0, 1]
+
+
+# -------------------------------------------------------- work counters --
+def test_work_counters_match_paper_analysis():
+    m = 128
+    hm = sum(1 / k for k in range(1, m + 1))
+    rng = np.random.default_rng(5)
+    for n in (1, 10, 1000):
+        pts, buf1 = [], []
+        for t in range(30):
+            ids, w = _rand_set(rng, n)
+            pts.append(oracle.sketch("1", ids, w, m, seed=t)[2]["points"])
+            buf1.append(oracle.sketch("1a", ids, w, m, seed=t)[2]["buffer_max"])
+        hn = sum(1 / k for k in range(1, n + 1))
+        # total points ~ m H_m H_n (Sec. ProbMinHash1) for n <~ m H_m; each element costs >= 1
+        assert np.mean(pts) == pytest.approx(max(m * hm * hn, n), rel=0.35)
+        # expected maximum buffer of 1a: sum_j min(1, m H_m / j) (Sec. Interleaved Element Processing)
+        eb = sum(min(1.0, m * hm / j) for j in range(1, n + 1))
+        assert np.mean(buf1) == pytest.approx(eb, rel=0.35)
+    # 3a, unit weights: buffer after pass 1 ~ min(n, m H_m) (plateau)
+    n = 5000
+    b3 = [oracle.sketch("3a", *_rand_set(rng, n, "unit"), m, seed=t)[2]["buffer_max"] for t in range(10)]
+    assert np.mean(b3) == pytest.approx(min(n, m * hm), rel=0.35)
+
+
+def test_near_tie_scan_consistency():
+    rng = np.random.default_rng(6)
+    for v in VARS:
+        ids, w = _rand_set(rng, 300, "pareto")
+        q, z, _ = oracle.sketch(v, ids, w, 64, seed=1)
+        flags, ru = oracle.near_ties(v, ids, w, 64, 1, q, z, 1e-12)
+        assert flags.sum() == 0
+        assert (ru >= q).all()
+        # a huge relative gap flags every component with a runner-up
+        flags, ru = oracle.near_ties(v, ids, w, 64, 1, q, z, 1e6)
+        assert flags.sum() == np.isfinite(ru).sum()
