@@ -1,0 +1,175 @@
+/*
+ * pmh.h -- C ABI of the GB300-native ProbMinHash library (libpmh.so).
+ *
+ * ProbMinHash (Ertl, arXiv 1911.00675) computes m-component signatures of
+ * weighted sets for the probability Jaccard similarity J_P (Sec.
+ * Incorporating Weights, Eq. def_hash_jp): component k holds the element
+ * minimising h_k(d), the first point of d's increasing random sequence whose
+ * label is k (Eq. def_new_exp, Eq. signature_def).  J_P is estimated from the
+ * fraction of equal components (Eq. jaccard_estimator).
+ *
+ * Conventions for every entry point:
+ *   - Pointers documented as "device" must point to memory of the handle's
+ *     device; "host" pointers to host memory.  The caller owns every input and
+ *     output buffer; the library owns only workspace inside the handle.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream).  Errors detected from the arguments
+ *     on the host are returned immediately and nothing is launched.  Errors in
+ *     the data (bad weights, iteration limits) are reported per set in
+ *     `set_status` once the stream reaches that point.
+ *   - A handle is not thread-safe: use one handle per host thread.
+ *   - The last error message of a handle is available from pmh_last_error.
+ */
+#ifndef PMH_H_
+#define PMH_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PMH_OK = 0,
+    PMH_ERR_INVALID_ARG = 1,   /* argument rejected on the host, or bad offsets (per set) */
+    PMH_ERR_BAD_WEIGHT = 2,    /* per set: a weight is < 0, NaN, +-inf, or 1/w is not finite */
+    PMH_ERR_ITER_LIMIT = 3,    /* per set: an iteration or resource cap was hit (Sec. Experiments) */
+    PMH_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    PMH_ERR_NO_MEMORY = 5,     /* workspace allocation failed */
+    PMH_ERR_UNSUPPORTED = 6    /* a size outside the supported limits */
+} pmh_status;
+
+/* The six algorithms of the paper.  1 and 1a (resp. 3 and 3a) are logically
+ * equivalent and produce identical signatures (Sec. Interleaved Element
+ * Processing); each is still computed as its own item. */
+typedef enum {
+    PMH_V1 = 0,   /* Algorithm ProbMinHash1: with replacement, uncorrelated */
+    PMH_V1A = 1,  /* Algorithm ProbMinHash1a: interleaved ProbMinHash1 */
+    PMH_V2 = 2,   /* Algorithm ProbMinHash2: without replacement, uncorrelated */
+    PMH_V3 = 3,   /* Algorithm ProbMinHash3: with replacement, correlated (m >= 2) */
+    PMH_V3A = 4,  /* Algorithm ProbMinHash3a: interleaved ProbMinHash3 (m >= 2) */
+    PMH_V4 = 5    /* Algorithm ProbMinHash4: without replacement, correlated (m >= 2) */
+} pmh_variant;
+
+typedef enum {
+    PMH_FP64 = 0,          /* every point value in FP64 */
+    PMH_FP32_RECHECK = 1   /* FP32 candidates with an error bound; FP64 recomputation of the
+                              candidates within the bound of each other.  Same output as PMH_FP64. */
+} pmh_precision;
+
+typedef struct pmh_handle_s *pmh_handle;
+
+/* Limits. */
+#define PMH_MAX_M 8192u                 /* signature size m <= 8192 */
+#define PMH_MAX_SET_ELEMENTS 0xFFFFFFFFll /* elements per set < 2^32 */
+
+/* Device counters written by pmh_sketch_batch when `counters` is non-NULL
+ * (device array of PMH_NUM_COUNTERS uint64, accumulated, never cleared). */
+enum {
+    PMH_CNT_ELEMENTS = 0,     /* elements with w > 0 visited (all rounds) */
+    PMH_CNT_POINTS32 = 1,     /* point values evaluated in FP32 */
+    PMH_CNT_POINTS64 = 2,     /* point values evaluated in FP64 */
+    PMH_CNT_CONTENDERS = 3,   /* FP32 near-margin contender records */
+    PMH_CNT_RESOLVED = 4,     /* exact FP64 re-evaluations of contenders */
+    PMH_CNT_ROUNDS = 5,       /* threshold rounds beyond the first */
+    PMH_CNT_DEEP = 6,         /* elements processed warp-cooperatively */
+    PMH_CNT_PREFILTERED = 7,  /* elements rejected without evaluating a logarithm */
+    PMH_NUM_COUNTERS = 8
+};
+
+/* Creates a handle bound to CUDA device `device` (the device is made current
+ * for every later call on this handle).  *out receives the handle.
+ * Returns PMH_ERR_CUDA if the device cannot be used. */
+pmh_status pmh_create(pmh_handle *out, int device);
+
+/* Releases the handle and its workspace (synchronises its device first).
+ * NULL is ignored. */
+void pmh_destroy(pmh_handle h);
+
+/* The last error message recorded on `h` ("" if none); valid until the next
+ * call on `h`.  With h == NULL: the message of the last failed pmh_create. */
+const char *pmh_last_error(pmh_handle h);
+
+/*
+ * pmh_sketch_batch -- signatures of a CSR batch of weighted sets, for one or
+ * several variants in one persistent launch.
+ *
+ * Defines: Algorithms ProbMinHash1/1a/2/3/3a/4 (Sec. ProbMinHash1 ...
+ * Interleaved Element Processing).  Random draws come from a counter-based
+ * SplitMix64 stream keyed by mix(id ^ mix(seed)): point i uses stream words
+ * 2i-2 (value) and 2i-1 (label).  Ties are broken by the lexicographic
+ * minimum of (value, id), and an element stops once a point exceeds q_max.
+ *
+ *   ids       device uint64[N]: element ids; set s owns ids[offsets[s] .. offsets[s+1]).
+ *             Ids must be distinct within a set (precondition, not checked).
+ *   weights   device float64[N]: weights; w = 0 (or -0) elements are skipped.
+ *   offsets   device int64[num_sets+1], offsets[0] = 0, non-decreasing; a set
+ *             whose offsets are decreasing gets PMH_ERR_INVALID_ARG in set_status.
+ *   num_sets  >= 0.
+ *   m         signature size, 1 <= m <= PMH_MAX_M (m >= 2 for V3/V3A/V4).
+ *   variants  host int32[num_variants] of pmh_variant values (repeats allowed);
+ *             item (v, s) is set s sketched with variants[v].
+ *   precision pmh_precision.
+ *   seed      stream seed; signatures are comparable only for equal (m, seed)
+ *             and variant family.
+ *   out_ids   device uint64[num_variants * num_sets * m], row (v*num_sets + s):
+ *             the winning element id of each component; 0 for empty sets.
+ *   out_q     device float64[same] or NULL: the component minima h (exact FP64);
+ *             +inf for empty sets.  With PMH_FP32_RECHECK this costs one exact
+ *             FP64 evaluation per component.
+ *   set_status device int32[num_variants * num_sets] or NULL: per-item pmh_status.
+ *   counters  device uint64[PMH_NUM_COUNTERS] or NULL: accumulated work counters.
+ *   stream    cudaStream_t.
+ * Workspace (the work queue) is allocated on the first call and grown when a
+ * larger batch arrives; repeated calls with the same arguments replay a cached
+ * CUDA graph.
+ * Returns PMH_OK once launched, or a host-side error.
+ */
+pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const double *weights, const int64_t *offsets,
+                            int64_t num_sets, uint32_t m, const int32_t *variants, int32_t num_variants,
+                            int32_t precision, uint64_t seed, uint64_t *out_ids, double *out_q,
+                            int32_t *set_status, uint64_t *counters, void *stream);
+
+/*
+ * pmh_estimate_allpairs -- numerators of the J_P estimator (Eq. jaccard_estimator)
+ * for every pair of signatures: counts[a*num_sigs + b] = #{k : sigs[a][k] == sigs[b][k]}.
+ *
+ *   sigs      device uint64[num_sigs * m], row-major (one signature per row).
+ *   num_sigs  >= 0;  m: 1 <= m <= 65535.
+ *   upper_only 0: the full matrix is written.  1: only entries with a <= b are
+ *             written (the rest of `counts` is left untouched).
+ *   counts    device uint16[num_sigs * num_sigs].
+ * Exact integer counts; J_P estimate = counts / m.
+ */
+pmh_status pmh_estimate_allpairs(pmh_handle h, const uint64_t *sigs, int64_t num_sigs, uint32_t m,
+                                 int32_t upper_only, uint16_t *counts, void *stream);
+
+/*
+ * pmh_estimate_pairs -- the same count for listed pairs (Eq. jaccard_estimator):
+ * counts[i] = #{k : sig_a[pairs_a[i]][k] == sig_b[pairs_b[i]][k]}.
+ *   sig_a, sig_b  device uint64[* x m] row-major signature tables (may alias).
+ *   pairs_a, pairs_b device int64[num_pairs] row indices (not checked).
+ *   counts    device uint32[num_pairs].
+ */
+pmh_status pmh_estimate_pairs(pmh_handle h, const uint64_t *sig_a, const uint64_t *sig_b, const int64_t *pairs_a,
+                              const int64_t *pairs_b, int64_t num_pairs, uint32_t m, uint32_t *counts,
+                              void *stream);
+
+/*
+ * pmh_merge -- signature of a union of disjoint sets from the signatures of
+ * its parts: per component the lexicographic minimum of (q, id) over `parts`
+ * partial signatures (Eq. signature_def; the minimum over a union is the
+ * minimum of the parts' minima, and q_max only decreases).
+ *   q, z      device float64 / uint64 [parts * m] (part-major).
+ *   out_q, out_z device [m].
+ * Bit-exact with sketching the union when the parts were sketched with the
+ * same (m, seed, variant family) and exact q (out_q).
+ */
+pmh_status pmh_merge(pmh_handle h, const double *q, const uint64_t *z, int64_t parts, uint32_t m, double *out_q,
+                     uint64_t *out_z, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMH_H_ */

@@ -1,0 +1,145 @@
+// Device-side building blocks of the ProbMinHash kernels: the counter-based
+// random stream, the canonical FP64 point values of the four algorithm
+// families and their FP32 approximations with error bounds.
+//
+// Families (Sec. Sequence Generation): F1 = ProbMinHash1/1a (with replacement,
+// uncorrelated), F2 = ProbMinHash2 (without replacement, uncorrelated),
+// F3 = ProbMinHash3/3a (with replacement, correlated), F4 = ProbMinHash4
+// (without replacement, correlated).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pmh {
+
+constexpr uint64_t kPhi = 0x9E3779B97F4A7C15ull;   // 2^64 / golden ratio (SplitMix64 increment)
+constexpr uint64_t kEmptyKey = ~0ull;
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+// Relative error bound of every FP32 point value against its canonical FP64
+// value: |x32 - x64| <= kEta * x32.  The sources (each in units u = 2^-24):
+// 1/w from a truncated mantissa and a correctly rounded reciprocal (3u),
+// Exp(1) via log1pf/logf (max 1 ulp each) with a correctly rounded U (5u),
+// Exp(lambda;0,1) via log1pf with |U*expm1(-lambda)| <= 1/2 (10u), the table
+// entries and their products (<= 4u), the FP32 prefix sums of the uncorrelated
+// families (warp scan of positive terms plus an error-free carry, <= 7u), the
+// final product (u) and the FP64 value's own rounding (< u).  The worst family
+// totals below 20u; kEta = 64u leaves a factor of three.
+constexpr float kEta = 0x1p-18f;
+
+__host__ __device__ inline int family_of(int variant) {
+    // PMH_V1 = 0, V1A = 1 -> F1; V2 = 2 -> F2; V3 = 3, V3A = 4 -> F3; V4 = 5 -> F4
+    return variant <= 1 ? 1 : (variant == 2 ? 2 : (variant <= 4 ? 3 : 4));
+}
+
+// Per-m constants of Sec. ProbMinHash2/3/4, computed on the host in FP64
+// (arrays indexed as in the paper, length m+1).
+struct Tables {
+    uint32_t m;
+    const double *beta;     // beta_i = m/(m-i+1)
+    const double *gamma;    // gamma_i = log1p(i/(m-i))/lambda_1, i < m
+    const double *dgamma;   // gamma_i - gamma_{i-1}
+    const double *c4;       // expm1(-lambda_i), lambda_i = log1p(1/(m-i))
+    const double *inv4;     // 1/lambda_i
+    const float *beta32, *gamma32, *dgamma32, *c4_32, *inv4_32;
+    double c3, inv3, delta; // ProbMinHash3: expm1(-lambda), 1/lambda; ProbMinHash4: delta = 1/lambda_1
+    float c3_32, inv3_32, delta32;
+    float te_lo;            // (1-e^{-lambda_1})/lambda_1 rounded down: Exp(lambda_1;0,1) >= U * te_lo
+};
+
+// ------------------------------------------------------------------ stream
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output j+1 of a generator
+// seeded with `key` is mix(key + (j+1)*phi).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t value_word(uint64_t key, uint64_t i) {   // word 2i-2
+    return mix64(key + (2 * i - 1) * kPhi);
+}
+__device__ __forceinline__ uint64_t label_word(uint64_t key, uint64_t i) {   // word 2i-1
+    return mix64(key + (2 * i) * kPhi);
+}
+// floor(w * r / 2^64)
+__device__ __forceinline__ uint32_t uniform_int(uint64_t w, uint32_t r) {
+    return (uint32_t)__umul64hi(w, (uint64_t)r);
+}
+
+// ----------------------------------------------------------- FP64 (canonical)
+// Fixed evaluation order t = b*c, s = a + t, x = w_inv*s with every operation
+// rounded on its own (the _rn intrinsics are never contracted into FMAs).
+__device__ __forceinline__ double unif53(uint64_t w) { return __dmul_rn((double)(w >> 11), 0x1p-53); }
+__device__ __forceinline__ double exp1_64(uint64_t w) { return -log1p(-unif53(w)); }
+__device__ __forceinline__ double texp_64(uint64_t w, double c, double inv) {
+    double a = __dmul_rn(unif53(w), c);
+    double l = log1p(a);
+    return __dmul_rn(-l, inv);
+}
+// F1 term: w_inv * E
+__device__ __forceinline__ double term1_64(uint64_t vw, double w_inv) { return __dmul_rn(w_inv, exp1_64(vw)); }
+// F2 term: w_inv * (beta_i * E)
+__device__ __forceinline__ double term2_64(const Tables &T, uint64_t vw, uint32_t i, double w_inv) {
+    return __dmul_rn(w_inv, __dmul_rn(T.beta[i], exp1_64(vw)));
+}
+// F3 point: w_inv * ((i-1) + TE_lambda)
+__device__ __forceinline__ double point3_64(const Tables &T, uint64_t vw, uint64_t i, double w_inv) {
+    double s = __dadd_rn((double)(i - 1), texp_64(vw, T.c3, T.inv3));
+    return __dmul_rn(w_inv, s);
+}
+// F4 point: w_inv * (gamma_{i-1} + dgamma_i * TE_{lambda_i}); i = m: w_inv * (gamma_{m-1} + delta * E)
+__device__ __forceinline__ double point4_64(const Tables &T, uint64_t vw, uint32_t i, double w_inv) {
+    double s;
+    if (i < T.m) {
+        double t = __dmul_rn(T.dgamma[i], texp_64(vw, T.c4[i], T.inv4[i]));
+        s = __dadd_rn(T.gamma[i - 1], t);
+    } else {
+        double t = __dmul_rn(T.delta, exp1_64(vw));
+        s = __dadd_rn(T.gamma[T.m - 1], t);
+    }
+    return __dmul_rn(w_inv, s);
+}
+__device__ __forceinline__ double lower3_64(uint64_t i, double w_inv) { return __dmul_rn(w_inv, (double)(i - 1)); }
+__device__ __forceinline__ double lower4_64(const Tables &T, uint32_t i, double w_inv) {
+    return __dmul_rn(w_inv, T.gamma[i - 1]);
+}
+
+// ------------------------------------------------------------ FP32 (filter)
+// Exp(1): for U < 1/2 log1pf(-U) keeps relative accuracy; otherwise V = 1-U is
+// formed exactly in integers before the conversion.
+__device__ __forceinline__ float exp1_32(uint64_t w) {
+    uint64_t k = w >> 11;
+    if (k < (1ull << 52)) {
+        float u = __fmul_rn(__ull2float_rn(k), 0x1p-53f);
+        return -log1pf(-u);
+    }
+    float v = __fmul_rn(__ull2float_rn((1ull << 53) - k), 0x1p-53f);
+    return -logf(v);
+}
+__device__ __forceinline__ float texp_32(uint64_t w, float c, float inv) {
+    float u = __fmul_rn(__ull2float_rn(w >> 11), 0x1p-53f);
+    float l = log1pf(__fmul_rn(u, c));
+    return __fmul_rn(-l, inv);
+}
+// A lower bound of U with 23-bit resolution (exact conversion of a 23-bit integer).
+__device__ __forceinline__ float unif_lo(uint64_t w) {
+    return __fmul_rn(__uint2float_rn((uint32_t)(w >> 41)), 0x1p-23f);
+}
+
+// 1/w scaled by 2^sigma as a float, from the double's bits (mantissa
+// truncated to 23 bits: relative error <= 2^-23, then a correctly rounded
+// reciprocal).  Weights too small for the float range give 2^100: every point
+// of such an element is then far beyond any bound (E >= 2^-53 unless E = 0,
+// and E = 0 gives x = 0 exactly in both precisions).
+__device__ __forceinline__ float winv_scaled(double w, int sigma) {
+    uint64_t b = (uint64_t)__double_as_longlong(w);
+    int e = (int)((b >> 52) & 0x7FF);
+    int ef = e - 1023 - sigma + 127;
+    if (e == 0 || ef <= 0) return 0x1p100f;
+    if (ef >= 254) ef = 254;
+    uint32_t fb = ((uint32_t)ef << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu);
+    return __frcp_rn(__uint_as_float(fb));
+}
+
+}  // namespace pmh

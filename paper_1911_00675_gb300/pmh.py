@@ -1,0 +1,214 @@
+"""Thin Python binding of libpmh.so (argument marshalling only).
+
+Every function has the name of the C entry point without the ``pmh_``
+prefix and passes raw device pointers of PyTorch tensors plus the current
+CUDA stream.  All arithmetic runs in the library's CUDA kernels; if the
+shared object is missing or does not load, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpmh.so")
+
+OK, ERR_INVALID_ARG, ERR_BAD_WEIGHT, ERR_ITER_LIMIT, ERR_CUDA, ERR_NO_MEMORY, ERR_UNSUPPORTED = range(7)
+V1, V1A, V2, V3, V3A, V4 = range(6)
+VARIANTS = {"1": V1, "1a": V1A, "2": V2, "3": V3, "3a": V3A, "4": V4}
+FP64, FP32_RECHECK = 0, 1
+COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "rounds", "deep", "prefiltered")
+EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_estimate_allpairs",
+           "pmh_estimate_pairs", "pmh_merge")
+
+_lib = None
+_lock = threading.Lock()
+
+
+class PmhError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pmh status {code}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    """Loads libpmh.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"libpmh.so not built ({path}); run paper_1911_00675_gb300/build.py")
+            lib = ctypes.CDLL(path)
+            vp, i32, i64, u32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+            lib.pmh_create.restype = i32
+            lib.pmh_create.argtypes = [ctypes.POINTER(vp), i32]
+            lib.pmh_destroy.restype = None
+            lib.pmh_destroy.argtypes = [vp]
+            lib.pmh_last_error.restype = ctypes.c_char_p
+            lib.pmh_last_error.argtypes = [vp]
+            lib.pmh_sketch_batch.restype = i32
+            lib.pmh_sketch_batch.argtypes = [vp, vp, vp, vp, i64, u32, ctypes.POINTER(i32), i32, i32, u64, vp, vp, vp,
+                                             vp, vp]
+            lib.pmh_estimate_allpairs.restype = i32
+            lib.pmh_estimate_allpairs.argtypes = [vp, vp, i64, u32, i32, vp, vp]
+            lib.pmh_estimate_pairs.restype = i32
+            lib.pmh_estimate_pairs.argtypes = [vp, vp, vp, vp, vp, i64, u32, vp, vp]
+            lib.pmh_merge.restype = i32
+            lib.pmh_merge.argtypes = [vp, vp, vp, i64, u32, vp, vp, vp]
+            _lib = lib
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(t, name, dtypes, device):
+    if t is None:
+        return
+    if not t.is_cuda or t.device != device:
+        raise ValueError(f"{name} must be a CUDA tensor on {device}")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name} has dtype {t.dtype}, expected one of {dtypes}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+_I64 = (torch.int64, getattr(torch, "uint64", torch.int64))
+
+
+class Handle:
+    """Owns a pmh_handle bound to one CUDA device."""
+
+    def __init__(self, device: int | None = None):
+        lib = load()
+        dev = torch.cuda.current_device() if device is None else int(device)
+        h = ctypes.c_void_p()
+        rc = lib.pmh_create(ctypes.byref(h), dev)
+        if rc:
+            raise PmhError(rc, lib.pmh_last_error(None).decode())
+        self._h = h
+        self.device = torch.device("cuda", dev)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pmh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _raise(self, rc):
+        if rc:
+            raise PmhError(rc, load().pmh_last_error(self._h).decode())
+
+    # -- pmh_sketch_batch ---------------------------------------------------
+    def sketch_batch(self, ids, weights, offsets, m: int, variants=("1",), precision: int = FP32_RECHECK,
+                     seed: int = 0, out_ids=None, out_q=None, status=None, counters=None, with_q: bool = False,
+                     with_status: bool = True, stream=None):
+        """Returns (out_ids [V, S, m] int64 view of the uint64 ids, out_q or None, status [V, S] or None)."""
+        dev = self.device
+        _check(ids, "ids", _I64, dev)
+        _check(weights, "weights", (torch.float64,), dev)
+        _check(offsets, "offsets", (torch.int64,), dev)
+        vs = [VARIANTS[v] if isinstance(v, str) else int(v) for v in variants]
+        s = offsets.numel() - 1
+        if out_ids is None:
+            out_ids = torch.empty((len(vs), s, m), dtype=torch.int64, device=dev)
+        if out_q is None and with_q:
+            out_q = torch.empty((len(vs), s, m), dtype=torch.float64, device=dev)
+        if status is None and with_status:
+            status = torch.empty((len(vs), s), dtype=torch.int32, device=dev)
+        _check(out_ids, "out_ids", _I64, dev)
+        _check(out_q, "out_q", (torch.float64,), dev)
+        _check(status, "status", (torch.int32,), dev)
+        _check(counters, "counters", _I64, dev)
+        arr = (ctypes.c_int32 * len(vs))(*vs)
+        rc = load().pmh_sketch_batch(self._h, _ptr(ids), _ptr(weights), _ptr(offsets), s, m, arr, len(vs),
+                                     int(precision), int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out_ids), _ptr(out_q),
+                                     _ptr(status), _ptr(counters), _stream(stream))
+        self._raise(rc)
+        return out_ids, out_q, status
+
+    # -- pmh_estimate_allpairs ---------------------------------------------
+    def estimate_allpairs(self, sigs, upper_only: bool = False, counts=None, stream=None):
+        _check(sigs, "sigs", _I64, self.device)
+        n, m = sigs.shape
+        if counts is None:
+            counts = torch.zeros((n, n), dtype=torch.int16, device=self.device)   # uint16 storage
+        _check(counts, "counts", (torch.int16, getattr(torch, "uint16", torch.int16)), self.device)
+        rc = load().pmh_estimate_allpairs(self._h, _ptr(sigs), n, m, 1 if upper_only else 0, _ptr(counts),
+                                          _stream(stream))
+        self._raise(rc)
+        return counts
+
+    # -- pmh_estimate_pairs ------------------------------------------------
+    def estimate_pairs(self, sig_a, sig_b, pairs_a, pairs_b, counts=None, stream=None):
+        _check(sig_a, "sig_a", _I64, self.device)
+        _check(sig_b, "sig_b", _I64, self.device)
+        _check(pairs_a, "pairs_a", (torch.int64,), self.device)
+        _check(pairs_b, "pairs_b", (torch.int64,), self.device)
+        m = sig_a.shape[1]
+        if counts is None:
+            counts = torch.empty(pairs_a.numel(), dtype=torch.int32, device=self.device)
+        rc = load().pmh_estimate_pairs(self._h, _ptr(sig_a), _ptr(sig_b), _ptr(pairs_a), _ptr(pairs_b),
+                                       pairs_a.numel(), m, _ptr(counts), _stream(stream))
+        self._raise(rc)
+        return counts
+
+    # -- pmh_merge ----------------------------------------------------------
+    def merge(self, q, z, out_q=None, out_z=None, stream=None):
+        _check(q, "q", (torch.float64,), self.device)
+        _check(z, "z", _I64, self.device)
+        parts, m = q.shape
+        if out_q is None:
+            out_q = torch.empty(m, dtype=torch.float64, device=self.device)
+        if out_z is None:
+            out_z = torch.empty(m, dtype=torch.int64, device=self.device)
+        rc = load().pmh_merge(self._h, _ptr(q), _ptr(z), parts, m, _ptr(out_q), _ptr(out_z), _stream(stream))
+        self._raise(rc)
+        return out_q, out_z
+
+
+_handles: dict[int, Handle] = {}
+
+
+def handle(device: int | None = None) -> Handle:
+    """The process-wide handle of a device (created on first use)."""
+    dev = torch.cuda.current_device() if device is None else int(device)
+    if dev not in _handles:
+        _handles[dev] = Handle(dev)
+    return _handles[dev]
+
+
+def sketch_batch(ids, weights, offsets, m, variants=("1",), precision=FP32_RECHECK, seed=0, **kw):
+    return handle(ids.device.index).sketch_batch(ids, weights, offsets, m, variants, precision, seed, **kw)
+
+
+def estimate_allpairs(sigs, upper_only=False, **kw):
+    return handle(sigs.device.index).estimate_allpairs(sigs, upper_only, **kw)
+
+
+def estimate_pairs(sig_a, sig_b, pairs_a, pairs_b, **kw):
+    return handle(sig_a.device.index).estimate_pairs(sig_a, sig_b, pairs_a, pairs_b, **kw)
+
+
+def merge(q, z, **kw):
+    return handle(q.device.index).merge(q, z, **kw)
+
+
+def to_u64(t) -> "numpy.ndarray":
+    """Host numpy uint64 copy of an int64-viewed id tensor."""
+    return t.detach().cpu().numpy().view("uint64")

@@ -1,0 +1,193 @@
+"""Parity of the CUDA sketch path (through the C ABI) with the CPU oracle.
+
+Rule (winning ids): bit-exact with the oracle, except components where the
+oracle's two best candidates differ by less than 1e-12 relative (near ties,
+counted; at most 1e-6 of all components).  CUDA's and the host's FP64 log1p
+may differ in the last ulp, which is what the exemption covers.
+
+Rule (q values): |q_gpu - q_oracle| <= 1e-10 * q_oracle.  A point value is a
+sum of at most i <= ~1e5 terms, each within 2 ulp (two log1p evaluations of at
+most 1 ulp error each) plus one rounding, so the two FP64 evaluations differ
+by at most ~4i * 2^-53 ~ 5e-11 relative.
+
+Rule (precisions): the FP32-candidate path and the FP64 path return identical
+ids and identical q.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1911_00675_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+VARS = ["1", "1a", "2", "3", "3a", "4"]
+NEAR_REL = 1e-12
+Q_RTOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_1911_00675_gb300 import build, pmh
+    build.build()
+    return pmh.Handle(0)
+
+
+def to_dev(batch):
+    dev = torch.device("cuda", 0)
+    ids = torch.from_numpy(batch.ids.view(np.int64).copy()).to(dev)
+    w = torch.from_numpy(np.ascontiguousarray(batch.weights)).to(dev)
+    off = torch.from_numpy(np.ascontiguousarray(batch.offsets)).to(dev)
+    return ids, w, off
+
+
+def run(H, batch, variants, precision, with_q=True, seed=0, counters=None):
+    from paper_1911_00675_gb300 import pmh
+    ids, w, off = to_dev(batch)
+    z, q, st = H.sketch_batch(ids, w, off, batch.m, variants, precision, seed, with_q=with_q, counters=counters)
+    torch.cuda.synchronize()
+    return (pmh.to_u64(z), q.cpu().numpy() if q is not None else None, st.cpu().numpy())
+
+
+def check_sets(batch, variant, z, q, sets, seed=0, stats=None):
+    """Compares GPU rows z[s], q[s] with the oracle for the listed sets."""
+    m = batch.m
+    for s in sets:
+        ids, w = batch.set(s)
+        qo, zo, _ = oracle.sketch(variant, ids, w, m, seed=seed)
+        diff = np.nonzero(z[s] != zo)[0]
+        if len(diff):
+            flags, _ = oracle.near_ties(variant, ids, w, m, seed, qo, zo, NEAR_REL)
+            assert flags[diff].all(), f"set {s} variant {variant}: {len(diff)} unflagged id mismatches, e.g. k={diff[:5]}"
+            if stats is not None:
+                stats["near"] += int(flags.sum())
+        if stats is not None:
+            stats["components"] += m
+        if q is not None:
+            fin = np.isfinite(qo)
+            assert np.array_equal(np.isfinite(q[s]), fin)
+            np.testing.assert_allclose(q[s][fin], qo[fin], rtol=Q_RTOL, atol=0)
+
+
+SIZES = [0, 1, 2, 3, 5, 31, 32, 33, 64, 100, 257, 1000, 3001]
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("m", [2, 7, 64, 300, 1024])
+def test_small_batches_all_variants(H, precision, m):
+    for weight in ("uniform", "pareto", "lognormal", "unit"):
+        b = W.random_batch(1000 + m, SIZES, m, weight)
+        z, q, st = run(H, b, VARS, precision, with_q=True, seed=3)
+        assert (st == 0).all(), st
+        for vi, v in enumerate(VARS):
+            check_sets(b, v, z[vi], q[vi], range(b.num_sets), seed=3)
+
+
+@pytest.mark.parametrize("m", [2, 33, 256, 4096])
+def test_fp32_equals_fp64_bit_exact(H, m):
+    b = W.random_batch(77 + m, [1, 4, 17, 200, 1500, 9000], m, "pareto")
+    z64, q64, _ = run(H, b, VARS, 0, with_q=True, seed=11)
+    z32, q32, _ = run(H, b, VARS, 1, with_q=True, seed=11)
+    assert np.array_equal(z64, z32)
+    assert np.array_equal(q64, q32)
+
+
+def test_m_one_and_single_element_sets(H):
+    b = W.random_batch(5, [1, 1, 2, 50], 1, "uniform")
+    for prec in (0, 1):
+        z, q, st = run(H, b, ["1", "1a", "2"], prec, seed=9)
+        assert (st == 0).all()
+        for vi, v in enumerate(["1", "1a", "2"]):
+            check_sets(b, v, z[vi], q[vi], range(b.num_sets), seed=9)
+    b = W.random_batch(6, [1, 1, 1], 4096, "lognormal")
+    for prec in (0, 1):
+        z, q, st = run(H, b, VARS, prec)
+        for vi in range(6):
+            for s in range(3):
+                assert (z[vi, s] == b.ids[s]).all()
+
+
+def test_zero_bad_and_empty_sets(H):
+    ids = W.distinct_ids(0, 9, 1)
+    w = np.array([0.0, 1.0, -0.0,          # set 0: one positive weight
+                  0.0, 0.0,                # set 1: all zero -> empty
+                  1.0, -1.0,               # set 2: negative -> bad weight
+                  np.nan,                  # set 3: NaN -> bad
+                  np.inf])                 # set 4: inf -> bad
+    off = np.array([0, 3, 5, 7, 8, 9, 9], dtype=np.int64)   # set 5 empty
+    b = W.Batch(ids, w, off, 16)
+    for prec in (0, 1):
+        z, q, st = run(H, b, ["1", "4"], prec)
+        assert st.tolist() == [[0, 0, 2, 2, 2, 0]] * 2
+        for vi in range(2):
+            assert (z[vi, 0] == ids[1]).all()
+            for s in (1, 2, 3, 4, 5):
+                assert (z[vi, s] == 0).all() and np.isinf(q[vi, s]).all()
+
+
+def test_decreasing_offsets_flagged(H):
+    ids = W.distinct_ids(0, 10, 2)
+    b = W.Batch(ids, np.ones(10), np.array([0, 6, 4, 10], dtype=np.int64), 8)
+    _, _, st = run(H, b, ["1"], 1)
+    assert st[0].tolist() == [0, 1, 0]
+
+
+def test_seed_changes_signature(H):
+    b = W.random_batch(8, [500], 64)
+    z0, _, _ = run(H, b, ["3a"], 1, seed=0)
+    z1, _, _ = run(H, b, ["3a"], 1, seed=1)
+    assert (z0 != z1).any()
+    check_sets(b, "3a", z1[0], None, [0], seed=1)
+
+
+def test_counters_and_repeat_calls(H):
+    from paper_1911_00675_gb300 import pmh
+    b = W.random_batch(12, [100, 2000, 5], 256, "uniform")
+    ids, w, off = to_dev(b)
+    cnt = torch.zeros(8, dtype=torch.int64, device="cuda")
+    outs = []
+    for _ in range(3):   # the second and third calls replay the cached graph
+        z, _, st = H.sketch_batch(ids, w, off, 256, VARS, 1, 0, counters=cnt)
+        torch.cuda.synchronize()
+        outs.append(pmh.to_u64(z).copy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+    c = dict(zip(pmh.COUNTERS, cnt.cpu().tolist()))
+    assert c["elements"] >= 3 * 6 * 2105      # every positive element is visited at least once per call
+    assert c["points32"] > 0
+
+
+# --------------------------------------------------------------- full sizes
+def test_c1_full(H):
+    b = W.batch_c1()
+    for prec in (0, 1):
+        z, q, st = run(H, b, ["1", "3"], prec, with_q=(prec == 0))
+        assert (st == 0).all()
+        for vi, v in enumerate(["1", "3"]):
+            check_sets(b, v, z[vi], q[vi] if q is not None else None, range(b.num_sets))
+
+
+def _sampled_parity(H, b, variants, n_sample, seed=0):
+    z64, _, st64 = run(H, b, variants, 0, with_q=False)
+    z32, _, st32 = run(H, b, variants, 1, with_q=False)
+    assert (st64 == 0).all() and (st32 == 0).all()
+    assert np.array_equal(z64, z32)              # identical output, every set, every variant
+    rng = np.random.default_rng(seed)
+    sizes = np.diff(b.offsets)
+    # sample small and large sets alike (stratified by log size)
+    order = np.argsort(sizes)
+    pick = np.unique(np.concatenate([order[np.linspace(0, len(order) - 1, n_sample).astype(int)],
+                                     rng.choice(len(order), n_sample // 2, replace=False)]))
+    stats = {"near": 0, "components": 0}
+    for vi, v in enumerate(variants):
+        check_sets(b, v, z32[vi], None, pick, stats=stats)
+    assert stats["near"] <= max(1e-6 * stats["components"], 0)
+
+
+@pytest.mark.slow
+def test_c2_full_sampled(H):
+    _sampled_parity(H, W.batch_c2(), VARS, 24)
+
+
+@pytest.mark.slow
+def test_c3_full_sampled(H):
+    _sampled_parity(H, W.batch_c3(), ["2", "4"], 10)
