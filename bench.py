@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark: set elements sketched per second (ProbMinHash, all six variants, m = 1024).
+
+Workload (default): 20,000 weighted sets, n log-uniform on [1, 1e5]
+(floor(10^(5U))), weights Uniform(0,1], distinct uniform-looking 64-bit ids,
+m = 1024, variants 1, 1a, 2, 3, 3a, 4 in one persistent launch.  One step =
+one pmh_sketch_batch call over the whole batch (every item is sketched; 1/1a
+and 3/3a are separate items).  The metric counts elements x variants per
+second.  The headline path is FP32 candidates + FP64 recheck; the plain FP64
+path is timed beside it and its ids are compared with the headline's.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pmh|reference]
+
+Under torchrun (N > 1) every rank sketches its own batch (seed + rank):
+weak scaling, no collective on the data path; rank 0 prints one JSON line.
+`--impl reference` times the CPU oracle (the plain FP64 C restatement of the
+paper) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "set elements sketched/sec at m=1024 on 1 GB300 (FP32+recheck vs plain FP64), % roofline"
+UNIT = "elements/s"
+VARIANTS = ["1", "1a", "2", "3", "3a", "4"]
+N_FAMILIES = 4   # ProbMinHash1/1a, 2, 3/3a, 4: one persistent kernel launch each
+
+# Algorithmic integer/FP32 operations per unit of work (counted from the
+# method's arithmetic): one SplitMix64 word is 2 64-bit
+# xor-shift-multiply rounds + 1 xor-shift + the counter add = 20 32-bit ops.
+OPS_KEY = 20            # element key: mix(id ^ mix(seed))
+OPS_FIRST_REJECT = 26   # value word (20) + log-free lower bound and compare (6)
+OPS_POINT = 60          # value word (20) + label word (20) + logarithm (~10) + scale/compare (5) + offer (5)
+LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes issue one instruction per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["pmh", "reference"], default="pmh")
+    ap.add_argument("--num-sets", type=int, default=20000, help="sets in the batch (20,000 = the benchmark config)")
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="wall budget of the CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ CPU oracle
+def _oracle_task(args):
+    """Worker: oracle signature of one (set, variant); returns the element count."""
+    variant, ids, w, m = args
+    import oracle
+    oracle.sketch(variant, ids, w, m, seed=0)
+    return len(ids)
+
+
+def _oracle_pool(cores):
+    """A spawn pool (never fork after CUDA is initialised), warmed up so that process start-up and
+    the oracle's import are not timed."""
+    import multiprocessing as mp
+
+    import numpy as np
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(cores)
+    pool.map(_oracle_task, [("1", np.array([1], dtype=np.uint64), np.ones(1), 8)] * cores)
+    return pool
+
+
+def oracle_throughput(batch, seconds, cores, rng_seed=1):
+    """Elements x variants per second of the oracle on a random sample of (set, variant) tasks,
+    run on `cores` processes for about `seconds` of wall time."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(rng_seed)
+    tasks = [(v, s) for s in rng.permutation(batch.num_sets) for v in VARIANTS]
+    pool = _oracle_pool(cores)
+    done_elems, done_tasks = 0, 0
+    t0 = time.perf_counter()
+    it = pool.imap_unordered(_oracle_task, ((v, *batch.set(s), batch.m) for v, s in tasks), chunksize=1)
+    try:
+        for n in it:
+            done_elems += n
+            done_tasks += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+    finally:
+        el = time.perf_counter() - t0
+        pool.terminate()
+    return done_elems / el, done_elems, done_tasks, el
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for ln in f:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = float(parts[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import numpy as np
+    from paper_1911_00675_gb300 import workloads as W
+    batch = W.batch_c2(num_sets=args.num_sets)
+    cores = os.cpu_count() or 1
+    per_step = max(2.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    for step in range(args.warmup + args.steps):
+        v, el, tasks, sec = oracle_throughput(batch, per_step, cores, rng_seed=step + 1)
+        if step >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"c2: {batch.num_sets} sets, n log-uniform [1,1e5], Uniform(0,1] weights, m=1024, "
+                               "variants 1,1a,2,3,3a,4", "m": 1024, "num_sets": batch.num_sets},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"random (set, variant) tasks of the workload for {per_step:.0f} s per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    from paper_1911_00675_gb300 import build, pmh
+    from paper_1911_00675_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    build.build()
+
+    batch = W.batch_c2(seed=0xC0FFEE02 + rank, num_sets=args.num_sets)
+    n_elem = batch.num_elements
+    work = n_elem * len(VARIANTS)
+    m = batch.m
+    ids_h = torch.from_numpy(batch.ids.view(np.int64)).pin_memory()
+    w_h = torch.from_numpy(batch.weights).pin_memory()
+    off_h = torch.from_numpy(batch.offsets).pin_memory()
+    ids = ids_h.to(dev)
+    w = w_h.to(dev)
+    off = off_h.to(dev)
+    S = batch.num_sets
+    out32 = torch.empty((len(VARIANTS), S, m), dtype=torch.int64, device=dev)
+    out64 = torch.empty_like(out32)
+    st32 = torch.empty((len(VARIANTS), S), dtype=torch.int32, device=dev)
+    st64 = torch.empty_like(st32)
+    h = pmh.Handle(local)
+    stream = torch.cuda.current_stream()
+
+    def step(prec, out, st):
+        h.sketch_batch(ids, w, off, m, VARIANTS, prec, 0, out_ids=out, status=st)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---------------- headline: FP32 + recheck
+    h.set_profiling(True)
+    for _ in range(args.warmup):
+        step(pmh.FP32_RECHECK, out32, st32)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    kernel_ms, queue_ms = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(pmh.FP32_RECHECK, out32, st32)
+        q, k = h.last_kernel_ms()
+        queue_ms.append(q)
+        kernel_ms.append(k)
+    e1.record(stream)
+    barrier()
+    t32 = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+
+    # ---------------- comparator: plain FP64
+    for _ in range(min(args.warmup, 2)):
+        step(pmh.FP64, out64, st64)
+    barrier()
+    e0.record(stream)
+    k64 = []
+    for _ in range(args.fp64_steps):
+        step(pmh.FP64, out64, st64)
+        k64.append(h.last_kernel_ms()[1])
+    e1.record(stream)
+    barrier()
+    t64 = max_over_ranks(e0.elapsed_time(e1) / args.fp64_steps)
+    clk = clocks.stop()
+    h.set_profiling(False)
+
+    identical = bool(torch.equal(out32, out64))
+    statuses_ok = bool((st32 == 0).all().item() and (st64 == 0).all().item())
+
+    # ---------------- counters of one (untimed) step
+    cnt = torch.zeros(16, dtype=torch.int64, device=dev)
+    h.sketch_batch(ids, w, off, m, VARIANTS, pmh.FP32_RECHECK, 0, out_ids=out32, status=st32, counters=cnt)
+    torch.cuda.synchronize()
+    c = dict(zip(pmh.COUNTERS, cnt.cpu().tolist()))
+
+    # ---------------- e2e: host buffers in, signatures back, every step
+    e2e = None
+    if not args.no_e2e:
+        out_h = torch.empty(out32.shape, dtype=torch.int64).pin_memory()
+        ids_d, w_d, off_d = torch.empty_like(ids), torch.empty_like(w), torch.empty_like(off)
+
+        def e2e_step():
+            ids_d.copy_(ids_h, non_blocking=True)
+            w_d.copy_(w_h, non_blocking=True)
+            off_d.copy_(off_h, non_blocking=True)
+            h.sketch_batch(ids_d, w_d, off_d, m, VARIANTS, pmh.FP32_RECHECK, 0, out_ids=out32, status=st32)
+            out_h.copy_(out32, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        ksteps = max(3, args.steps // 2)
+        e0.record(stream)
+        for _ in range(ksteps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        te = max_over_ranks(e0.elapsed_time(e1) / ksteps)
+        h2d = ids_h.numel() * 8 + w_h.numel() * 8 + off_h.numel() * 8
+        d2h = out_h.numel() * 8
+        e2e = {"value": work * world / (te * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": te}
+
+    # ---------------- roofline of the dominant kernel (the persistent sketch kernel)
+    k_avg = statistics.mean(kernel_ms)
+    sm_mhz = clk["sm_mhz"] if clk else 2070.0
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    per_launch_ops = (c["elements"] * OPS_KEY + c["prefiltered"] * OPS_FIRST_REJECT + c["points32"] * OPS_POINT)
+    achieved = per_launch_ops / (k_avg * 1e-3) / 1e12
+    peak = n_sms * LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (32-bit lane ops)",
+                "frac": achieved / peak, "traffic": None, "kernel": "pmh::sketch_kernel<FP32>",
+                "kernel_ms": k_avg, "ops_per_launch": per_launch_ops,
+                "peak_basis": f"{n_sms} SMs x {LANES_PER_SM_CLK} lane-ops/clk x {sm_mhz:.0f} MHz (median under load)"}
+
+    # ---------------- CPU baseline (rank 0, N=1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        v, el, tasks, sec = oracle_throughput(batch, args.cpu_seconds, cores)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{tasks} random (set, variant) tasks, {el} elements, {sec:.1f} s wall on {cores} processes"}
+
+    if rank == 0:
+        value = work * world / (t32 * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t32, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"c2: {S} sets, n log-uniform [1,1e5], Uniform(0,1] weights, m=1024, "
+                                   "variants 1,1a,2,3,3a,4 in one persistent launch",
+                       "m": m, "num_sets": S, "elements_per_rank": n_elem, "variants": VARIANTS,
+                       "precision": "fp32 candidates + fp64 recheck", "parallelism": f"weak x{world}",
+                       "l2": f"inputs {(16 * n_elem + 8 * S) / 1e9:.2f} GB per step > 129 MB L2"},
+            "fp64": {"value": work * world / (t64 * 1e-3), "ms_per_step": t64, "kernel_ms": statistics.mean(k64),
+                     "speedup_fp32_vs_fp64": t64 / t32},
+            "identical_output": identical, "status_ok": statuses_ok,
+            "counters": c,
+            "queue_build_ms": statistics.mean(queue_ms),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": (4 + N_FAMILIES) * args.steps,   # queue count/starts/scatter, set stats, one per family
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    h.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

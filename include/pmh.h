@@ -74,7 +74,15 @@ enum {
     PMH_CNT_ROUNDS = 5,       /* threshold rounds beyond the first */
     PMH_CNT_DEEP = 6,         /* elements processed warp-cooperatively */
     PMH_CNT_PREFILTERED = 7,  /* elements rejected without evaluating a logarithm */
-    PMH_NUM_COUNTERS = 8
+    /* SM clock cycles spent per phase, summed over warps (timers read by lane 0) */
+    PMH_CNT_CYC_PASS0 = 8,    /* weight validation and weight sum */
+    PMH_CNT_CYC_FIRST = 9,    /* first points and short sequences (lane per element) */
+    PMH_CNT_CYC_DEEP = 10,    /* warp-cooperative expansion of long sequences */
+    PMH_CNT_CYC_REFRESH = 11, /* q_max refreshes */
+    PMH_CNT_CYC_FINISH = 12,  /* contender resolution and write-out */
+    PMH_CNT_ITEMS = 13,       /* items processed */
+    PMH_CNT_CYC_SURV = 14,    /* survivor processing and segments (includes deep mode) */
+    PMH_NUM_COUNTERS = 16
 };
 
 /* Creates a handle bound to CUDA device `device` (the device is made current
@@ -129,6 +137,17 @@ pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const double *wei
                             int64_t num_sets, uint32_t m, const int32_t *variants, int32_t num_variants,
                             int32_t precision, uint64_t seed, uint64_t *out_ids, double *out_q,
                             int32_t *set_status, uint64_t *counters, void *stream);
+
+/*
+ * Profiling.  pmh_set_profiling(h, 1) makes every later pmh_sketch_batch on
+ * `h` record CUDA events on its stream before the work-queue build, between
+ * the queue build and the persistent sketch kernel, and after the kernel.
+ * pmh_last_kernel_ms waits for the most recent such call to finish and
+ * returns the two intervals in milliseconds (queue build, sketch kernel).
+ * Returns PMH_ERR_INVALID_ARG if profiling was off for that call.
+ */
+pmh_status pmh_set_profiling(pmh_handle h, int32_t enable);
+pmh_status pmh_last_kernel_ms(pmh_handle h, float *queue_ms, float *sketch_ms);
 
 /*
  * pmh_estimate_allpairs -- numerators of the J_P estimator (Eq. jaccard_estimator)

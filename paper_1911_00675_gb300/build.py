@@ -16,8 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpmh.so")
-SOURCES = ["api.cu", "sketch_f32.cu", "sketch_f64.cu"]
-HEADERS = ["pmh_device.cuh", "sketch_kernel.cuh", "launch.h"]
+SOURCES = ["api.cu", "sketch_dispatch.cu"] + [f"sketch_{p}_f{f}.cu" for p in ("f32", "f64") for f in (1, 2, 3, 4)]
+HEADERS = ["pmh_device.cuh", "sketch_kernel.cuh", "sketch_inst.cuh", "launch.h"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",
          "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", os.path.join(HERE, "..", "include")]
@@ -48,7 +48,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         results = list(ex.map(compile_one, SOURCES))
     if verbose:
         for _, err in results:

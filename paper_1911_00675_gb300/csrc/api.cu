@@ -28,7 +28,7 @@ struct GraphKey {
     int64_t num_sets;
     uint32_t m;
     int32_t variants[8];
-    int32_t num_variants, precision;
+    int32_t num_variants, precision, profiling;
     uint64_t seed;
     bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(*this)) == 0; }
 };
@@ -43,7 +43,9 @@ struct pmh_handle_s {
     // work queue
     uint64_t *queue = nullptr;
     int64_t queue_cap = 0;
-    unsigned int *qmeta = nullptr;   // [0..63] histogram, [64..127] starts, [128] head
+    unsigned int *qmeta = nullptr;   // histogram, running starts, per-family heads
+    SetStat *stats = nullptr;        // per-set statistics
+    int64_t stats_cap = 0;
     cudaStream_t cap_stream = nullptr;
     bool graph_valid = false;
     GraphKey gkey{};
@@ -52,6 +54,10 @@ struct pmh_handle_s {
     // planner knobs (tunable)
     float t_c = 4.0f;
     int rounds = 5;
+    // profiling events
+    bool profiling = false;
+    bool prof_recorded = false;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
 };
 
 static pmh_status fail(pmh_handle h, pmh_status code, const char *fmt, ...) {
@@ -133,43 +139,101 @@ static pmh_status get_tables(pmh_handle h, uint32_t m, Tables *out) {
     float lo32 = (float)lo;
     if ((double)lo32 > lo) lo32 = std::nextafterf(lo32, 0.0f);
     t.te_lo = lo32;
+    t.lambda1_32 = (float)lambda1;
     h->tables[m] = tb;
     *out = t;
     return PMH_OK;
 }
 
 // ------------------------------------------------------------------ queue
-// Items (variant, set) sorted by decreasing floor(log2(n+1)) (largest first).
-__global__ void queue_count(const int64_t *off, int64_t num_sets, int32_t nv, unsigned int *meta) {
+// Items (variant, set) in family-major order (ProbMinHash1/1a, 2, 3/3a, 4),
+// each family sorted by decreasing floor(log2(n+1)) (largest sets first).
+// Meta layout: [0, 256) histogram per (family, bucket), [256, 512) running
+// starts, [512, 516) per-family head counters of the persistent kernels.
+constexpr int kQHist = 0, kQStart = 256, kQHead = 512, kQMetaWords = 520;
+
+struct FamOfVariant {
+    int f[8];
+};
+
+__device__ __forceinline__ int queue_bucket(const int64_t *off, int64_t s) {
+    int64_t n = off[s + 1] - off[s];
+    if (n < 0) n = 0;
+    return 63 - __clzll((long long)(n + 1));
+}
+
+__global__ void queue_count(const int64_t *off, int64_t num_sets, int32_t nv, FamOfVariant fv, unsigned int *meta) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < num_sets * nv; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = i % num_sets;
-        int64_t n = off[s + 1] - off[s];
-        if (n < 0) n = 0;
-        const int b = 63 - __clzll((long long)(n + 1));
-        atomicAdd(&meta[b], 1u);
+        const int v = (int)(i / num_sets);
+        atomicAdd(&meta[kQHist + (fv.f[v] - 1) * 64 + queue_bucket(off, s)], 1u);
     }
 }
 __global__ void queue_starts(unsigned int *meta) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         unsigned int acc = 0;
-        for (int b = 63; b >= 0; --b) { meta[64 + b] = acc; acc += meta[b]; }
-        meta[128] = 0;
+        for (int f = 0; f < 4; ++f)
+            for (int b = 63; b >= 0; --b) { meta[kQStart + f * 64 + b] = acc; acc += meta[kQHist + f * 64 + b]; }
+        for (int f = 0; f < 4; ++f) meta[kQHead + f] = 0;
     }
 }
-__global__ void queue_scatter(const int64_t *off, int64_t num_sets, int32_t nv, unsigned int *meta, uint64_t *queue) {
+__global__ void queue_scatter(const int64_t *off, int64_t num_sets, int32_t nv, FamOfVariant fv, unsigned int *meta,
+                              uint64_t *queue) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < num_sets * nv; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = i % num_sets;
         const int64_t v = i / num_sets;
-        int64_t n = off[s + 1] - off[s];
-        if (n < 0) n = 0;
-        const int b = 63 - __clzll((long long)(n + 1));
-        const unsigned int pos = atomicAdd(&meta[64 + b], 1u);
+        const unsigned int pos = atomicAdd(&meta[kQStart + (fv.f[v] - 1) * 64 + queue_bucket(off, s)], 1u);
         queue[pos] = ((uint64_t)v << 40) | (uint64_t)s;
     }
 }
 
+// Per-set statistics, computed once per set for all variants: the weight sum
+// (FP64; it only sets the threshold T), the number of positive weights, and a
+// bad-weight flag (negative, NaN, +-inf, or a subnormal whose reciprocal
+// overflows).  One block per set, grid-stride over sets.
+__global__ void __launch_bounds__(256) set_stats_kernel(const int64_t *off, const double *w, int64_t num_sets,
+                                                        SetStat *out) {
+    __shared__ double ssum[8];
+    __shared__ int snp[8], sbad[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t s = blockIdx.x; s < num_sets; s += gridDim.x) {
+        const int64_t b = off[s], e = off[s + 1];
+        double sum = 0.0;
+        int np = 0, bad = 0;
+        for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+            const double x = w[i];
+            const uint64_t bits = (uint64_t)__double_as_longlong(x);
+            const int ex = (int)(bits >> 52) & 0x7FF;
+            const bool neg = (bits >> 63) != 0;
+            if (ex == 0x7FF || (neg && (bits << 1) != 0)) { bad = 1; continue; }
+            if (neg || (bits << 1) == 0) continue;
+            if (ex == 0 && isinf(__drcp_rn(x))) { bad = 1; continue; }
+            sum += x;
+            np++;
+        }
+        for (int o = 16; o; o >>= 1) {
+            sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+            np += __shfl_xor_sync(0xFFFFFFFFu, np, o);
+            bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, o);
+        }
+        if (lane == 0) { ssum[warp] = sum; snp[warp] = np; sbad[warp] = bad; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double S = 0.0;
+            int N = 0, B = 0;
+            for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { S += ssum[j]; N += snp[j]; B |= sbad[j]; }
+            SetStat r;
+            r.wsum = S;
+            r.npos = N;
+            r.bad = B;
+            out[s] = r;
+        }
+        __syncthreads();
+    }
+}
+
 static pmh_status ensure_queue(pmh_handle h, int64_t items) {
-    if (!h->qmeta) CUDA_TRY(h, cudaMalloc(&h->qmeta, 160 * sizeof(unsigned int)));
+    if (!h->qmeta) CUDA_TRY(h, cudaMalloc(&h->qmeta, kQMetaWords * sizeof(unsigned int)));
     if (items > h->queue_cap) {
         if (h->queue) cudaFree(h->queue);
         h->queue = nullptr;
@@ -183,61 +247,99 @@ static pmh_status ensure_queue(pmh_handle h, int64_t items) {
     return PMH_OK;
 }
 
+static pmh_status ensure_stats(pmh_handle h, int64_t num_sets) {
+    if (num_sets > h->stats_cap) {
+        if (h->stats) cudaFree(h->stats);
+        h->stats = nullptr;
+        h->stats_cap = 0;
+        int64_t cap = num_sets < 1024 ? 1024 : num_sets;
+        cudaError_t e = cudaMalloc(&h->stats, (size_t)cap * sizeof(SetStat));
+        if (e != cudaSuccess) return fail(h, PMH_ERR_NO_MEMORY, "set statistics (%lld sets): %s", (long long)cap, cudaGetErrorString(e));
+        h->stats_cap = cap;
+        h->graph_valid = false;
+    }
+    return PMH_OK;
+}
+
 static uint64_t host_mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
 }
 
-// Launch plan: warp teams when at least 12 warps per SM fit, else CTA teams.
-// Computed outside any stream capture (it sets kernel attributes).
+// Launch plan per family present: warp teams when at least 12 warps per SM
+// fit, else CTA teams.  Computed outside any stream capture (it sets kernel
+// attributes).
 struct Plan {
-    LaunchShape shape;
-    int grid;
+    int nfam;
+    int fam[4];
+    int64_t qbase[4], qlen[4];
+    LaunchShape shape[4];
+    int grid[4];
 };
 
 static pmh_status plan_sketch(pmh_handle h, const SketchParams &p, int precision, Plan *out) {
-    const int64_t items = p.num_sets * p.num_variants;
-    LaunchShape warp_s{}, cta_s{};
-    const bool perm = p.has_perm != 0;
-    cudaError_t e = precision == PMH_FP32_RECHECK ? sketch_shape_f32(false, p.m, perm, &warp_s)
-                                                  : sketch_shape_f64(false, p.m, perm, &warp_s);
-    if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
-    LaunchShape shape = warp_s;
-    if (warp_s.blocks_per_sm * 4 < 12) {
-        e = precision == PMH_FP32_RECHECK ? sketch_shape_f32(true, p.m, perm, &cta_s)
-                                          : sketch_shape_f64(true, p.m, perm, &cta_s);
+    const bool f32 = precision == PMH_FP32_RECHECK;
+    const bool perm = false;   // the permutation arrays are part of the ProbMinHash2/4 kernels' layout
+    int64_t per_fam[4] = {0, 0, 0, 0};
+    for (int v = 0; v < p.num_variants; v++) per_fam[family_of(p.variants[v]) - 1] += p.num_sets;
+    out->nfam = 0;
+    int64_t base = 0;
+    for (int f = 1; f <= 4; f++) {
+        const int64_t items = per_fam[f - 1];
+        if (items == 0) continue;
+        LaunchShape warp_s{}, cta_s{};
+        cudaError_t e = sketch_shape_any(f32, f, false, p.m, perm, &warp_s);
         if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
-        if (cta_s.blocks_per_sm > 0) shape = cta_s;
+        LaunchShape shape = warp_s;
+        if (warp_s.blocks_per_sm * 4 < 12) {
+            e = sketch_shape_any(f32, f, true, p.m, perm, &cta_s);
+            if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
+            if (cta_s.blocks_per_sm > 0) shape = cta_s;
+        }
+        if (shape.blocks_per_sm <= 0) return fail(h, PMH_ERR_UNSUPPORTED, "m = %u does not fit in shared memory", p.m);
+        int grid = h->sm_count * shape.blocks_per_sm;
+        const int64_t teams_needed = shape.cta_team ? items : (items + 3) / 4;
+        if (teams_needed < grid) grid = (int)std::max<int64_t>(1, teams_needed);
+        const int j = out->nfam++;
+        out->fam[j] = f;
+        out->qbase[j] = base;
+        out->qlen[j] = items;
+        out->shape[j] = shape;
+        out->grid[j] = grid;
+        base += items;
     }
-    if (shape.blocks_per_sm <= 0) return fail(h, PMH_ERR_UNSUPPORTED, "m = %u does not fit in shared memory", p.m);
-    int grid = h->sm_count * shape.blocks_per_sm;
-    const int64_t teams_needed = shape.cta_team ? items : (items + 3) / 4;
-    if (teams_needed < grid) grid = (int)std::max<int64_t>(1, teams_needed);
-    out->shape = shape;
-    out->grid = grid;
     return PMH_OK;
 }
 
-// Enqueues the whole batch (queue build + persistent kernel) on `st`.
+// Enqueues the whole batch (queue build + one persistent kernel per family) on `st`.
 static pmh_status enqueue_sketch(pmh_handle h, const SketchParams &p0, const Plan &plan, int precision,
                                  cudaStream_t st) {
     SketchParams p = p0;
     const int64_t items = p.num_sets * p.num_variants;
+    FamOfVariant fv{};
+    for (int v = 0; v < p.num_variants; v++) fv.f[v] = family_of(p.variants[v]);
     const int qb = 256;
     int qg = (int)std::min<int64_t>((items + qb - 1) / qb, (int64_t)h->sm_count * 8);
     if (qg < 1) qg = 1;
-    CUDA_TRY(h, cudaMemsetAsync(h->qmeta, 0, 160 * sizeof(unsigned int), st));
-    queue_count<<<qg, qb, 0, st>>>(p.offsets, p.num_sets, p.num_variants, h->qmeta);
+    if (h->profiling) CUDA_TRY(h, cudaEventRecord(h->ev[0], st));
+    CUDA_TRY(h, cudaMemsetAsync(h->qmeta, 0, kQMetaWords * sizeof(unsigned int), st));
+    queue_count<<<qg, qb, 0, st>>>(p.offsets, p.num_sets, p.num_variants, fv, h->qmeta);
     queue_starts<<<1, 32, 0, st>>>(h->qmeta);
-    queue_scatter<<<qg, qb, 0, st>>>(p.offsets, p.num_sets, p.num_variants, h->qmeta, h->queue);
+    queue_scatter<<<qg, qb, 0, st>>>(p.offsets, p.num_sets, p.num_variants, fv, h->qmeta, h->queue);
+    const int sg = (int)std::min<int64_t>(p.num_sets, (int64_t)h->sm_count * 8);
+    set_stats_kernel<<<sg, 256, 0, st>>>(p.offsets, p.weights, p.num_sets, h->stats);
     CUDA_TRY(h, cudaGetLastError());
-    p.queue = h->queue;
-    p.queue_len = items;
-    p.head = h->qmeta + 128;
-    cudaError_t e = precision == PMH_FP32_RECHECK ? sketch_launch_f32(plan.shape, plan.grid, p, st)
-                                                  : sketch_launch_f64(plan.shape, plan.grid, p, st);
-    if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "sketch launch: %s", cudaGetErrorString(e));
+    p.stats = h->stats;
+    if (h->profiling) CUDA_TRY(h, cudaEventRecord(h->ev[1], st));
+    for (int j = 0; j < plan.nfam; j++) {
+        p.queue = h->queue + plan.qbase[j];
+        p.queue_len = plan.qlen[j];
+        p.head = h->qmeta + kQHead + (plan.fam[j] - 1);
+        cudaError_t e = sketch_launch_any(precision == PMH_FP32_RECHECK, plan.fam[j], plan.shape[j], plan.grid[j], p, st);
+        if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "sketch launch: %s", cudaGetErrorString(e));
+    }
+    if (h->profiling) CUDA_TRY(h, cudaEventRecord(h->ev[2], st));
     return PMH_OK;
 }
 
@@ -270,14 +372,39 @@ extern "C" void pmh_destroy(pmh_handle h) {
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    for (int i = 0; i < 3; i++) if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     for (auto &kv : h->tables) cudaFree(kv.second.dev);
     if (h->queue) cudaFree(h->queue);
     if (h->qmeta) cudaFree(h->qmeta);
+    if (h->stats) cudaFree(h->stats);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
 
 extern "C" const char *pmh_last_error(pmh_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+extern "C" pmh_status pmh_set_profiling(pmh_handle h, int32_t enable) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    if (enable && !h->ev[0])
+        for (int i = 0; i < 3; i++) CUDA_TRY(h, cudaEventCreate(&h->ev[i]));
+    h->profiling = enable != 0;
+    return PMH_OK;
+}
+
+extern "C" pmh_status pmh_last_kernel_ms(pmh_handle h, float *queue_ms, float *sketch_ms) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    if (!h->prof_recorded || !h->ev[0]) return fail(h, PMH_ERR_INVALID_ARG, "profiling was off for the last call");
+    CUDA_TRY(h, cudaEventSynchronize(h->ev[2]));
+    float a = 0.0f, b = 0.0f;
+    CUDA_TRY(h, cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
+    CUDA_TRY(h, cudaEventElapsedTime(&b, h->ev[1], h->ev[2]));
+    if (queue_ms) *queue_ms = a;
+    if (sketch_ms) *sketch_ms = b;
+    return PMH_OK;
+}
 
 extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const double *weights, const int64_t *offsets,
                                        int64_t num_sets, uint32_t m, const int32_t *variants, int32_t num_variants,
@@ -308,6 +435,8 @@ extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const 
     if (rc) return rc;
     rc = ensure_queue(h, num_sets * num_variants);
     if (rc) return rc;
+    rc = ensure_stats(h, num_sets);
+    if (rc) return rc;
 
     SketchParams p{};
     p.ids = ids;
@@ -326,20 +455,25 @@ extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const 
     p.t_factor = (float)(std::log((double)m) + h->t_c);
     p.rounds = h->rounds;
     p.cap_points = (uint32_t)(64.0 * m * std::log((double)m + 1.0)) + 4096;
-    p.has_perm = has_perm ? 1 : 0;
+    (void)has_perm;
 
     Plan plan;
     rc = plan_sketch(h, p, precision, &plan);
     if (rc) return rc;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (st) CUDA_TRY(h, cudaStreamIsCapturing(st, &cs));
-    if (!h->use_graph || cs != cudaStreamCaptureStatusNone || !st) return enqueue_sketch(h, p, plan, precision, st);
+    if (!h->use_graph || cs != cudaStreamCaptureStatusNone || !st) {
+        h->prof_recorded = h->profiling;
+        return enqueue_sketch(h, p, plan, precision, st);
+    }
 
     GraphKey key{};
     key.ids = ids; key.weights = weights; key.offsets = offsets; key.out_ids = out_ids; key.out_q = out_q;
     key.status = set_status; key.counters = counters; key.num_sets = num_sets; key.m = m;
     for (int v = 0; v < num_variants; v++) key.variants[v] = variants[v];
     key.num_variants = num_variants; key.precision = precision; key.seed = seed;
+    key.profiling = h->profiling ? 1 : 0;
+    h->prof_recorded = h->profiling;
     if (!(h->graph_valid && h->gkey == key)) {
         if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
         h->graph_valid = false;

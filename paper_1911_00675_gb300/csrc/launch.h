@@ -15,10 +15,16 @@ struct LaunchShape {
     int blocks_per_sm;  // occupancy (0 = does not fit)
 };
 
-// Occupancy of the sketch kernel for (precision, team shape, m, permutation arrays).
-cudaError_t sketch_shape_f32(bool cta_team, uint32_t m, bool has_perm, LaunchShape *out);
-cudaError_t sketch_shape_f64(bool cta_team, uint32_t m, bool has_perm, LaunchShape *out);
-cudaError_t sketch_launch_f32(const LaunchShape &s, int grid, const SketchParams &p, cudaStream_t st);
-cudaError_t sketch_launch_f64(const LaunchShape &s, int grid, const SketchParams &p, cudaStream_t st);
+// One persistent kernel per (precision, team shape, family): each launch holds
+// only its own family's code.  Defined in sketch_<precision>_f<family>.cu.
+template <bool F32, int FAM>
+cudaError_t sketch_shape(bool cta_team, uint32_t m, bool has_perm, LaunchShape *out);
+template <bool F32, int FAM>
+cudaError_t sketch_launch(const LaunchShape &s, int grid, const SketchParams &p, cudaStream_t st);
+
+// Dispatch on (precision, family) at run time.
+cudaError_t sketch_shape_any(bool f32, int fam, bool cta_team, uint32_t m, bool has_perm, LaunchShape *out);
+cudaError_t sketch_launch_any(bool f32, int fam, const LaunchShape &s, int grid, const SketchParams &p,
+                              cudaStream_t st);
 
 }  // namespace pmh

@@ -20,12 +20,13 @@ constexpr uint32_t kFull = 0xFFFFFFFFu;
 // Relative error bound of every FP32 point value against its canonical FP64
 // value: |x32 - x64| <= kEta * x32.  The sources (each in units u = 2^-24):
 // 1/w from a truncated mantissa and a correctly rounded reciprocal (3u),
-// Exp(1) via log1pf/logf (max 1 ulp each) with a correctly rounded U (5u),
-// Exp(lambda;0,1) via log1pf with |U*expm1(-lambda)| <= 1/2 (10u), the table
-// entries and their products (<= 4u), the FP32 prefix sums of the uncorrelated
-// families (warp scan of positive terms plus an error-free carry, <= 7u), the
-// final product (u) and the FP64 value's own rounding (< u).  The worst family
-// totals below 20u; kEta = 64u leaves a factor of three.
+// Exp(1) via log1pf/logf (max 1 ulp each) with a truncated U (6u),
+// Exp(lambda;0,1) via log1pf with |U*expm1(-lambda)| <= 1/2 (12u), the table
+// entries and their products (<= 4u), the FP32 sums of the uncorrelated
+// families (a lane-sequential running sum of at most 32 positive terms, <= 31u;
+// in deep mode a warp scan plus an error-free carry, <= 7u), the final
+// product (u) and the FP64 value's own rounding (< u).  The worst family
+// totals below 48u; kEta = 64u covers it.
 constexpr float kEta = 0x1p-18f;
 
 __host__ __device__ inline int family_of(int variant) {
@@ -46,6 +47,7 @@ struct Tables {
     double c3, inv3, delta; // ProbMinHash3: expm1(-lambda), 1/lambda; ProbMinHash4: delta = 1/lambda_1
     float c3_32, inv3_32, delta32;
     float te_lo;            // (1-e^{-lambda_1})/lambda_1 rounded down: Exp(lambda_1;0,1) >= U * te_lo
+    float lambda1_32;       // lambda_1 = log(1 + 1/(m-1))
 };
 
 // ------------------------------------------------------------------ stream
@@ -106,25 +108,35 @@ __device__ __forceinline__ double lower4_64(const Tables &T, uint32_t i, double 
 }
 
 // ------------------------------------------------------------ FP32 (filter)
+// k * 2^-53 as a float for a 53-bit integer k, built from integer operations
+// (normalise, truncate the mantissa to 23 bits): relative error < 2^-23, and
+// exactly 0 for k = 0.  Keeps the FP32 path off the FP64 / conversion pipes.
+__device__ __forceinline__ float u53_to_float(uint64_t k) {
+    if (k == 0) return 0.0f;
+    const int lz = __clzll((long long)k);          // 11..63
+    const uint64_t nrm = k << lz;                   // leading one at bit 63
+    const uint32_t mant = (uint32_t)(nrm >> 40) & 0x7FFFFFu;
+    const uint32_t ex = (uint32_t)(63 - lz - 53 + 127);
+    return __uint_as_float((ex << 23) | mant);
+}
 // Exp(1): for U < 1/2 log1pf(-U) keeps relative accuracy; otherwise V = 1-U is
 // formed exactly in integers before the conversion.
 __device__ __forceinline__ float exp1_32(uint64_t w) {
     uint64_t k = w >> 11;
-    if (k < (1ull << 52)) {
-        float u = __fmul_rn(__ull2float_rn(k), 0x1p-53f);
-        return -log1pf(-u);
-    }
-    float v = __fmul_rn(__ull2float_rn((1ull << 53) - k), 0x1p-53f);
-    return -logf(v);
+    if (k < (1ull << 52)) return -log1pf(-u53_to_float(k));
+    return -logf(u53_to_float((1ull << 53) - k));
 }
 __device__ __forceinline__ float texp_32(uint64_t w, float c, float inv) {
-    float u = __fmul_rn(__ull2float_rn(w >> 11), 0x1p-53f);
-    float l = log1pf(__fmul_rn(u, c));
+    float l = log1pf(__fmul_rn(u53_to_float(w >> 11), c));
     return __fmul_rn(-l, inv);
 }
-// A lower bound of U with 23-bit resolution (exact conversion of a 23-bit integer).
+// A positive, finite weight (the item's weights are validated before use):
+// the sign bit is clear and the bits are not all zero (rejects +-0).
+__device__ __forceinline__ bool weight_positive(double w) { return __double_as_longlong(w) > 0; }
+// A lower bound of U with 23-bit resolution: 1.f - 1 for the float 1.f whose
+// mantissa is the word's top 23 bits (the subtraction is exact).
 __device__ __forceinline__ float unif_lo(uint64_t w) {
-    return __fmul_rn(__uint2float_rn((uint32_t)(w >> 41)), 0x1p-23f);
+    return __fsub_rn(__uint_as_float(0x3F800000u | (uint32_t)(w >> 41)), 1.0f);
 }
 
 // 1/w scaled by 2^sigma as a float, from the double's bits (mantissa

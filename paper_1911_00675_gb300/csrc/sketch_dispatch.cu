@@ -1,0 +1,41 @@
+// Run-time dispatch to the per-(precision, family) sketch kernels.
+#include "launch.h"
+
+namespace pmh {
+
+cudaError_t sketch_shape_any(bool f32, int fam, bool cta_team, uint32_t m, bool has_perm, LaunchShape *out) {
+    if (f32) {
+        switch (fam) {
+            case 1: return sketch_shape<true, 1>(cta_team, m, has_perm, out);
+            case 2: return sketch_shape<true, 2>(cta_team, m, has_perm, out);
+            case 3: return sketch_shape<true, 3>(cta_team, m, has_perm, out);
+            default: return sketch_shape<true, 4>(cta_team, m, has_perm, out);
+        }
+    }
+    switch (fam) {
+        case 1: return sketch_shape<false, 1>(cta_team, m, has_perm, out);
+        case 2: return sketch_shape<false, 2>(cta_team, m, has_perm, out);
+        case 3: return sketch_shape<false, 3>(cta_team, m, has_perm, out);
+        default: return sketch_shape<false, 4>(cta_team, m, has_perm, out);
+    }
+}
+
+cudaError_t sketch_launch_any(bool f32, int fam, const LaunchShape &s, int grid, const SketchParams &p,
+                              cudaStream_t st) {
+    if (f32) {
+        switch (fam) {
+            case 1: return sketch_launch<true, 1>(s, grid, p, st);
+            case 2: return sketch_launch<true, 2>(s, grid, p, st);
+            case 3: return sketch_launch<true, 3>(s, grid, p, st);
+            default: return sketch_launch<true, 4>(s, grid, p, st);
+        }
+    }
+    switch (fam) {
+        case 1: return sketch_launch<false, 1>(s, grid, p, st);
+        case 2: return sketch_launch<false, 2>(s, grid, p, st);
+        case 3: return sketch_launch<false, 3>(s, grid, p, st);
+        default: return sketch_launch<false, 4>(s, grid, p, st);
+    }
+}
+
+}  // namespace pmh

@@ -1,10 +1,13 @@
-// Persistent ProbMinHash sketch kernel (template over precision and team shape).
+// Persistent ProbMinHash sketch kernel (template over precision, team shape
+// and algorithm family).
 //
 // GPU design (replaces the paper's sequential element loop, Algorithm
 // "Basic structure of ProbMinHash algorithms"):
 //   * A team (one warp, or a whole CTA) owns one work item = (set, variant) at
 //     a time; its signature lives in shared memory.  Items come from a global
-//     queue ordered by decreasing set size.
+//     queue, one segment per family, ordered by decreasing set size; each
+//     family has its own persistent kernel so a launch carries only that
+//     family's code.
 //   * Threshold rounds.  The sequential algorithm lets q_max fall element by
 //     element; a data-parallel pass cannot wait for that.  Round r instead
 //     stops every element at min(T*4^r, q_max) with T = m(ln m + c)/sum(w):
@@ -13,14 +16,18 @@
 //     Every point <= the final q_max is still generated (q_max only decreases),
 //     so the signature is exactly that of the paper; a round that leaves a
 //     component empty is repeated with a larger T (offers are idempotent), and
-//     the last round has T = +inf.
-//   * First points: one lane per element, with a log-free prefilter
-//     (Exp(1) >= U, Exp(lambda;0,1) >= U*(1-e^-lambda)/lambda).  Survivors
-//     continue lane-sequentially for a few points; longer sequences go to a
-//     warp queue and are expanded 32 points at a time (warp scan of the
-//     uncorrelated spacings, Eq. uncorrelated_recursion; the lazy
+//     the last round has T = +inf.  sum(w) comes from a per-set statistics
+//     kernel that runs once per set for all variants.
+//   * Filter: each lane takes two elements per step and rejects the first
+//     point without a logarithm (Exp(1) >= U, Exp(lambda;0,1) >=
+//     U(1-e^-lambda)/lambda).  Survivors are compacted and processed 32 at a
+//     time (first point, label, offer, continuation count); continuations are
+//     packed as segments of consecutive points into 32-lane rounds (segmented
+//     scan of the uncorrelated spacings, Eq. uncorrelated_recursion; the lazy
 //     Fisher-Yates permutation of Algorithm "Lazy generation of random
-//     permutation elements" resolved inside the group with match/shuffle).
+//     permutation elements" resolved inside the round with match/shuffle).
+//     Sequences longer than one round are expanded 32 points at a time in
+//     deep mode.
 //   * q_max (Sec. Stop Limit Update) is a warp max-reduction over the shared
 //     signature, refreshed after updates, instead of the binary tree.
 //   * FP64 path: each component holds (q, id), updated with a 128-bit CAS
@@ -37,19 +44,28 @@
 
 namespace pmh {
 
-constexpr int kMaxCont = 64;     // contender records per team (overflow -> PMH_ERR_ITER_LIMIT)
-constexpr int kLSeq = 4;         // points generated lane-sequentially before the warp queue
-constexpr int kCasLimit = 1 << 16;
+constexpr int kMaxCont = 64;       // contender records per team (overflow -> PMH_ERR_ITER_LIMIT)
+constexpr int kCasLimit = 1 << 16; // CAS retries per offer (each failure means another offer succeeded)
+constexpr int kSurvCap = 128;      // survivor buffer per warp: < 64 left over + <= 64 new per filter step
+constexpr int kSurvBatch = 64;     // survivors expanded together (keeps the lanes of the expansion busy)
 
 struct __align__(16) Rec64 {
     double q;
     unsigned long long id;
 };
 
+// Per-set statistics (one entry per set, computed once for all variants).
+struct SetStat {
+    double wsum;   // sum of the positive weights
+    int npos;      // elements with w > 0
+    int bad;       // a weight is negative, NaN, infinite, or has no finite reciprocal
+};
+
 struct SketchParams {
     const uint64_t *ids;
     const double *weights;
     const int64_t *offsets;
+    const SetStat *stats;
     int64_t num_sets;
     uint32_t m;
     uint64_t mixed_seed;          // mix64(seed)
@@ -60,13 +76,12 @@ struct SketchParams {
     double *out_q;
     int32_t *status;
     unsigned long long *counters;
-    const uint64_t *queue;        // (variant index << 40) | set index
+    const uint64_t *queue;        // this family's segment: (variant index << 40) | set index
     int64_t queue_len;
-    unsigned int *head;           // next queue position
+    unsigned int *head;           // next queue position of this family
     float t_factor;               // ln m + c
     int rounds;                   // finite-T rounds before the T = +inf round
     uint32_t cap_points;          // iteration cap (with replacement)
-    int has_perm;                 // shared permutation arrays allocated
 };
 
 struct TeamShared {
@@ -78,21 +93,26 @@ struct TeamShared {
     int sigma;
     double bound64;     // FP64 path: exact stop bound
     float t_s;          // T * 2^sigma
-    int n_pos;
-    float red_s[32];
-    int red_e[32];
-    int red_i[32];
     uint32_t cont_k[kMaxCont];
     uint32_t cont_e[kMaxCont];
 };
 
 struct WarpShared {
-    uint32_t dq[32];
+    unsigned long long cnt[PMH_NUM_COUNTERS];   // work counters of this warp (lane 0 adds)
+    uint32_t dq[kSurvCap];     // deep-mode queue (element indices)
     int dq_n;
-    int slot[32];
+    int slot[32];              // Fisher-Yates scratch (deep mode)
+    uint32_t sb_e[kSurvCap];   // prefilter survivors: element index
+    uint64_t sb_key[kSurvCap]; //   and stream key
+    int sb_n;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// ProbMinHash2/4 per-warp region: the dense permutation of deep mode (m x u16)
+// followed by the per-lane Fisher-Yates write lists (kFyCap x 32 x u32).
+constexpr int kFyCap = 32;
+__host__ __device__ inline size_t perm_bytes(uint32_t m) { return align16((size_t)m * 2) + (size_t)kFyCap * 32 * 4; }
 
 struct SmemLayout {
     size_t team_off, sig_off, warp_off, perm_off, total;
@@ -101,29 +121,23 @@ struct SmemLayout {
         sig_off = align16(team_off + (size_t)teams * align16(sizeof(TeamShared)));
         warp_off = align16(sig_off + (size_t)teams * m * (f32 ? 8 : 16));
         perm_off = align16(warp_off + (size_t)warps * align16(sizeof(WarpShared)));
-        total = align16(perm_off + (perm ? (size_t)warps * m * 2 : 0));
+        total = align16(perm_off + (perm ? (size_t)warps * perm_bytes(m) : 0));
     }
 };
 
-// Work counters kept in registers and flushed once per item.
-struct Counters {
-    unsigned long long c[PMH_NUM_COUNTERS];
-};
-
 // ------------------------------------------------------------------------
-// Per-item context.
+// Per-item context (registers).
 template <bool F32>
 struct Ctx {
     const SketchParams *p;
     TeamShared *ts;
     void *sig;
     WarpShared *ws;
-    uint16_t *perm;     // this warp's permutation array (or null)
+    uint16_t *perm;     // this warp's permutation array (ProbMinHash2/4), else null
+    uint32_t *fy;       // this warp's Fisher-Yates write lists [kFyCap][32] (ProbMinHash2/4)
     int64_t beg;
     uint32_t n;
     int sigma;
-    int fam;
-    Counters cnt;
 };
 
 __device__ __forceinline__ float ld_volatile(const float *p) { return *(volatile const float *)p; }
@@ -137,6 +151,12 @@ __device__ __forceinline__ void atomic_min_pos_float(float *addr, float v) {
 __device__ __forceinline__ void atomic_min_pos_double(double *addr, double v) {
     atomicMin((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
 }
+// Warp-uniform counter update (lane 0 adds).
+template <bool F32>
+__device__ __forceinline__ void count(Ctx<F32> &c, int idx, unsigned long long v) {
+    if ((threadIdx.x & 31) == 0) c.ws->cnt[idx] += v;
+}
+__device__ __forceinline__ unsigned popc_ballot(bool b) { return __popc(__ballot_sync(kFull, b)); }
 
 // ------------------------------------------------------------ offers
 template <bool F32> struct Offer;
@@ -167,7 +187,7 @@ template <> struct Offer<true> {
                 c.ts->cont_k[at + 1] = k;
                 c.ts->cont_e[at + 1] = (uint32_t)(old & 0xFFFFFFFFu);
             }
-            c.cnt.c[PMH_CNT_CONTENDERS] += 1;
+            atomicAdd(&c.ws->cnt[PMH_CNT_CONTENDERS], 1ull);
         }
         return key < old;
     }
@@ -204,13 +224,11 @@ template <bool F32>
 __device__ void refresh_bound(Ctx<F32> &c) {
     const int lane = threadIdx.x & 31;
     const uint32_t m = c.p->m;
+    const long long t0 = clock64();
     if constexpr (F32) {
         const uint64_t *sig = (const uint64_t *)c.sig;
         uint32_t mx = 0;
-        for (uint32_t k = lane; k < m; k += 32) {
-            uint32_t hi = (uint32_t)(ld_volatile(&sig[k]) >> 32);
-            mx = max(mx, hi);
-        }
+        for (uint32_t k = lane; k < m; k += 32) mx = max(mx, (uint32_t)(ld_volatile(&sig[k]) >> 32));
         for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
         if (lane == 0 && mx != 0xFFFFFFFFu) atomic_min_pos_float(&c.ts->bound32, __uint_as_float(mx) * (1.0f + 2.0f * kEta));
     } else {
@@ -223,6 +241,7 @@ __device__ void refresh_bound(Ctx<F32> &c) {
             atomic_min_pos_float(&c.ts->bound32, __double2float_ru(ldexp(mx, c.sigma)));
         }
     }
+    count(c, PMH_CNT_CYC_REFRESH, (unsigned long long)(clock64() - t0));
 }
 
 // ------------------------------------------------------------ Fisher-Yates group
@@ -265,137 +284,53 @@ __device__ __forceinline__ uint32_t fy_group(uint16_t *perm, int *slot, uint32_t
     return label;
 }
 
-// Sparse Fisher-Yates for the first kLSeq steps of one element (registers).
-struct SparseFY {
-    uint32_t r[kLSeq], mv[kLSeq];
-    __device__ __forceinline__ uint32_t lookup(uint32_t pos, int t) const {
-        uint32_t v = pos;
-#pragma unroll
-        for (int s = 0; s < kLSeq; ++s)
-            if (s < t && r[s] == pos) v = mv[s];
-        return v;
+// Segmented Fisher-Yates inside one round: lanes [a, a+len) hold steps
+// 0..len-1 of one element whose permutation is still the identity (the
+// segment starts at step 0).  Returns each lane's label; the dependency rules
+// are those of fy_group.
+__device__ __forceinline__ uint32_t fy_segment(int *slot, uint32_t m, int a, int len, int t, uint64_t lw, bool act) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t r = act ? (uint32_t)t + uniform_int(lw, m - (uint32_t)t) : 0xFFFFFFFFu;
+    slot[lane] = -1;
+    __syncwarp();
+    // a write to position p < len of this element lands in lane a + p (the lane of step p);
+    // positions >= len belong to no step of the segment and are read only as labels
+    if (act && r != (uint32_t)t && r < (uint32_t)len) atomicMax(&slot[a + (int)r], lane);
+    __syncwarp();
+    int ptr = act ? slot[lane] : -1;
+    uint32_t val = (act && ptr < 0) ? (uint32_t)t : 0u;     // identity: P[t] = t
+    for (int it = 0; it < 5; ++it) {
+        int src = ptr >= 0 ? ptr : lane;
+        uint32_t v2 = __shfl_sync(kFull, val, src);
+        int p2 = __shfl_sync(kFull, ptr, src);
+        if (ptr >= 0) {
+            if (p2 < 0) { val = v2; ptr = -1; } else ptr = p2;
+        }
     }
-    __device__ __forceinline__ uint32_t step(int t, uint64_t lw, uint32_t m) {
-        uint32_t rt = (uint32_t)t + uniform_int(lw, m - (uint32_t)t);
-        uint32_t moved = lookup((uint32_t)t, t);
-        uint32_t label = lookup(rt, t);
-#pragma unroll
-        for (int s = 0; s < kLSeq; ++s)
-            if (s == t) { r[s] = rt; mv[s] = moved; }
-        return label;
-    }
-};
+    const uint32_t key = act ? (((uint32_t)a << 16) | r) : 0xFFFFFFFFu;
+    const uint32_t same = __match_any_sync(kFull, key);
+    const uint32_t earlier = same & ((1u << lane) - 1u);
+    const int w2 = (act && earlier) ? 31 - __clz(earlier) : -1;
+    const uint32_t from_lane = __shfl_sync(kFull, val, w2 >= 0 ? w2 : lane);
+    __syncwarp();
+    return (w2 >= 0) ? from_lane : r;   // identity: P[r] = r
+}
 
-// ------------------------------------------------------------ element weights
-struct ElemW {
-    double w_inv;    // FP64 path
-    float winv32;    // scaled FP32 reciprocal (both paths: prefilter)
-};
-
-// ------------------------------------------------------------ stage A
-// One lane, one element: first point (with prefilter) and up to kLSeq points
-// sequentially.  Returns kNeedDeep if the element needs the warp queue, plus
-// kWon if one of its offers became a component minimum.
-constexpr int kNeedDeep = 1, kWon = 2;
-template <int FAM, bool F32>
-__device__ int stage_a(Ctx<F32> &c, uint32_t e, uint64_t id, double w) {
-    const SketchParams &P = *c.p;
-    const Tables &T = P.tab;
-    const uint32_t m = P.m;
-    ElemW ew;
-    ew.winv32 = winv_scaled(w, c.sigma);
-    ew.w_inv = F32 ? 0.0 : __drcp_rn(w);
-    const uint64_t key = mix64(id ^ P.mixed_seed);
-    c.cnt.c[PMH_CNT_ELEMENTS] += 1;
-    uint64_t vw = value_word(key, 1);
-    // log-free prefilter on the first point: x_1 >= w_inv * U (* te_lo for the correlated families)
-    {
-        float b32 = ld_volatile(&c.ts->bound32);
-        float xlo = ew.winv32 * unif_lo(vw);
-        if (FAM >= 3) xlo *= T.te_lo;
-        if (xlo * (1.0f - 8.0f * 0x1p-24f) > b32) {
-            c.cnt.c[PMH_CNT_PREFILTERED] += 1;
-            return 0;
-        }
-    }
-    int won = 0;
-    SparseFY fy;
-    float s32 = 0.0f;      // F1/F2: running unscaled sum (FP32)
-    double x64 = 0.0;      // F1/F2: running value (FP64)
-#pragma unroll 1
-    for (int i = 1; i <= kLSeq; ++i) {
-        if ((FAM == 2 || FAM == 4) && (uint32_t)i > m) return won;
-        if (FAM == 1 || FAM == 3) {
-            if ((uint32_t)i > P.cap_points) { c.ts->status = PMH_ERR_ITER_LIMIT; return won; }
-        }
-        if (i > 1) vw = value_word(key, (uint64_t)i);
-        // correlated: lower bound of point i
-        if (FAM >= 3 && i > 1) {
-            if constexpr (F32) {
-                float lb = (FAM == 3) ? ew.winv32 * (float)(i - 1) : ew.winv32 * T.gamma32[i - 1];
-                if (lb * (1.0f - kEta) > ld_volatile(&c.ts->bound32)) return won;
-            } else {
-                double lb = (FAM == 3) ? lower3_64((uint64_t)i, ew.w_inv) : lower4_64(T, (uint32_t)i, ew.w_inv);
-                if (lb > ld_volatile(&c.ts->bound64)) return won;
-            }
-        }
-        // point value
-        bool beyond;
-        float x32 = 0.0f;
-        if constexpr (F32) {
-            if (FAM == 1) { s32 = __fadd_rn(s32, exp1_32(vw)); x32 = __fmul_rn(ew.winv32, s32); }
-            else if (FAM == 2) { s32 = __fadd_rn(s32, __fmul_rn(T.beta32[i], exp1_32(vw))); x32 = __fmul_rn(ew.winv32, s32); }
-            else if (FAM == 3) { x32 = __fmul_rn(ew.winv32, __fadd_rn((float)(i - 1), texp_32(vw, T.c3_32, T.inv3_32))); }
-            else {
-                float sv;
-                if ((uint32_t)i < m) sv = __fadd_rn(T.gamma32[i - 1], __fmul_rn(T.dgamma32[i], texp_32(vw, T.c4_32[i], T.inv4_32[i])));
-                else sv = __fadd_rn(T.gamma32[m - 1], __fmul_rn(T.delta32, exp1_32(vw)));
-                x32 = __fmul_rn(ew.winv32, sv);
-            }
-            c.cnt.c[PMH_CNT_POINTS32] += 1;
-            beyond = x32 * (1.0f - kEta) > ld_volatile(&c.ts->bound32);
-        } else {
-            if (FAM == 1) x64 = __dadd_rn(x64, term1_64(vw, ew.w_inv));
-            else if (FAM == 2) x64 = __dadd_rn(x64, term2_64(T, vw, (uint32_t)i, ew.w_inv));
-            else if (FAM == 3) x64 = point3_64(T, vw, (uint64_t)i, ew.w_inv);
-            else x64 = point4_64(T, vw, (uint32_t)i, ew.w_inv);
-            c.cnt.c[PMH_CNT_POINTS64] += 1;
-            beyond = x64 > ld_volatile(&c.ts->bound64);
-        }
-        if ((FAM == 1 || FAM == 2) && beyond) return won;   // uncorrelated: points increase
-        // label
-        uint64_t lw = label_word(key, (uint64_t)i);
-        uint32_t k;
-        if (FAM == 1 || FAM == 3) k = uniform_int(lw, m);
-        else k = fy.step(i - 1, lw, m);
-        if (!beyond) {
-            bool wi;
-            if constexpr (F32) wi = Offer<true>::run(c, k, x32, e);
-            else wi = Offer<false>::run(c, k, x64, id);
-            if (wi) won = kWon;
-        }
-        if ((FAM == 2 || FAM == 4) && (uint32_t)i == m) return won;   // the sequence has m points
-    }
-    // still going after kLSeq points?
-    if (FAM == 1 || FAM == 2) return won | kNeedDeep;   // the last point was <= bound
-    if (FAM == 4 && (uint32_t)kLSeq >= m) return won;
-    bool more;
-    if constexpr (F32) {
-        float lb = (FAM == 3) ? ew.winv32 * (float)kLSeq : ew.winv32 * T.gamma32[kLSeq];
-        more = !(lb * (1.0f - kEta) > ld_volatile(&c.ts->bound32));
-    } else {
-        double lb = (FAM == 3) ? lower3_64((uint64_t)kLSeq + 1, ew.w_inv) : lower4_64(T, (uint32_t)kLSeq + 1, ew.w_inv);
-        more = !(lb > ld_volatile(&c.ts->bound64));
-    }
-    return won | (more ? kNeedDeep : 0);
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+    uint32_t lo = __shfl_sync(kFull, (uint32_t)v, src);
+    uint32_t hi = __shfl_sync(kFull, (uint32_t)(v >> 32), src);
+    return ((uint64_t)hi << 32) | lo;
+}
+__device__ __forceinline__ double shfl_d(double v, int src) {
+    return __longlong_as_double((long long)shfl64((uint64_t)__double_as_longlong(v), src));
 }
 
 // ------------------------------------------------------------ deep mode
 // Warp-cooperative expansion of one element from point 1, 32 points per step.
-// mode 0: offer points <= bound.  mode 1 (exact search): stop at the first
-// point with label `want` and return its canonical FP64 value in *out.
+// EXACT = false: offer points <= bound.  EXACT = true (exact search): stop at
+// the first point with label `want` and return its canonical FP64 value.
 template <int FAM, bool F32, bool EXACT>
-__device__ void deep(Ctx<F32> &c, uint32_t e, uint32_t want, double *out) {
+__device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
     const SketchParams &P = *c.p;
     const Tables &T = P.tab;
     const uint32_t m = P.m;
@@ -409,7 +344,7 @@ __device__ void deep(Ctx<F32> &c, uint32_t e, uint32_t want, double *out) {
         for (uint32_t p = lane; p < m; p += 32) c.perm[p] = (uint16_t)p;
         __syncwarp();
     }
-    if (!EXACT) c.cnt.c[PMH_CNT_DEEP] += (lane == 0);
+    if (!EXACT) count(c, PMH_CNT_DEEP, 1);
     double carry64 = 0.0;
     float c_hi = 0.0f, c_lo = 0.0f;
     const uint32_t limit = (FAM == 2 || FAM == 4) ? m : P.cap_points;
@@ -417,8 +352,7 @@ __device__ void deep(Ctx<F32> &c, uint32_t e, uint32_t want, double *out) {
     for (uint32_t base = 1;; base += 32) {
         if (base > limit) {
             if (FAM == 1 || FAM == 3) { if (lane == 0) c.ts->status = PMH_ERR_ITER_LIMIT; }
-            if (EXACT && lane == 0) *out = __longlong_as_double(0x7FF0000000000001ll);
-            return;
+            return __longlong_as_double(0x7FF0000000000001ll);
         }
         // correlated: the group starts beyond the bound?
         if (!EXACT && FAM >= 3) {
@@ -430,19 +364,18 @@ __device__ void deep(Ctx<F32> &c, uint32_t e, uint32_t want, double *out) {
                 double lb = (FAM == 3) ? lower3_64(base, w_inv) : lower4_64(T, base, w_inv);
                 stop = lb > ld_volatile(&c.ts->bound64);
             }
-            if (__shfl_sync(kFull, (int)stop, 0)) return;
+            if (__shfl_sync(kFull, (int)stop, 0)) return 0.0;
         }
         const uint32_t i = base + lane;
         const bool act = i <= limit;
         const uint64_t vw = act ? value_word(key, i) : 0;
         const uint64_t lw = act ? label_word(key, i) : 0;
-        // labels
         uint32_t k;
         if (FAM == 1 || FAM == 3) k = uniform_int(lw, m);
         else k = fy_group(c.perm, c.ws->slot, m, base - 1, lw, act);
         if constexpr (EXACT) {
-            unsigned hit = __ballot_sync(kFull, act && k == want);
-            // FP64 canonical values of this group (needed for the carry and the hit)
+            const unsigned hit = __ballot_sync(kFull, act && k == want);
+            // canonical FP64 values of this group (the uncorrelated families need the carry)
             double x = 0.0;
             if (FAM == 1 || FAM == 2) {
                 double t = act ? (FAM == 1 ? term1_64(vw, w_inv) : term2_64(T, vw, i, w_inv)) : 0.0;
@@ -457,18 +390,10 @@ __device__ void deep(Ctx<F32> &c, uint32_t e, uint32_t want, double *out) {
                 int src = __ffs(hit) - 1;
                 if (lane == src) x = (FAM == 3) ? point3_64(T, vw, i, w_inv) : point4_64(T, vw, i, w_inv);
             }
-            if (hit) {
-                int src = __ffs(hit) - 1;
-                double v = __shfl_sync(kFull, x, src);
-                if (lane == 0) *out = v;
-                c.cnt.c[PMH_CNT_RESOLVED] += (lane == 0);
-                return;
-            }
+            if (hit) return __shfl_sync(kFull, x, __ffs(hit) - 1);
             continue;
         }
-        // values and offers
-        bool last_beyond;
-        bool any_win;
+        bool last_beyond, any_win;
         if constexpr (F32) {
             float x32;
             if (FAM == 1 || FAM == 2) {
@@ -479,6 +404,7 @@ __device__ void deep(Ctx<F32> &c, uint32_t e, uint32_t want, double *out) {
                     if (lane >= o) s = __fadd_rn(s, y);
                 }
                 x32 = __fmul_rn(winv32, __fadd_rn(c_hi, __fadd_rn(c_lo, s)));
+                // error-free carry (TwoSum): c_hi + c_lo = sum of all earlier groups exactly
                 float tot = __shfl_sync(kFull, s, 31);
                 float sh = __fadd_rn(c_hi, tot);
                 float bb = __fsub_rn(sh, c_hi);
@@ -495,21 +421,19 @@ __device__ void deep(Ctx<F32> &c, uint32_t e, uint32_t want, double *out) {
                 }
                 x32 = __fmul_rn(winv32, sv);
             }
-            c.cnt.c[PMH_CNT_POINTS32] += act;
-            const float b32 = ld_volatile(&c.ts->bound32);
-            const bool beyond = x32 * (1.0f - kEta) > b32;
+            count(c, PMH_CNT_POINTS32, popc_ballot(act));
+            const bool beyond = x32 * (1.0f - kEta) > ld_volatile(&c.ts->bound32);
             bool wi = false;
             if (act && !beyond) wi = Offer<true>::run(c, k, x32, e);
             any_win = __any_sync(kFull, wi);
-            const int last = (int)min((uint32_t)31, limit - base);
-            last_beyond = __shfl_sync(kFull, (int)beyond, last);
+            last_beyond = __shfl_sync(kFull, (int)beyond, (int)min((uint32_t)31, limit - base));
         } else {
             double x;
             if (FAM == 1 || FAM == 2) {
                 double t = act ? (FAM == 1 ? term1_64(vw, w_inv) : term2_64(T, vw, i, w_inv)) : 0.0;
                 double run = carry64;
                 x = 0.0;
-                for (int s = 0; s < 32; ++s) {
+                for (int s = 0; s < 32; ++s) {   // canonical left-to-right sum
                     double ts = __shfl_sync(kFull, t, s);
                     run = __dadd_rn(run, ts);
                     if (lane == s) x = run;
@@ -520,48 +444,240 @@ __device__ void deep(Ctx<F32> &c, uint32_t e, uint32_t want, double *out) {
             } else {
                 x = act ? point4_64(T, vw, i, w_inv) : 0.0;
             }
-            c.cnt.c[PMH_CNT_POINTS64] += act;
-            const double b64 = ld_volatile(&c.ts->bound64);
-            const bool beyond = x > b64;
+            count(c, PMH_CNT_POINTS64, popc_ballot(act));
+            const bool beyond = x > ld_volatile(&c.ts->bound64);
             bool wi = false;
             if (act && !beyond) wi = Offer<false>::run(c, k, x, id);
             any_win = __any_sync(kFull, wi);
-            const int last = (int)min((uint32_t)31, limit - base);
-            last_beyond = __shfl_sync(kFull, (int)beyond, last);
+            last_beyond = __shfl_sync(kFull, (int)beyond, (int)min((uint32_t)31, limit - base));
         }
-        if (base + 31 >= limit && (FAM == 2 || FAM == 4)) return;
-        if ((FAM == 1 || FAM == 2) && last_beyond) return;
+        if (base + 31 >= limit && (FAM == 2 || FAM == 4)) return 0.0;
+        if ((FAM == 1 || FAM == 2) && last_beyond) return 0.0;
         // keep q_max fresh while expanding (after groups that changed a minimum)
-        int uf = __shfl_sync(kFull, lane == 0 ? ld_volatile(&c.ts->unfilled) : 1, 0);
+        const int uf = __shfl_sync(kFull, lane == 0 ? ld_volatile(&c.ts->unfilled) : 1, 0);
         if (uf == 0 && any_win) refresh_bound<F32>(c);
     }
 }
 
 // Exact FP64 value of h_k(e) (the first point of element e with label k).
+// Cold path (contender resolution, exact q output): kept out of line.
 template <int FAM, bool F32>
-__device__ double exact_h(Ctx<F32> &c, uint32_t e, uint32_t k) {
-    __shared__ double xs[32];   // per warp slot (the warp's index)
-    const int warp = threadIdx.x >> 5;
-    deep<FAM, F32, true>(c, e, k, &xs[warp]);
+__device__ __noinline__ double exact_h(Ctx<F32> c, uint32_t e, uint32_t k) {
+    return deep<FAM, F32, true>(c, e, k);
+}
+
+// FP32 path: re-evaluates every logged contender (and the holder of its
+// component) exactly in FP64 and installs the lexicographic (value, id)
+// minimum.  Runs in one warp of the team.  Returns the number of exact
+// evaluations.
+template <int FAM>
+__device__ __noinline__ uint32_t resolve_contenders(Ctx<true> c) {
+    const SketchParams &P = *c.p;
+    TeamShared *ts = c.ts;
+    const int lane = threadIdx.x & 31;
+    uint32_t evals = 0;
+    const int ncont_all = ld_volatile(&ts->cont_n);
+    if (ncont_all > kMaxCont) { if (lane == 0) ts->status = PMH_ERR_ITER_LIMIT; }
+    const int ncont = min(ncont_all, kMaxCont);
+    uint64_t *sig = (uint64_t *)c.sig;
+    for (int a = 0; a < ncont; ++a) {
+        const uint32_t k = ts->cont_k[a];
+        bool seen = false;
+        for (int b = 0; b < a; ++b) seen |= (ts->cont_k[b] == k);
+        if (seen) continue;
+        const uint64_t hk = sig[k];
+        uint32_t best_e = (uint32_t)(hk & 0xFFFFFFFFu);
+        double best_x = exact_h<FAM, true>(c, best_e, k);
+        uint64_t best_id = P.ids[c.beg + best_e];
+        evals++;
+        for (int b = a; b < ncont; ++b) {
+            if (ts->cont_k[b] != k) continue;
+            const uint32_t ce = ts->cont_e[b];
+            if (ce == best_e) continue;
+            double x = exact_h<FAM, true>(c, ce, k);
+            evals++;
+            uint64_t cid = P.ids[c.beg + ce];
+            if (x < best_x || (x == best_x && cid < best_id)) { best_x = x; best_id = cid; best_e = ce; }
+        }
+        if (lane == 0) sig[k] = (hk & 0xFFFFFFFF00000000ull) | best_e;
+        __syncwarp();
+    }
+    return evals;
+}
+
+// ------------------------------------------------------------ survivors
+// Elements whose first point passed the log-free lower bound are expanded
+// lane-sequentially with work stealing: every lane owns one survivor, computes
+// one point of it per step (value word, label word, value, label, offer), and
+// takes the next buffered survivor when its sequence ends.  Sequential
+// per-lane sums follow the uncorrelated recursion exactly as written, and the
+// lazy Fisher-Yates permutation of ProbMinHash2/4 keeps a per-lane list of its
+// writes.  At the first point the number of further points below the bound is
+// estimated:
+//   ProbMinHash3: points i >= 2 with lower bound w_inv*(i-1) <= bound, i.e.
+//     i-1 <= bound*w;
+//   ProbMinHash4: lower bound w_inv*gamma_{i-1} with
+//     gamma_j = log(m/(m-j))/lambda_1 <= bound*w, i.e. j <= m(1-e^{-lambda_1 bound w});
+//   ProbMinHash1/2: after x_1 a Poisson count of mean w*(bound - x_1)
+//     (ProbMinHash1's spacings are Exp(1)/w; ProbMinHash2's are longer).
+// Long sequences go to warp-cooperative deep mode instead; so does a
+// sequence that outgrows the lane-sequential cap (the FP32 running sum's error
+// bound holds for at most kSeqCap terms, the write list has kFyCap entries).
+constexpr int kSeqCap = 32;   // lane-sequential points (ProbMinHash1/2/4)
+constexpr int kSeqCap3 = 64;  // lane-sequential points (ProbMinHash3)
+
+template <int FAM, bool F32>
+__device__ bool process_survivors(Ctx<F32> &c, int n) {
+    const long long t_sv = clock64();
+    const SketchParams &P = *c.p;
+    const Tables &T = P.tab;
+    const uint32_t m = P.m;
+    const int lane = threadIdx.x & 31;
+    WarpShared *ws = c.ws;
+    constexpr bool kPerm = (FAM == 2 || FAM == 4);
+    constexpr int kCap = (FAM == 3) ? kSeqCap3 : kSeqCap;
+    bool has = false, won = false;
+    uint32_t e = 0, i = 0;
+    uint64_t key = 0, id = 0;
+    float winv32 = 0.0f, s32 = 0.0f;
+    double w_inv = 0.0, x64 = 0.0;
+    int fyn = 0;
+    int next = 0;
+    uint32_t npts = 0;
+    if (lane == 0) ws->dq_n = 0;
     __syncwarp();
-    double v = xs[warp];
+#pragma unroll 1
+    for (int step = 0;; ++step) {
+        // idle lanes take the next survivors
+        const unsigned idle = __ballot_sync(kFull, !has);
+        const int avail = n - next;
+        if (avail > 0 && idle) {
+            const int rank = __popc(idle & ((1u << lane) - 1u));
+            if (!has && rank < avail) {
+                const int j = next + rank;
+                e = ws->sb_e[j];
+                key = ws->sb_key[j];
+                const double w = P.weights[c.beg + e];
+                winv32 = winv_scaled(w, c.sigma);
+                if constexpr (!F32) { w_inv = __drcp_rn(w); id = P.ids[c.beg + e]; }
+                i = 1;
+                s32 = 0.0f;
+                x64 = 0.0;
+                fyn = 0;
+                has = true;
+            }
+            next += min(__popc(idle), avail);
+        }
+        if (!__any_sync(kFull, has)) break;
+        if (has) {
+            bool done = false, to_deep = false;
+            // correlated families: point i lies above its lower bound
+            if (FAM >= 3 && i >= 2) {
+                if constexpr (F32) {
+                    const float lb = (FAM == 3) ? winv32 * (float)(i - 1) : winv32 * T.gamma32[i - 1];
+                    done = lb * (1.0f - kEta) > ld_volatile(&c.ts->bound32);
+                } else {
+                    const double lb = (FAM == 3) ? lower3_64(i, w_inv) : lower4_64(T, i, w_inv);
+                    done = lb > ld_volatile(&c.ts->bound64);
+                }
+            }
+            if (!done) {
+                const uint64_t vw = value_word(key, i);
+                const uint64_t lw = label_word(key, i);
+                uint32_t k;
+                if constexpr (kPerm) {
+                    // step t = i-1 of the lazy Fisher-Yates permutation; list entry = (position << 16) | value
+                    const uint32_t t = i - 1;
+                    const uint32_t r = t + uniform_int(lw, m - t);
+                    uint32_t moved = t, lab = r;   // untouched positions hold their own index
+                    // the latest write wins: scanning backwards, keep the first match
+                    for (int j = fyn - 1; j >= 0; --j) {
+                        const uint32_t ent = c.fy[j * 32 + lane];
+                        if ((ent >> 16) == t) { moved = ent & 0xFFFFu; break; }
+                    }
+                    for (int j = fyn - 1; j >= 0; --j) {
+                        const uint32_t ent = c.fy[j * 32 + lane];
+                        if ((ent >> 16) == r) { lab = ent & 0xFFFFu; break; }
+                    }
+                    if (fyn < kFyCap) c.fy[fyn * 32 + lane] = (r << 16) | moved;
+                    fyn++;
+                    k = lab;
+                } else {
+                    k = uniform_int(lw, m);
+                }
+                bool beyond;
+                float y = 0.0f;
+                if constexpr (F32) {
+                    float x32;
+                    if (FAM == 1) { s32 = __fadd_rn(s32, exp1_32(vw)); x32 = __fmul_rn(winv32, s32); }
+                    else if (FAM == 2) { s32 = __fadd_rn(s32, __fmul_rn(T.beta32[i], exp1_32(vw))); x32 = __fmul_rn(winv32, s32); }
+                    else if (FAM == 3) x32 = __fmul_rn(winv32, __fadd_rn((float)(i - 1), texp_32(vw, T.c3_32, T.inv3_32)));
+                    else {
+                        float sv;
+                        if (i < m) sv = __fadd_rn(T.gamma32[i - 1], __fmul_rn(T.dgamma32[i], texp_32(vw, T.c4_32[i], T.inv4_32[i])));
+                        else sv = __fadd_rn(T.gamma32[m - 1], __fmul_rn(T.delta32, exp1_32(vw)));
+                        x32 = __fmul_rn(winv32, sv);
+                    }
+                    const float b32 = ld_volatile(&c.ts->bound32);
+                    beyond = x32 * (1.0f - kEta) > b32;
+                    if (!beyond) won |= Offer<true>::run(c, k, x32, e);
+                    if (i == 1) {
+                        y = __fdiv_rn(b32, winv32) * (1.0f + 4.0f * kEta);
+                        if (FAM == 1 || FAM == 2) y -= s32 * (1.0f - kEta);
+                    }
+                } else {
+                    if (FAM == 1) x64 = __dadd_rn(x64, term1_64(vw, w_inv));
+                    else if (FAM == 2) x64 = __dadd_rn(x64, term2_64(T, vw, i, w_inv));
+                    else if (FAM == 3) x64 = point3_64(T, vw, i, w_inv);
+                    else x64 = point4_64(T, vw, i, w_inv);
+                    const double b64 = ld_volatile(&c.ts->bound64);
+                    beyond = x64 > b64;
+                    if (!beyond) won |= Offer<false>::run(c, k, x64, id);
+                    if (i == 1)
+                        y = (FAM == 1 || FAM == 2) ? (float)((b64 - x64) * (1.0 / w_inv))
+                                                   : __fdiv_rn(ld_volatile(&c.ts->bound32), winv32);
+                    if (i == 1) y *= (1.0f + 4.0f * kEta);
+                }
+                npts++;
+                if ((FAM == 1 || FAM == 2) && beyond) done = true;                 // uncorrelated: points increase
+                if (kPerm && i >= m) done = true;                                  // the sequence has m points
+                if (!done && i == 1) {
+                    // estimated number of further points below the bound
+                    int est;
+                    if (!(y < 1e9f)) est = 1 << 30;
+                    else if (FAM == 1 || FAM == 2) { const float mu = fmaxf(y, 0.0f); est = (int)(mu + 3.0f * sqrtf(mu) + 2.0f); }
+                    else if (FAM == 3) est = (int)y;
+                    else est = (int)((float)m * (1.0f - __expf(-T.lambda1_32 * y)) * 1.001f) + 1;
+                    if (est >= kCap) to_deep = true;
+                }
+                if (!done && !to_deep && (int)i >= kCap) to_deep = true;            // outgrew the lane-sequential cap
+                i++;
+            }
+            if (to_deep) {
+                const int at = atomicAdd(&ws->dq_n, 1);   // at most one entry per survivor (n <= kSurvCap)
+                if (at < kSurvCap) ws->dq[at] = e;
+                done = true;
+            }
+            if (done) has = false;
+        }
+    }
+    if (npts) atomicAdd(&ws->cnt[F32 ? PMH_CNT_POINTS32 : PMH_CNT_POINTS64], (unsigned long long)npts);
     __syncwarp();
-    return v;
+    // ---- deep mode for the long sequences
+    const int total_deep = min(ws->dq_n, kSurvCap);
+    if (total_deep) {
+        const long long td = clock64();
+        for (int j = 0; j < total_deep; ++j) deep<FAM, F32, false>(c, ws->dq[j], 0);
+        count(c, PMH_CNT_CYC_DEEP, (unsigned long long)(clock64() - td));
+    }
+    count(c, PMH_CNT_CYC_SURV, (unsigned long long)(clock64() - t_sv));
+    return __any_sync(kFull, won);
 }
 
 // ------------------------------------------------------------ team helpers
 template <bool CTA_TEAM>
 __device__ __forceinline__ void team_sync() {
     if (CTA_TEAM) __syncthreads(); else __syncwarp();
-}
-
-// Combines two scaled sums s1*2^e1 + s2*2^e2.
-__device__ __forceinline__ void combine_sum(float &s, int &e, float s2, int e2) {
-    if (s2 == 0.0f) return;
-    if (s == 0.0f) { s = s2; e = e2; return; }
-    if (e2 > e) { s = ldexpf(s, max(e - e2, -200)); e = e2; }
-    else s2 = ldexpf(s2, max(e2 - e, -200));
-    s += s2;
 }
 
 // ------------------------------------------------------------ one item
@@ -575,162 +691,140 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
     const int tt = tw * 32 + lane;
     const int team_threads = team_warps * 32;
     TeamShared *ts = c.ts;
+    WarpShared *ws = c.ws;
     const bool leader = (tt == 0);
     const int64_t out_row = (int64_t)item_v * P.num_sets + set;
+    long long t_ph = clock64();
+    count(c, PMH_CNT_ITEMS, tw == 0);
 
-    // ---- init
+    // ---- init: empty signature; T = m (ln m + c) / sum(w) = t_s * 2^-sigma, t_s in [1, 2)
     for (uint32_t k = tt; k < m; k += team_threads) {
         if constexpr (F32) ((uint64_t *)c.sig)[k] = kEmptyKey;
         else { ((Rec64 *)c.sig)[k].q = __longlong_as_double(0x7FF0000000000000ll); ((Rec64 *)c.sig)[k].id = 0; }
     }
-    // ---- pass 0: validate weights, scaled weight sum
-    float s = 0.0f;
-    int se = -100000, bad = 0, npos = 0;
-    for (uint32_t e = tt; e < c.n; e += team_threads) {
-        double w = P.weights[c.beg + e];
-        uint64_t b = (uint64_t)__double_as_longlong(w);
-        uint32_t ex = (uint32_t)(b >> 52) & 0x7FF;
-        uint64_t mant = b & 0xFFFFFFFFFFFFFull;
-        bool neg = (b >> 63) != 0;
-        if (ex == 0x7FF) { bad = 1; continue; }
-        if (neg) { if (ex != 0 || mant != 0) bad = 1; continue; }
-        if (ex == 0 && mant == 0) continue;
-        if (ex == 0) {
-            double r = __drcp_rn(w);
-            if (isinf(r)) { bad = 1; continue; }
-        }
-        npos++;
-        int ew = (ex == 0) ? -1075 : (int)ex - 1023;
-        float mf = __uint_as_float(0x3F800000u | (uint32_t)(mant >> 29));   // [1,2)
-        combine_sum(s, se, mf, ew);
-    }
-    for (int o = 16; o; o >>= 1) {
-        float s2 = __shfl_xor_sync(kFull, s, o);
-        int e2 = __shfl_xor_sync(kFull, se, o);
-        combine_sum(s, se, s2, e2);
-        bad |= __shfl_xor_sync(kFull, bad, o);
-        npos += __shfl_xor_sync(kFull, npos, o);
-    }
-    if (lane == 0) { ts->red_s[tw] = s; ts->red_e[tw] = se; ts->red_i[tw] = bad | (npos << 1); }
-    team_sync<CTA_TEAM>();
+    const SetStat st0 = P.stats[set];
     if (leader) {
-        float S = 0.0f;
-        int E = -100000, B = 0, NP = 0;
-        for (int w = 0; w < team_warps; ++w) {
-            combine_sum(S, E, ts->red_s[w], ts->red_e[w]);
-            B |= ts->red_i[w] & 1;
-            NP += ts->red_i[w] >> 1;
-        }
-        ts->status = B ? PMH_ERR_BAD_WEIGHT : PMH_OK;
-        ts->n_pos = NP;
+        ts->status = st0.bad ? PMH_ERR_BAD_WEIGHT : PMH_OK;
         ts->unfilled = (int)m;
         ts->cont_n = 0;
-        // T = m (ln m + c) / sum(w) = t_s * 2^-sigma with t_s in [1, 2)
         int sigma = 0;
-        float t_s = 1.0f;
-        if (NP > 0) {
-            float num = (float)m * P.t_factor / S;
-            int en;
-            float fr = frexpf(num, &en);   // num = fr * 2^en, fr in [0.5, 1)
-            t_s = 2.0f * fr;
-            sigma = E - (en - 1);
+        float t_s = __int_as_float(0x7F800000);   // no usable estimate: a single unbounded round
+        const double T = (double)m * (double)P.t_factor / st0.wsum;
+        if (st0.npos > 0 && T > 0.0 && T < 1e300) {
+            int ex;
+            const double fr = frexp(T, &ex);      // T = fr * 2^ex, fr in [0.5, 1)
+            t_s = (float)(2.0 * fr);
+            sigma = -(ex - 1);
         }
         ts->sigma = sigma;
         ts->t_s = t_s;
     }
     team_sync<CTA_TEAM>();
-    const int st0 = ts->status;
-    const int np = ts->n_pos;
     c.sigma = ts->sigma;
-    if (st0 != PMH_OK || np == 0) {
+    if (st0.bad || st0.npos == 0) {
         // bad weights or empty set: zero ids, +inf q
         for (uint32_t k = tt; k < m; k += team_threads) {
             P.out_ids[out_row * m + k] = 0;
             if (P.out_q) P.out_q[out_row * m + k] = __longlong_as_double(0x7FF0000000000000ll);
         }
-        if (leader && P.status) P.status[out_row] = st0;
+        if (leader && P.status) P.status[out_row] = st0.bad ? PMH_ERR_BAD_WEIGHT : PMH_OK;
         return;
     }
+    count(c, PMH_CNT_CYC_PASS0, (unsigned long long)(clock64() - t_ph));
+    t_ph = clock64();
 
     // ---- rounds
-    WarpShared *ws = c.ws;
+    const float te_lo = (FAM >= 3) ? P.tab.te_lo : 1.0f;
     for (int round = 0; round <= P.rounds; ++round) {
         if (leader) {
-            if (round < P.rounds) {
-                float b = ldexpf(ts->t_s, 2 * round);
-                ts->bound32 = b;
+            if (round < P.rounds && !isinf(ts->t_s)) {
+                ts->bound32 = ldexpf(ts->t_s, 2 * round);
                 ts->bound64 = ldexp((double)ts->t_s, 2 * round - c.sigma);
             } else {
                 ts->bound32 = __int_as_float(0x7F800000);
                 ts->bound64 = __longlong_as_double(0x7FF0000000000000ll);
             }
-            if (round > 0) c.cnt.c[PMH_CNT_ROUNDS] += 1;
         }
+        if (round > 0) count(c, PMH_CNT_ROUNDS, leader);
+        if (lane == 0) ws->sb_n = 0;
         team_sync<CTA_TEAM>();
         bool refreshed = false;
-        for (uint32_t base = tw * 32; base < c.n; base += team_warps * 32) {
-            const uint32_t e = base + lane;
-            int r = 0;
-            if (e < c.n) {
-                const double w = P.weights[c.beg + e];
-                if (w > 0.0) {
-                    const uint64_t id = P.ids[c.beg + e];
-                    r = stage_a<FAM, F32>(c, e, id, w);
+        for (uint32_t base = tw * 64; base < c.n; base += team_warps * 64) {
+            // filter two elements per lane: the log-free lower bound of the first point
+            bool surv[2];
+            uint64_t key[2];
+            uint32_t ev[2];
+            bool valid[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t e = base + 32 * h + lane;
+                ev[h] = e;
+                surv[h] = false;
+                key[h] = 0;
+                valid[h] = false;
+                if (e < c.n) {
+                    const double w = P.weights[c.beg + e];
+                    if (weight_positive(w)) {
+                        valid[h] = true;
+                        key[h] = mix64(P.ids[c.beg + e] ^ P.mixed_seed);
+                        const float xlo = winv_scaled(w, c.sigma) * unif_lo(value_word(key[h], 1)) * te_lo;
+                        surv[h] = !(xlo * (1.0f - 8.0f * 0x1p-24f) > ld_volatile(&ts->bound32));
+                    }
                 }
             }
-            const bool need = (r & kNeedDeep) != 0;
-            const bool any_win = __any_sync(kFull, (r & kWon) != 0);
-            // warp queue of long sequences
-            unsigned msk = __ballot_sync(kFull, need);
-            if (msk) {
-                if (need) ws->dq[__popc(msk & ((1u << lane) - 1u))] = e;
-                __syncwarp();
-                const int cnt = __popc(msk);
-                for (int j = 0; j < cnt; ++j) {
-                    const uint32_t de = ws->dq[j];
-                    deep<FAM, F32, false>(c, de, 0, nullptr);
+            int n = ws->sb_n;
+            unsigned nvalid = 0, nsurv = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const unsigned msk = __ballot_sync(kFull, surv[h]);
+                if (surv[h]) {
+                    const int pos = n + __popc(msk & ((1u << lane) - 1u));
+                    if (pos < kSurvCap) {   // always true: n <= kSurvBatch - 1 before the two appends of <= 32
+                        ws->sb_e[pos] = ev[h];
+                        ws->sb_key[pos] = key[h];
+                    } else {
+                        ts->status = PMH_ERR_ITER_LIMIT;
+                    }
                 }
-                __syncwarp();
+                n = min(n + __popc(msk), kSurvCap);
+                nsurv += __popc(msk);
+                nvalid += popc_ballot(valid[h]);
             }
+            count(c, PMH_CNT_ELEMENTS, nvalid);
+            count(c, PMH_CNT_PREFILTERED, nvalid - nsurv);
+            __syncwarp();
+            bool any_win = false;
+            if (n >= kSurvBatch) {
+                any_win = process_survivors<FAM, F32>(c, n);
+                n = 0;
+            }
+            if (lane == 0) ws->sb_n = n;
+            __syncwarp();
             // refresh q_max once everything is filled
-            int uf = __shfl_sync(kFull, lane == 0 ? ld_volatile(&ts->unfilled) : 1, 0);
-            if (uf == 0 && (!refreshed || msk || any_win)) {
+            const int uf = __shfl_sync(kFull, lane == 0 ? ld_volatile(&ts->unfilled) : 1, 0);
+            if (uf == 0 && (!refreshed || any_win)) {
                 refresh_bound<F32>(c);
                 refreshed = true;
             }
         }
+        {
+            const int rest = ws->sb_n;
+            __syncwarp();
+            if (rest > 0) process_survivors<FAM, F32>(c, rest);
+        }
         team_sync<CTA_TEAM>();
+        count(c, PMH_CNT_CYC_FIRST, (unsigned long long)(clock64() - t_ph));
+        t_ph = clock64();
         if (ld_volatile(&ts->unfilled) == 0 || ld_volatile(&ts->status) != PMH_OK) break;
         team_sync<CTA_TEAM>();
     }
     team_sync<CTA_TEAM>();
 
     // ---- FP32: resolve contenders exactly
-    if constexpr (F32) if (tw == 0) {
-        Ctx<F32> &cc = c;
-        const int ncont_all = ld_volatile(&ts->cont_n);
-        if (ncont_all > kMaxCont) { if (lane == 0) ts->status = PMH_ERR_ITER_LIMIT; }
-        const int ncont = min(ncont_all, kMaxCont);
-        uint64_t *sig = (uint64_t *)cc.sig;
-        for (int a = 0; a < ncont; ++a) {
-            const uint32_t k = ts->cont_k[a];
-            bool seen = false;
-            for (int b = 0; b < a; ++b) seen |= (ts->cont_k[b] == k);
-            if (seen) continue;
-            const uint64_t hk = sig[k];
-            uint32_t best_e = (uint32_t)(hk & 0xFFFFFFFFu);
-            double best_x = exact_h<FAM, F32>(cc, best_e, k);
-            uint64_t best_id = P.ids[c.beg + best_e];
-            for (int b = a; b < ncont; ++b) {
-                if (ts->cont_k[b] != k) continue;
-                const uint32_t ce = ts->cont_e[b];
-                if (ce == best_e) continue;
-                double x = exact_h<FAM, F32>(cc, ce, k);
-                uint64_t cid = P.ids[c.beg + ce];
-                if (x < best_x || (x == best_x && cid < best_id)) { best_x = x; best_id = cid; best_e = ce; }
-            }
-            if (lane == 0) sig[k] = (hk & 0xFFFFFFFF00000000ull) | best_e;
-            __syncwarp();
+    if constexpr (F32) {
+        if (tw == 0 && ld_volatile(&ts->cont_n) > 0) {
+            const uint32_t ev = resolve_contenders<FAM>(c);
+            count(c, PMH_CNT_RESOLVED, ev);
         }
     }
     team_sync<CTA_TEAM>();
@@ -762,25 +856,29 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
         }
     }
     if (leader && P.status) P.status[out_row] = st;
+    count(c, PMH_CNT_CYC_FINISH, (unsigned long long)(clock64() - t_ph));
 }
 
 // ------------------------------------------------------------ kernel
-template <bool F32, int NW, bool CTA_TEAM>
-__global__ void __launch_bounds__(NW * 32) sketch_kernel(SketchParams p) {
+template <bool F32, int NW, bool CTA_TEAM, int FAM>
+__global__ void __launch_bounds__(NW * 32, CTA_TEAM ? 2 : 5) sketch_kernel(SketchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr bool kPerm = (FAM == 2 || FAM == 4);
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int teams = CTA_TEAM ? 1 : NW;
     const int team = CTA_TEAM ? 0 : warp;
-    SmemLayout L(teams, NW, p.m, F32, p.has_perm != 0);
+    SmemLayout L(teams, NW, p.m, F32, kPerm);
     TeamShared *ts = (TeamShared *)(smem + L.team_off + (size_t)team * align16(sizeof(TeamShared)));
     Ctx<F32> c;
     c.p = &p;
     c.ts = ts;
     c.sig = smem + L.sig_off + (size_t)team * p.m * (F32 ? 8 : 16);
     c.ws = (WarpShared *)(smem + L.warp_off + (size_t)warp * align16(sizeof(WarpShared)));
-    c.perm = p.has_perm ? (uint16_t *)(smem + L.perm_off + (size_t)warp * p.m * 2) : nullptr;
-    for (int j = 0; j < PMH_NUM_COUNTERS; ++j) c.cnt.c[j] = 0;
+    c.perm = kPerm ? (uint16_t *)(smem + L.perm_off + (size_t)warp * perm_bytes(p.m)) : nullptr;
+    c.fy = kPerm ? (uint32_t *)(smem + L.perm_off + (size_t)warp * perm_bytes(p.m) + align16((size_t)p.m * 2)) : nullptr;
+    if (lane < PMH_NUM_COUNTERS) c.ws->cnt[lane] = 0;
+    __syncwarp();
     const bool team_leader = CTA_TEAM ? (threadIdx.x == 0) : (lane == 0);
     for (;;) {
         if (team_leader) ts->item_idx = (int)atomicAdd(p.head, 1u);
@@ -806,22 +904,11 @@ __global__ void __launch_bounds__(NW * 32) sketch_kernel(SketchParams p) {
         }
         c.beg = b;
         c.n = (uint32_t)(e - b);
-        const int fam = family_of(p.variants[v]);
-        switch (fam) {
-            case 1: process_item<1, F32, CTA_TEAM>(c, v, set); break;
-            case 2: process_item<2, F32, CTA_TEAM>(c, v, set); break;
-            case 3: process_item<3, F32, CTA_TEAM>(c, v, set); break;
-            default: process_item<4, F32, CTA_TEAM>(c, v, set); break;
-        }
+        process_item<FAM, F32, CTA_TEAM>(c, v, set);
         team_sync<CTA_TEAM>();
     }
-    if (p.counters) {
-        for (int j = 0; j < PMH_NUM_COUNTERS; ++j) {
-            unsigned long long v = c.cnt.c[j];
-            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-            if (lane == 0 && v) atomicAdd(&p.counters[j], v);
-        }
-    }
+    __syncwarp();
+    if (p.counters && lane < PMH_NUM_COUNTERS && c.ws->cnt[lane]) atomicAdd(&p.counters[lane], c.ws->cnt[lane]);
 }
 
 }  // namespace pmh

@@ -20,9 +20,10 @@ OK, ERR_INVALID_ARG, ERR_BAD_WEIGHT, ERR_ITER_LIMIT, ERR_CUDA, ERR_NO_MEMORY, ER
 V1, V1A, V2, V3, V3A, V4 = range(6)
 VARIANTS = {"1": V1, "1a": V1A, "2": V2, "3": V3, "3a": V3A, "4": V4}
 FP64, FP32_RECHECK = 0, 1
-COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "rounds", "deep", "prefiltered")
-EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_estimate_allpairs",
-           "pmh_estimate_pairs", "pmh_merge")
+COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "rounds", "deep", "prefiltered",
+            "cyc_pass0", "cyc_first", "cyc_deep", "cyc_refresh", "cyc_finish", "items", "cyc_surv", "reserved15")
+EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_set_profiling",
+           "pmh_last_kernel_ms", "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge")
 
 _lib = None
 _lock = threading.Lock()
@@ -52,6 +53,10 @@ def load(path: str = LIB_PATH):
             lib.pmh_sketch_batch.restype = i32
             lib.pmh_sketch_batch.argtypes = [vp, vp, vp, vp, i64, u32, ctypes.POINTER(i32), i32, i32, u64, vp, vp, vp,
                                              vp, vp]
+            lib.pmh_set_profiling.restype = i32
+            lib.pmh_set_profiling.argtypes = [vp, i32]
+            lib.pmh_last_kernel_ms.restype = i32
+            lib.pmh_last_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
             lib.pmh_estimate_allpairs.restype = i32
             lib.pmh_estimate_allpairs.argtypes = [vp, vp, i64, u32, i32, vp, vp]
             lib.pmh_estimate_pairs.restype = i32
@@ -141,6 +146,16 @@ class Handle:
                                      _ptr(status), _ptr(counters), _stream(stream))
         self._raise(rc)
         return out_ids, out_q, status
+
+    # -- pmh_set_profiling / pmh_last_kernel_ms ------------------------------
+    def set_profiling(self, enable: bool = True):
+        self._raise(load().pmh_set_profiling(self._h, 1 if enable else 0))
+
+    def last_kernel_ms(self):
+        """(queue build ms, sketch kernel ms) of the last profiled pmh_sketch_batch call."""
+        a, b = ctypes.c_float(), ctypes.c_float()
+        self._raise(load().pmh_last_kernel_ms(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     # -- pmh_estimate_allpairs ---------------------------------------------
     def estimate_allpairs(self, sigs, upper_only: bool = False, counts=None, stream=None):
