@@ -139,6 +139,34 @@ pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const double *wei
                             int32_t *set_status, uint64_t *counters, void *stream);
 
 /*
+ * pmh_sketch_batch_noalloc -- pmh_sketch_batch for callers that cannot
+ * allocate GPU memory: code that runs under another runtime's fixed memory
+ * budget, inside a framework that forbids cudaMalloc on its hot path, or
+ * where an allocation could stall or fail at the worst moment.  The paper has
+ * no counterpart; this is an interface of this library only.
+ *
+ * Same arguments and results as pmh_sketch_batch (without a handle: it runs
+ * on the current device), computed by the same kernels.  Its scratch memory
+ * (constant tables, work queue, per-set statistics) is one fixed array of
+ * about 3.5 MiB that every GPU holds for as long as the library is loaded;
+ * the call itself allocates and frees no device memory and builds no CUDA
+ * graph.  Limits: num_sets <= PMH_NOALLOC_MAX_SETS and
+ * num_sets * num_variants <= PMH_NOALLOC_MAX_ITEMS; larger batches return
+ * PMH_ERR_UNSUPPORTED (message in pmh_last_error(NULL)).
+ * The first call on a device resolves the array's device address; make that
+ * first call before any stream capture.  Every call on a device shares the
+ * array, which keeps the last call's contents: calls whose work overlaps on
+ * the GPU (other streams, other host threads) race and must be ordered by the
+ * caller.
+ */
+#define PMH_NOALLOC_MAX_SETS 65536
+#define PMH_NOALLOC_MAX_ITEMS 262144
+pmh_status pmh_sketch_batch_noalloc(const uint64_t *ids, const double *weights, const int64_t *offsets,
+                                    int64_t num_sets, uint32_t m, const int32_t *variants, int32_t num_variants,
+                                    int32_t precision, uint64_t seed, uint64_t *out_ids, double *out_q,
+                                    int32_t *set_status, uint64_t *counters, void *stream);
+
+/*
  * Profiling.  pmh_set_profiling(h, 1) makes every later pmh_sketch_batch on
  * `h` record CUDA events on its stream before the work-queue build, between
  * the queue build and the persistent sketch kernel, and after the kernel.

@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "launch.h"
+#include "batch_common.cuh"
 
 using namespace pmh;
 
@@ -60,6 +60,8 @@ struct pmh_handle_s {
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
 };
 
+void pmh::set_thread_error(const char *msg) { g_create_error = msg; }
+
 static pmh_status fail(pmh_handle h, pmh_status code, const char *fmt, ...) {
     char buf[512];
     va_list ap;
@@ -77,159 +79,20 @@ static pmh_status fail(pmh_handle h, pmh_status code, const char *fmt, ...) {
     } while (0)
 
 // ------------------------------------------------------------------ tables
-// Per-m constants of Sec. ProbMinHash2/3/4 in FP64 (host libm), plus FP32
-// copies for the filter.
+// Per-m constant tables, built on the host and uploaded once per (handle, m).
 static pmh_status get_tables(pmh_handle h, uint32_t m, Tables *out) {
     auto it = h->tables.find(m);
     if (it != h->tables.end()) { *out = it->second.t; return PMH_OK; }
-    const size_t n = (size_t)m + 1;
-    std::vector<double> beta(n, 0.0), gamma(n, 0.0), dgamma(n, 0.0), c4(n, 0.0), inv4(n, 0.0);
-    for (uint32_t i = 1; i <= m; i++) beta[i] = (double)m / (double)(m - i + 1);
-    double lambda1 = 0.0, c3 = 0.0, inv3 = 0.0, delta = 0.0;
-    if (m >= 2) {
-        lambda1 = std::log1p(1.0 / (double)(m - 1));
-        c3 = std::expm1(-lambda1);
-        inv3 = 1.0 / lambda1;
-        delta = 1.0 / lambda1;
-        for (uint32_t i = 1; i < m; i++) {
-            const double li = std::log1p(1.0 / (double)(m - i));
-            c4[i] = std::expm1(-li);
-            inv4[i] = 1.0 / li;
-            gamma[i] = std::log1p((double)i / (double)(m - i)) / lambda1;
-            dgamma[i] = gamma[i] - gamma[i - 1];
-        }
-    }
-    std::vector<float> f[5];
-    const std::vector<double> *src[5] = {&beta, &gamma, &dgamma, &c4, &inv4};
-    for (int a = 0; a < 5; a++) {
-        f[a].resize(n);
-        for (size_t i = 0; i < n; i++) f[a][i] = (float)(*src[a])[i];
-    }
-    const size_t bytes = 5 * n * sizeof(double) + 5 * n * sizeof(float);
+    const size_t bytes = table_bytes(m);
     TableBuf tb;
     CUDA_TRY(h, cudaMalloc(&tb.dev, bytes));
-    char *d = (char *)tb.dev;
-    std::vector<char> host(bytes);
-    for (int a = 0; a < 5; a++) std::memcpy(host.data() + a * n * sizeof(double), src[a]->data(), n * sizeof(double));
-    for (int a = 0; a < 5; a++)
-        std::memcpy(host.data() + 5 * n * sizeof(double) + a * n * sizeof(float), f[a].data(), n * sizeof(float));
+    std::vector<unsigned char> host(bytes);
+    build_tables(m, host.data(), tb.dev, &tb.t);
     cudaError_t e = cudaMemcpy(tb.dev, host.data(), bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(tb.dev); return fail(h, PMH_ERR_CUDA, "table upload: %s", cudaGetErrorString(e)); }
-    Tables &t = tb.t;
-    t.m = m;
-    t.beta = (const double *)(d);
-    t.gamma = (const double *)(d + 1 * n * sizeof(double));
-    t.dgamma = (const double *)(d + 2 * n * sizeof(double));
-    t.c4 = (const double *)(d + 3 * n * sizeof(double));
-    t.inv4 = (const double *)(d + 4 * n * sizeof(double));
-    const char *fb = d + 5 * n * sizeof(double);
-    t.beta32 = (const float *)(fb);
-    t.gamma32 = (const float *)(fb + 1 * n * sizeof(float));
-    t.dgamma32 = (const float *)(fb + 2 * n * sizeof(float));
-    t.c4_32 = (const float *)(fb + 3 * n * sizeof(float));
-    t.inv4_32 = (const float *)(fb + 4 * n * sizeof(float));
-    t.c3 = c3;
-    t.inv3 = inv3;
-    t.delta = delta;
-    t.c3_32 = (float)c3;
-    t.inv3_32 = (float)inv3;
-    t.delta32 = (float)delta;
-    // Exp(lambda_1;0,1) >= U * (1-e^-lambda_1)/lambda_1 (since -log1p(-a) >= a); round the factor down
-    double lo = (m >= 2) ? -c3 / lambda1 : 1.0;
-    float lo32 = (float)lo;
-    if ((double)lo32 > lo) lo32 = std::nextafterf(lo32, 0.0f);
-    t.te_lo = lo32;
-    t.lambda1_32 = (float)lambda1;
     h->tables[m] = tb;
-    *out = t;
+    *out = tb.t;
     return PMH_OK;
-}
-
-// ------------------------------------------------------------------ queue
-// Items (variant, set) in family-major order (ProbMinHash1/1a, 2, 3/3a, 4),
-// each family sorted by decreasing floor(log2(n+1)) (largest sets first).
-// Meta layout: [0, 256) histogram per (family, bucket), [256, 512) running
-// starts, [512, 516) per-family head counters of the persistent kernels.
-constexpr int kQHist = 0, kQStart = 256, kQHead = 512, kQMetaWords = 520;
-
-struct FamOfVariant {
-    int f[8];
-};
-
-__device__ __forceinline__ int queue_bucket(const int64_t *off, int64_t s) {
-    int64_t n = off[s + 1] - off[s];
-    if (n < 0) n = 0;
-    return 63 - __clzll((long long)(n + 1));
-}
-
-__global__ void queue_count(const int64_t *off, int64_t num_sets, int32_t nv, FamOfVariant fv, unsigned int *meta) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < num_sets * nv; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = i % num_sets;
-        const int v = (int)(i / num_sets);
-        atomicAdd(&meta[kQHist + (fv.f[v] - 1) * 64 + queue_bucket(off, s)], 1u);
-    }
-}
-__global__ void queue_starts(unsigned int *meta) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        unsigned int acc = 0;
-        for (int f = 0; f < 4; ++f)
-            for (int b = 63; b >= 0; --b) { meta[kQStart + f * 64 + b] = acc; acc += meta[kQHist + f * 64 + b]; }
-        for (int f = 0; f < 4; ++f) meta[kQHead + f] = 0;
-    }
-}
-__global__ void queue_scatter(const int64_t *off, int64_t num_sets, int32_t nv, FamOfVariant fv, unsigned int *meta,
-                              uint64_t *queue) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < num_sets * nv; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = i % num_sets;
-        const int64_t v = i / num_sets;
-        const unsigned int pos = atomicAdd(&meta[kQStart + (fv.f[v] - 1) * 64 + queue_bucket(off, s)], 1u);
-        queue[pos] = ((uint64_t)v << 40) | (uint64_t)s;
-    }
-}
-
-// Per-set statistics, computed once per set for all variants: the weight sum
-// (FP64; it only sets the threshold T), the number of positive weights, and a
-// bad-weight flag (negative, NaN, +-inf, or a subnormal whose reciprocal
-// overflows).  One block per set, grid-stride over sets.
-__global__ void __launch_bounds__(256) set_stats_kernel(const int64_t *off, const double *w, int64_t num_sets,
-                                                        SetStat *out) {
-    __shared__ double ssum[8];
-    __shared__ int snp[8], sbad[8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t s = blockIdx.x; s < num_sets; s += gridDim.x) {
-        const int64_t b = off[s], e = off[s + 1];
-        double sum = 0.0;
-        int np = 0, bad = 0;
-        for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-            const double x = w[i];
-            const uint64_t bits = (uint64_t)__double_as_longlong(x);
-            const int ex = (int)(bits >> 52) & 0x7FF;
-            const bool neg = (bits >> 63) != 0;
-            if (ex == 0x7FF || (neg && (bits << 1) != 0)) { bad = 1; continue; }
-            if (neg || (bits << 1) == 0) continue;
-            if (ex == 0 && isinf(__drcp_rn(x))) { bad = 1; continue; }
-            sum += x;
-            np++;
-        }
-        for (int o = 16; o; o >>= 1) {
-            sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-            np += __shfl_xor_sync(0xFFFFFFFFu, np, o);
-            bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, o);
-        }
-        if (lane == 0) { ssum[warp] = sum; snp[warp] = np; sbad[warp] = bad; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double S = 0.0;
-            int N = 0, B = 0;
-            for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { S += ssum[j]; N += snp[j]; B |= sbad[j]; }
-            SetStat r;
-            r.wsum = S;
-            r.npos = N;
-            r.bad = B;
-            out[s] = r;
-        }
-        __syncthreads();
-    }
 }
 
 static pmh_status ensure_queue(pmh_handle h, int64_t items) {
@@ -261,85 +124,12 @@ static pmh_status ensure_stats(pmh_handle h, int64_t num_sets) {
     return PMH_OK;
 }
 
-static uint64_t host_mix64(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-// Launch plan per family present: warp teams when at least 12 warps per SM
-// fit, else CTA teams.  Computed outside any stream capture (it sets kernel
-// attributes).
-struct Plan {
-    int nfam;
-    int fam[4];
-    int64_t qbase[4], qlen[4];
-    LaunchShape shape[4];
-    int grid[4];
-};
-
-static pmh_status plan_sketch(pmh_handle h, const SketchParams &p, int precision, Plan *out) {
-    const bool f32 = precision == PMH_FP32_RECHECK;
-    const bool perm = false;   // the permutation arrays are part of the ProbMinHash2/4 kernels' layout
-    int64_t per_fam[4] = {0, 0, 0, 0};
-    for (int v = 0; v < p.num_variants; v++) per_fam[family_of(p.variants[v]) - 1] += p.num_sets;
-    out->nfam = 0;
-    int64_t base = 0;
-    for (int f = 1; f <= 4; f++) {
-        const int64_t items = per_fam[f - 1];
-        if (items == 0) continue;
-        LaunchShape warp_s{}, cta_s{};
-        cudaError_t e = sketch_shape_any(f32, f, false, p.m, perm, &warp_s);
-        if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
-        LaunchShape shape = warp_s;
-        if (warp_s.blocks_per_sm * 4 < 12) {
-            e = sketch_shape_any(f32, f, true, p.m, perm, &cta_s);
-            if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
-            if (cta_s.blocks_per_sm > 0) shape = cta_s;
-        }
-        if (shape.blocks_per_sm <= 0) return fail(h, PMH_ERR_UNSUPPORTED, "m = %u does not fit in shared memory", p.m);
-        int grid = h->sm_count * shape.blocks_per_sm;
-        const int64_t teams_needed = shape.cta_team ? items : (items + 3) / 4;
-        if (teams_needed < grid) grid = (int)std::max<int64_t>(1, teams_needed);
-        const int j = out->nfam++;
-        out->fam[j] = f;
-        out->qbase[j] = base;
-        out->qlen[j] = items;
-        out->shape[j] = shape;
-        out->grid[j] = grid;
-        base += items;
-    }
-    return PMH_OK;
-}
-
-// Enqueues the whole batch (queue build + one persistent kernel per family) on `st`.
-static pmh_status enqueue_sketch(pmh_handle h, const SketchParams &p0, const Plan &plan, int precision,
+// Enqueues the whole batch on `st` with the handle's workspace.
+static pmh_status enqueue_sketch(pmh_handle h, const SketchParams &p, const Plan &plan, int precision,
                                  cudaStream_t st) {
-    SketchParams p = p0;
-    const int64_t items = p.num_sets * p.num_variants;
-    FamOfVariant fv{};
-    for (int v = 0; v < p.num_variants; v++) fv.f[v] = family_of(p.variants[v]);
-    const int qb = 256;
-    int qg = (int)std::min<int64_t>((items + qb - 1) / qb, (int64_t)h->sm_count * 8);
-    if (qg < 1) qg = 1;
-    if (h->profiling) CUDA_TRY(h, cudaEventRecord(h->ev[0], st));
-    CUDA_TRY(h, cudaMemsetAsync(h->qmeta, 0, kQMetaWords * sizeof(unsigned int), st));
-    queue_count<<<qg, qb, 0, st>>>(p.offsets, p.num_sets, p.num_variants, fv, h->qmeta);
-    queue_starts<<<1, 32, 0, st>>>(h->qmeta);
-    queue_scatter<<<qg, qb, 0, st>>>(p.offsets, p.num_sets, p.num_variants, fv, h->qmeta, h->queue);
-    const int sg = (int)std::min<int64_t>(p.num_sets, (int64_t)h->sm_count * 8);
-    set_stats_kernel<<<sg, 256, 0, st>>>(p.offsets, p.weights, p.num_sets, h->stats);
-    CUDA_TRY(h, cudaGetLastError());
-    p.stats = h->stats;
-    if (h->profiling) CUDA_TRY(h, cudaEventRecord(h->ev[1], st));
-    for (int j = 0; j < plan.nfam; j++) {
-        p.queue = h->queue + plan.qbase[j];
-        p.queue_len = plan.qlen[j];
-        p.head = h->qmeta + kQHead + (plan.fam[j] - 1);
-        cudaError_t e = sketch_launch_any(precision == PMH_FP32_RECHECK, plan.fam[j], plan.shape[j], plan.grid[j], p, st);
-        if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "sketch launch: %s", cudaGetErrorString(e));
-    }
-    if (h->profiling) CUDA_TRY(h, cudaEventRecord(h->ev[2], st));
+    cudaError_t e = enqueue_batch(p, plan, precision, h->sm_count, h->queue, h->qmeta, h->stats, st,
+                                  h->profiling ? h->ev : nullptr);
+    if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "sketch launch: %s", cudaGetErrorString(e));
     return PMH_OK;
 }
 
@@ -438,28 +228,16 @@ extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const 
     rc = ensure_stats(h, num_sets);
     if (rc) return rc;
 
-    SketchParams p{};
-    p.ids = ids;
-    p.weights = weights;
-    p.offsets = offsets;
-    p.num_sets = num_sets;
-    p.m = m;
-    p.mixed_seed = host_mix64(seed);
-    for (int v = 0; v < num_variants; v++) p.variants[v] = variants[v];
-    p.num_variants = num_variants;
+    SketchParams p;
+    fill_params(&p, ids, weights, offsets, num_sets, m, variants, num_variants, seed, out_ids, out_q, set_status, counters,
+                h->t_c, h->rounds);
     p.tab = tab;
-    p.out_ids = out_ids;
-    p.out_q = out_q;
-    p.status = set_status;
-    p.counters = (unsigned long long *)counters;
-    p.t_factor = (float)(std::log((double)m) + h->t_c);
-    p.rounds = h->rounds;
-    p.cap_points = (uint32_t)(64.0 * m * std::log((double)m + 1.0)) + 4096;
     (void)has_perm;
-
     Plan plan;
-    rc = plan_sketch(h, p, precision, &plan);
-    if (rc) return rc;
+    bool fits = true;
+    cudaError_t pe = plan_batch(h->sm_count, precision, m, variants, num_variants, num_sets, &plan, &fits);
+    if (pe != cudaSuccess) return fail(h, PMH_ERR_CUDA, "occupancy: %s", cudaGetErrorString(pe));
+    if (!fits) return fail(h, PMH_ERR_UNSUPPORTED, "m = %u does not fit in shared memory", m);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (st) CUDA_TRY(h, cudaStreamIsCapturing(st, &cs));
     if (!h->use_graph || cs != cudaStreamCaptureStatusNone || !st) {

@@ -1,0 +1,269 @@
+// Pieces of pmh_sketch_batch shared by the allocating entry point (api.cu)
+// and the allocation-free one (noalloc.cu): per-m constant tables, the device
+// work queue, per-set statistics, the launch plan and the launch sequence.
+// Kernels here are static: each translation unit that includes the header
+// owns its copy.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "launch.h"
+
+namespace pmh {
+
+// ------------------------------------------------------------------ tables
+// Per-m constants of Sec. ProbMinHash2/3/4 in FP64 (host libm), plus FP32
+// copies for the filter: five FP64 arrays then five FP32 arrays of m+1 entries.
+inline size_t table_bytes(uint32_t m) { return 5 * ((size_t)m + 1) * (sizeof(double) + sizeof(float)); }
+
+// Fills `host` (table_bytes(m) bytes) and sets `out` to point into the same
+// layout at device address `dev`.
+inline void build_tables(uint32_t m, unsigned char *host, const void *dev, Tables *out) {
+    const size_t n = (size_t)m + 1;
+    double *beta = (double *)host, *gamma = beta + n, *dgamma = gamma + n, *c4 = dgamma + n, *inv4 = c4 + n;
+    for (size_t i = 0; i < 5 * n; i++) beta[i] = 0.0;
+    for (uint32_t i = 1; i <= m; i++) beta[i] = (double)m / (double)(m - i + 1);
+    double lambda1 = 0.0, c3 = 0.0, inv3 = 0.0, delta = 0.0;
+    if (m >= 2) {
+        lambda1 = std::log1p(1.0 / (double)(m - 1));
+        c3 = std::expm1(-lambda1);
+        inv3 = 1.0 / lambda1;
+        delta = 1.0 / lambda1;
+        for (uint32_t i = 1; i < m; i++) {
+            const double li = std::log1p(1.0 / (double)(m - i));
+            c4[i] = std::expm1(-li);
+            inv4[i] = 1.0 / li;
+            gamma[i] = std::log1p((double)i / (double)(m - i)) / lambda1;
+            dgamma[i] = gamma[i] - gamma[i - 1];
+        }
+    }
+    float *f = (float *)(host + 5 * n * sizeof(double));
+    for (size_t i = 0; i < 5 * n; i++) f[i] = (float)beta[i];
+    const char *d = (const char *)dev;
+    Tables &t = *out;
+    t.m = m;
+    t.beta = (const double *)d;
+    t.gamma = (const double *)(d + 1 * n * sizeof(double));
+    t.dgamma = (const double *)(d + 2 * n * sizeof(double));
+    t.c4 = (const double *)(d + 3 * n * sizeof(double));
+    t.inv4 = (const double *)(d + 4 * n * sizeof(double));
+    const char *fb = d + 5 * n * sizeof(double);
+    t.beta32 = (const float *)fb;
+    t.gamma32 = (const float *)(fb + 1 * n * sizeof(float));
+    t.dgamma32 = (const float *)(fb + 2 * n * sizeof(float));
+    t.c4_32 = (const float *)(fb + 3 * n * sizeof(float));
+    t.inv4_32 = (const float *)(fb + 4 * n * sizeof(float));
+    t.c3 = c3;
+    t.inv3 = inv3;
+    t.delta = delta;
+    t.c3_32 = (float)c3;
+    t.inv3_32 = (float)inv3;
+    t.delta32 = (float)delta;
+    // Exp(lambda_1;0,1) >= U * (1-e^-lambda_1)/lambda_1 (since -log1p(-a) >= a); round the factor down
+    const double lo = (m >= 2) ? -c3 / lambda1 : 1.0;
+    float lo32 = (float)lo;
+    if ((double)lo32 > lo) lo32 = std::nextafterf(lo32, 0.0f);
+    t.te_lo = lo32;
+    t.lambda1_32 = (float)lambda1;
+}
+
+inline uint64_t host_mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ------------------------------------------------------------------ queue
+// Items (variant, set) in family-major order (ProbMinHash1/1a, 2, 3/3a, 4),
+// each family sorted by decreasing floor(log2(n+1)) (largest sets first).
+// Meta layout: [0, 256) histogram per (family, bucket), [256, 512) running
+// starts, [512, 516) per-family head counters of the persistent kernels.
+constexpr int kQHist = 0, kQStart = 256, kQHead = 512, kQMetaWords = 520;
+
+struct FamOfVariant {
+    int f[8];
+};
+
+__device__ __forceinline__ int queue_bucket(const int64_t *off, int64_t s) {
+    int64_t n = off[s + 1] - off[s];
+    if (n < 0) n = 0;
+    return 63 - __clzll((long long)(n + 1));
+}
+
+static __global__ void queue_count(const int64_t *off, int64_t num_sets, int32_t nv, FamOfVariant fv, unsigned int *meta) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < num_sets * nv; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = i % num_sets;
+        const int v = (int)(i / num_sets);
+        atomicAdd(&meta[kQHist + (fv.f[v] - 1) * 64 + queue_bucket(off, s)], 1u);
+    }
+}
+static __global__ void queue_starts(unsigned int *meta) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        unsigned int acc = 0;
+        for (int f = 0; f < 4; ++f)
+            for (int b = 63; b >= 0; --b) { meta[kQStart + f * 64 + b] = acc; acc += meta[kQHist + f * 64 + b]; }
+        for (int f = 0; f < 4; ++f) meta[kQHead + f] = 0;
+    }
+}
+static __global__ void queue_scatter(const int64_t *off, int64_t num_sets, int32_t nv, FamOfVariant fv,
+                                     unsigned int *meta, uint64_t *queue) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < num_sets * nv; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = i % num_sets;
+        const int64_t v = i / num_sets;
+        const unsigned int pos = atomicAdd(&meta[kQStart + (fv.f[v] - 1) * 64 + queue_bucket(off, s)], 1u);
+        queue[pos] = ((uint64_t)v << 40) | (uint64_t)s;
+    }
+}
+
+// Per-set statistics, computed once per set for all variants: the weight sum
+// (FP64; it only sets the threshold T), the number of positive weights, and a
+// bad-weight flag (negative, NaN, +-inf, or a subnormal whose reciprocal
+// overflows).  One block per set, grid-stride over sets.
+static __global__ void __launch_bounds__(256) set_stats_kernel(const int64_t *off, const double *w, int64_t num_sets,
+                                                               SetStat *out) {
+    __shared__ double ssum[8];
+    __shared__ int snp[8], sbad[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t s = blockIdx.x; s < num_sets; s += gridDim.x) {
+        const int64_t b = off[s], e = off[s + 1];
+        double sum = 0.0;
+        int np = 0, bad = 0;
+        for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+            const double x = w[i];
+            const uint64_t bits = (uint64_t)__double_as_longlong(x);
+            const int ex = (int)(bits >> 52) & 0x7FF;
+            const bool neg = (bits >> 63) != 0;
+            if (ex == 0x7FF || (neg && (bits << 1) != 0)) { bad = 1; continue; }
+            if (neg || (bits << 1) == 0) continue;
+            if (ex == 0 && isinf(__drcp_rn(x))) { bad = 1; continue; }
+            sum += x;
+            np++;
+        }
+        for (int o = 16; o; o >>= 1) {
+            sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+            np += __shfl_xor_sync(0xFFFFFFFFu, np, o);
+            bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, o);
+        }
+        if (lane == 0) { ssum[warp] = sum; snp[warp] = np; sbad[warp] = bad; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double S = 0.0;
+            int N = 0, B = 0;
+            for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { S += ssum[j]; N += snp[j]; B |= sbad[j]; }
+            SetStat r;
+            r.wsum = S;
+            r.npos = N;
+            r.bad = B;
+            out[s] = r;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ plan
+// Launch plan per family present: warp teams when at least 12 warps per SM
+// fit, else CTA teams.  Computed outside any stream capture (it sets kernel
+// attributes).
+struct Plan {
+    int nfam;
+    int fam[4];
+    int64_t qbase[4], qlen[4];
+    LaunchShape shape[4];
+    int grid[4];
+};
+
+// Returns cudaSuccess and sets *fits = false when m does not fit in shared memory.
+inline cudaError_t plan_batch(int sm_count, int precision, uint32_t m, const int32_t *variants, int nv,
+                              int64_t num_sets, Plan *out, bool *fits) {
+    const bool f32 = precision == PMH_FP32_RECHECK;
+    int64_t per_fam[4] = {0, 0, 0, 0};
+    for (int v = 0; v < nv; v++) per_fam[family_of(variants[v]) - 1] += num_sets;
+    out->nfam = 0;
+    *fits = true;
+    int64_t base = 0;
+    for (int f = 1; f <= 4; f++) {
+        const int64_t items = per_fam[f - 1];
+        if (items == 0) continue;
+        LaunchShape warp_s{}, cta_s{};
+        cudaError_t e = sketch_shape_any(f32, f, false, m, false, &warp_s);
+        if (e != cudaSuccess) return e;
+        LaunchShape shape = warp_s;
+        if (warp_s.blocks_per_sm * 4 < 12) {
+            e = sketch_shape_any(f32, f, true, m, false, &cta_s);
+            if (e != cudaSuccess) return e;
+            if (cta_s.blocks_per_sm > 0) shape = cta_s;
+        }
+        if (shape.blocks_per_sm <= 0) { *fits = false; return cudaSuccess; }
+        int grid = sm_count * shape.blocks_per_sm;
+        const int64_t teams_needed = shape.cta_team ? items : (items + 3) / 4;
+        if (teams_needed < grid) grid = (int)std::max<int64_t>(1, teams_needed);
+        const int j = out->nfam++;
+        out->fam[j] = f;
+        out->qbase[j] = base;
+        out->qlen[j] = items;
+        out->shape[j] = shape;
+        out->grid[j] = grid;
+        base += items;
+    }
+    return cudaSuccess;
+}
+
+// Enqueues queue build, set statistics and one persistent kernel per family
+// on `st`.  `ev` (optional) receives records before the queue build, before
+// the sketch kernels and after them.
+inline cudaError_t enqueue_batch(SketchParams p, const Plan &plan, int precision, int sm_count, uint64_t *queue,
+                                 unsigned int *qmeta, SetStat *stats, cudaStream_t st, cudaEvent_t *ev) {
+    const int64_t items = p.num_sets * p.num_variants;
+    FamOfVariant fv{};
+    for (int v = 0; v < p.num_variants; v++) fv.f[v] = family_of(p.variants[v]);
+    const int qb = 256;
+    int qg = (int)std::min<int64_t>((items + qb - 1) / qb, (int64_t)sm_count * 8);
+    if (qg < 1) qg = 1;
+    cudaError_t e;
+    if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(qmeta, 0, kQMetaWords * sizeof(unsigned int), st)) != cudaSuccess) return e;
+    queue_count<<<qg, qb, 0, st>>>(p.offsets, p.num_sets, p.num_variants, fv, qmeta);
+    queue_starts<<<1, 32, 0, st>>>(qmeta);
+    queue_scatter<<<qg, qb, 0, st>>>(p.offsets, p.num_sets, p.num_variants, fv, qmeta, queue);
+    const int sg = (int)std::max<int64_t>(1, std::min<int64_t>(p.num_sets, (int64_t)sm_count * 8));
+    set_stats_kernel<<<sg, 256, 0, st>>>(p.offsets, p.weights, p.num_sets, stats);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    p.stats = stats;
+    if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
+    for (int j = 0; j < plan.nfam; j++) {
+        p.queue = queue + plan.qbase[j];
+        p.queue_len = plan.qlen[j];
+        p.head = qmeta + kQHead + (plan.fam[j] - 1);
+        e = sketch_launch_any(precision == PMH_FP32_RECHECK, plan.fam[j], plan.shape[j], plan.grid[j], p, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+// Fills the fields of SketchParams common to both entry points.
+inline void fill_params(SketchParams *p, const uint64_t *ids, const double *weights, const int64_t *offsets,
+                        int64_t num_sets, uint32_t m, const int32_t *variants, int32_t nv, uint64_t seed,
+                        uint64_t *out_ids, double *out_q, int32_t *set_status, uint64_t *counters, float t_c,
+                        int rounds) {
+    std::memset(p, 0, sizeof(*p));
+    p->ids = ids;
+    p->weights = weights;
+    p->offsets = offsets;
+    p->num_sets = num_sets;
+    p->m = m;
+    p->mixed_seed = host_mix64(seed);
+    for (int v = 0; v < nv; v++) p->variants[v] = variants[v];
+    p->num_variants = nv;
+    p->out_ids = out_ids;
+    p->out_q = out_q;
+    p->status = set_status;
+    p->counters = (unsigned long long *)counters;
+    p->t_factor = (float)(std::log((double)m) + t_c);
+    p->rounds = rounds;
+    p->cap_points = (uint32_t)(64.0 * m * std::log((double)m + 1.0)) + 4096;
+}
+
+}  // namespace pmh

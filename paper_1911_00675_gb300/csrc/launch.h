@@ -22,6 +22,9 @@ cudaError_t sketch_shape(bool cta_team, uint32_t m, bool has_perm, LaunchShape *
 template <bool F32, int FAM>
 cudaError_t sketch_launch(const LaunchShape &s, int grid, const SketchParams &p, cudaStream_t st);
 
+// Records the message returned by pmh_last_error(NULL) on this host thread.
+void set_thread_error(const char *msg);
+
 // Dispatch on (precision, family) at run time.
 cudaError_t sketch_shape_any(bool f32, int fam, bool cta_team, uint32_t m, bool has_perm, LaunchShape *out);
 cudaError_t sketch_launch_any(bool f32, int fam, const LaunchShape &s, int grid, const SketchParams &p,

@@ -1,0 +1,123 @@
+// pmh_sketch_batch_noalloc: the batch sketch for callers that cannot allocate
+// GPU memory (for example code running inside another runtime's memory
+// budget, or under a framework that forbids cudaMalloc on its hot path).  It
+// runs the same kernels as pmh_sketch_batch, but its scratch memory (constant
+// tables, work queue and per-set statistics) lives in one file-scope device
+// array of fixed size that every GPU holds from the moment the library is
+// loaded until the process exits.  No call here allocates or frees device
+// memory, and no CUDA graph is built.
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "batch_common.cuh"
+
+using namespace pmh;
+
+namespace {
+
+// Scratch layout: tables for m <= PMH_MAX_M | queue metadata | work queue | per-set statistics.
+constexpr size_t kTableRegion = 512u * 1024u;                                  // >= table_bytes(PMH_MAX_M)
+constexpr size_t kMetaRegion = 4096;                                            // >= kQMetaWords * 4
+constexpr size_t kQueueRegion = (size_t)PMH_NOALLOC_MAX_ITEMS * sizeof(uint64_t);
+constexpr size_t kStatsRegion = (size_t)PMH_NOALLOC_MAX_SETS * 16;
+constexpr size_t kScratchBytes = kTableRegion + kMetaRegion + kQueueRegion + kStatsRegion;
+static_assert(kMetaRegion >= kQMetaWords * sizeof(unsigned int), "queue metadata region too small");
+static_assert(sizeof(SetStat) == 16, "per-set statistics entry is 16 bytes");
+
+// Lives in every GPU's memory while the library is loaded.  In host code this
+// name is only a stand-in: the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+struct DeviceState {
+    bool ready = false;
+    unsigned char *base = nullptr;   // device address of g_noalloc_scratch on this device
+    int sm_count = 0;
+    uint32_t table_m = 0;            // m whose tables the table region holds (0 = none)
+};
+DeviceState g_state[kMaxDevices];
+std::mutex g_mu;
+unsigned char g_host_tables[kTableRegion];   // staging for table uploads (static: no allocation)
+
+pmh_status fail_na(pmh_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    set_thread_error(buf);
+    return code;
+}
+
+}  // namespace
+
+extern "C" pmh_status pmh_sketch_batch_noalloc(const uint64_t *ids, const double *weights, const int64_t *offsets,
+                                               int64_t num_sets, uint32_t m, const int32_t *variants,
+                                               int32_t num_variants, int32_t precision, uint64_t seed,
+                                               uint64_t *out_ids, double *out_q, int32_t *set_status,
+                                               uint64_t *counters, void *stream) {
+    set_thread_error("");
+    if (num_sets < 0) return fail_na(PMH_ERR_INVALID_ARG, "num_sets < 0");
+    if (m < 1 || m > PMH_MAX_M) return fail_na(PMH_ERR_UNSUPPORTED, "m = %u outside [1, %u]", m, PMH_MAX_M);
+    if (!variants || num_variants < 1 || num_variants > 8) return fail_na(PMH_ERR_INVALID_ARG, "need 1..8 variants");
+    if (precision != PMH_FP64 && precision != PMH_FP32_RECHECK) return fail_na(PMH_ERR_INVALID_ARG, "bad precision %d", precision);
+    for (int v = 0; v < num_variants; v++) {
+        if (variants[v] < PMH_V1 || variants[v] > PMH_V4) return fail_na(PMH_ERR_INVALID_ARG, "bad variant %d", variants[v]);
+        if ((variants[v] == PMH_V3 || variants[v] == PMH_V3A || variants[v] == PMH_V4) && m < 2)
+            return fail_na(PMH_ERR_INVALID_ARG, "variant %d requires m >= 2", variants[v]);
+    }
+    if (num_sets > PMH_NOALLOC_MAX_SETS)
+        return fail_na(PMH_ERR_UNSUPPORTED, "num_sets = %lld exceeds the allocation-free limit of %d sets",
+                       (long long)num_sets, PMH_NOALLOC_MAX_SETS);
+    if (num_sets * num_variants > PMH_NOALLOC_MAX_ITEMS)
+        return fail_na(PMH_ERR_UNSUPPORTED, "num_sets * num_variants = %lld exceeds the allocation-free limit of %d items",
+                       (long long)(num_sets * num_variants), PMH_NOALLOC_MAX_ITEMS);
+    if (num_sets == 0) return PMH_OK;
+    if (!ids || !weights || !offsets || !out_ids) return fail_na(PMH_ERR_INVALID_ARG, "NULL ids/weights/offsets/out_ids");
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail_na(PMH_ERR_UNSUPPORTED, "device %d beyond %d", dev, kMaxDevices);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(g_mu);
+    DeviceState &ds = g_state[dev];
+    if (!ds.ready) {
+        // first call on this device: resolve the array's device address (do this before any stream capture)
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        e = cudaDeviceGetAttribute(&ds.sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "device attribute: %s", cudaGetErrorString(e));
+        ds.base = (unsigned char *)ptr;
+        ds.ready = true;
+    }
+    unsigned char *tables = ds.base;
+    unsigned int *qmeta = (unsigned int *)(ds.base + kTableRegion);
+    uint64_t *queue = (uint64_t *)(ds.base + kTableRegion + kMetaRegion);
+    SetStat *stats = (SetStat *)(ds.base + kTableRegion + kMetaRegion + kQueueRegion);
+
+    Tables tab;
+    build_tables(m, g_host_tables, tables, &tab);
+    if (ds.table_m != m) {
+        // the table region keeps the last call's contents; upload only when m changes
+        e = cudaMemcpyAsync(tables, g_host_tables, table_bytes(m), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
+        ds.table_m = m;
+    }
+    SketchParams p;
+    fill_params(&p, ids, weights, offsets, num_sets, m, variants, num_variants, seed, out_ids, out_q, set_status,
+                counters, 4.0f, 5);
+    p.tab = tab;
+    Plan plan;
+    bool fits = true;
+    e = plan_batch(ds.sm_count, precision, m, variants, num_variants, num_sets, &plan, &fits);
+    if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
+    if (!fits) return fail_na(PMH_ERR_UNSUPPORTED, "m = %u does not fit in shared memory", m);
+    // enqueue_batch clears the queue metadata; the queue and the statistics are rewritten in full
+    e = enqueue_batch(p, plan, precision, ds.sm_count, queue, qmeta, stats, st, nullptr);
+    if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "sketch launch: %s", cudaGetErrorString(e));
+    return PMH_OK;
+}

@@ -22,8 +22,8 @@ VARIANTS = {"1": V1, "1a": V1A, "2": V2, "3": V3, "3a": V3A, "4": V4}
 FP64, FP32_RECHECK = 0, 1
 COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "rounds", "deep", "prefiltered",
             "cyc_pass0", "cyc_first", "cyc_deep", "cyc_refresh", "cyc_finish", "items", "cyc_surv", "reserved15")
-EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_set_profiling",
-           "pmh_last_kernel_ms", "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge")
+EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_sketch_batch_noalloc",
+           "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge")
 
 _lib = None
 _lock = threading.Lock()
@@ -53,6 +53,9 @@ def load(path: str = LIB_PATH):
             lib.pmh_sketch_batch.restype = i32
             lib.pmh_sketch_batch.argtypes = [vp, vp, vp, vp, i64, u32, ctypes.POINTER(i32), i32, i32, u64, vp, vp, vp,
                                              vp, vp]
+            lib.pmh_sketch_batch_noalloc.restype = i32
+            lib.pmh_sketch_batch_noalloc.argtypes = [vp, vp, vp, i64, u32, ctypes.POINTER(i32), i32, i32, u64, vp, vp,
+                                                     vp, vp, vp]
             lib.pmh_set_profiling.restype = i32
             lib.pmh_set_profiling.argtypes = [vp, i32]
             lib.pmh_last_kernel_ms.restype = i32
@@ -210,6 +213,36 @@ def handle(device: int | None = None) -> Handle:
 
 def sketch_batch(ids, weights, offsets, m, variants=("1",), precision=FP32_RECHECK, seed=0, **kw):
     return handle(ids.device.index).sketch_batch(ids, weights, offsets, m, variants, precision, seed, **kw)
+
+
+def sketch_batch_noalloc(ids, weights, offsets, m, variants=("1",), precision=FP32_RECHECK, seed=0, out_ids=None,
+                         out_q=None, status=None, counters=None, with_q=False, stream=None):
+    """pmh_sketch_batch_noalloc on the tensors' device (no handle, no GPU allocation inside the library).
+    Outputs are allocated here only when not given."""
+    dev = ids.device
+    _check(ids, "ids", _I64, dev)
+    _check(weights, "weights", (torch.float64,), dev)
+    _check(offsets, "offsets", (torch.int64,), dev)
+    vs = [VARIANTS[v] if isinstance(v, str) else int(v) for v in variants]
+    s = offsets.numel() - 1
+    if out_ids is None:
+        out_ids = torch.empty((len(vs), s, m), dtype=torch.int64, device=dev)
+    if out_q is None and with_q:
+        out_q = torch.empty((len(vs), s, m), dtype=torch.float64, device=dev)
+    if status is None:
+        status = torch.empty((len(vs), s), dtype=torch.int32, device=dev)
+    _check(out_ids, "out_ids", _I64, dev)
+    _check(out_q, "out_q", (torch.float64,), dev)
+    _check(status, "status", (torch.int32,), dev)
+    _check(counters, "counters", _I64, dev)
+    arr = (ctypes.c_int32 * len(vs))(*vs)
+    with torch.cuda.device(dev):
+        rc = load().pmh_sketch_batch_noalloc(_ptr(ids), _ptr(weights), _ptr(offsets), s, m, arr, len(vs),
+                                             int(precision), int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out_ids),
+                                             _ptr(out_q), _ptr(status), _ptr(counters), _stream(stream))
+    if rc:
+        raise PmhError(rc, load().pmh_last_error(None).decode())
+    return out_ids, out_q, status
 
 
 def estimate_allpairs(sigs, upper_only=False, **kw):
