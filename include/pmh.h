@@ -178,6 +178,37 @@ pmh_status pmh_set_profiling(pmh_handle h, int32_t enable);
 pmh_status pmh_last_kernel_ms(pmh_handle h, float *queue_ms, float *sketch_ms);
 
 /*
+ * pmh_last_launches -- number of kernels the most recent pmh_sketch_batch on
+ * `h` launched (queue build, statistics, per-family sketch kernels and, when
+ * grid mode is on, its reset kernel and per-family grid kernels).
+ */
+pmh_status pmh_last_launches(pmh_handle h, int32_t *launches);
+
+/*
+ * pmh_set_thresholds -- work-only tuning of later pmh_sketch_batch calls on `h`.
+ * Results never depend on these values; only the amount of work does.
+ *
+ * The paper's algorithms generate each element's points in increasing order
+ * and stop once a point exceeds the running maximum of the signature
+ * (Sec. "ProbMinHash1", stop rule).  The GPU kernels first generate only the
+ * points below a threshold T (round 1: T = m (ln m + t_c) / sum of weights,
+ * which leaves a given component empty with probability about e^-t_c / m);
+ * while a component is still empty they repeat with T x 4, and after `rounds`
+ * finite rounds with T = infinity (the paper's unbounded loop).
+ *
+ *   t_c       finite; default 4.
+ *   t_c_grid  the same constant for grid-mode items; default 8.
+ *   rounds    0..64 finite rounds; default 5.
+ *   grid_min  sets with at least grid_min elements are processed by all SMs
+ *             together (grid mode; at most 16 such items per family and
+ *             call, the rest as usual); <= 0 turns grid mode off.
+ *             Default 2^20.
+ * Errors: PMH_ERR_INVALID_ARG for NULL h, a non-finite t_c / t_c_grid or
+ * rounds outside [0, 64].
+ */
+pmh_status pmh_set_thresholds(pmh_handle h, double t_c, double t_c_grid, int32_t rounds, int64_t grid_min);
+
+/*
  * pmh_estimate_allpairs -- numerators of the J_P estimator (Eq. jaccard_estimator)
  * for every pair of signatures: counts[a*num_sigs + b] = #{k : sigs[a][k] == sigs[b][k]}.
  *

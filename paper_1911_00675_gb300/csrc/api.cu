@@ -46,14 +46,16 @@ struct pmh_handle_s {
     unsigned int *qmeta = nullptr;   // histogram, running starts, per-family heads
     SetStat *stats = nullptr;        // per-set statistics
     int64_t stats_cap = 0;
+    void *grid = nullptr;            // grid-mode workspace (huge sets)
+    size_t grid_bytes = 0;
     cudaStream_t cap_stream = nullptr;
     bool graph_valid = false;
     GraphKey gkey{};
     cudaGraphExec_t gexec = nullptr;
     bool use_graph = true;
     // planner knobs (tunable)
-    float t_c = 4.0f;
-    int rounds = 5;
+    Thresholds th;
+    int last_launches = 0;
     // profiling events
     bool profiling = false;
     bool prof_recorded = false;
@@ -105,6 +107,20 @@ static pmh_status ensure_queue(pmh_handle h, int64_t items) {
         cudaError_t e = cudaMalloc(&h->queue, (size_t)cap * sizeof(uint64_t));
         if (e != cudaSuccess) return fail(h, PMH_ERR_NO_MEMORY, "queue allocation (%lld items): %s", (long long)cap, cudaGetErrorString(e));
         h->queue_cap = cap;
+        h->graph_valid = false;
+    }
+    return PMH_OK;
+}
+
+static pmh_status ensure_grid(pmh_handle h, uint32_t m) {
+    const size_t need = grid_scratch_bytes(m);
+    if (need > h->grid_bytes) {
+        if (h->grid) cudaFree(h->grid);
+        h->grid = nullptr;
+        h->grid_bytes = 0;
+        cudaError_t e = cudaMalloc(&h->grid, need);
+        if (e != cudaSuccess) return fail(h, PMH_ERR_NO_MEMORY, "grid workspace (%zu bytes): %s", need, cudaGetErrorString(e));
+        h->grid_bytes = need;
         h->graph_valid = false;
     }
     return PMH_OK;
@@ -167,6 +183,7 @@ extern "C" void pmh_destroy(pmh_handle h) {
     if (h->queue) cudaFree(h->queue);
     if (h->qmeta) cudaFree(h->qmeta);
     if (h->stats) cudaFree(h->stats);
+    if (h->grid) cudaFree(h->grid);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
@@ -180,6 +197,26 @@ extern "C" pmh_status pmh_set_profiling(pmh_handle h, int32_t enable) {
     if (enable && !h->ev[0])
         for (int i = 0; i < 3; i++) CUDA_TRY(h, cudaEventCreate(&h->ev[i]));
     h->profiling = enable != 0;
+    return PMH_OK;
+}
+
+extern "C" pmh_status pmh_set_thresholds(pmh_handle h, double t_c, double t_c_grid, int32_t rounds, int64_t grid_min) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    if (!std::isfinite(t_c) || !std::isfinite(t_c_grid)) return fail(h, PMH_ERR_INVALID_ARG, "t_c and t_c_grid must be finite");
+    if (rounds < 0 || rounds > 64) return fail(h, PMH_ERR_INVALID_ARG, "rounds = %d outside [0, 64]", rounds);
+    h->th.t_c = t_c;
+    h->th.t_c_grid = t_c_grid;
+    h->th.rounds = rounds;
+    h->th.grid_min = grid_min;
+    h->graph_valid = false;
+    return PMH_OK;
+}
+
+extern "C" pmh_status pmh_last_launches(pmh_handle h, int32_t *launches) {
+    if (!h || !launches) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    *launches = h->last_launches;
     return PMH_OK;
 }
 
@@ -227,17 +264,25 @@ extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const 
     if (rc) return rc;
     rc = ensure_stats(h, num_sets);
     if (rc) return rc;
+    rc = ensure_grid(h, m);
+    if (rc) return rc;
 
     SketchParams p;
     fill_params(&p, ids, weights, offsets, num_sets, m, variants, num_variants, seed, out_ids, out_q, set_status, counters,
-                h->t_c, h->rounds);
+                h->th);
     p.tab = tab;
+    if (h->th.grid_min > 0) bind_grid_scratch(&p, h->grid);
     (void)has_perm;
     Plan plan;
     bool fits = true;
     cudaError_t pe = plan_batch(h->sm_count, precision, m, variants, num_variants, num_sets, &plan, &fits);
     if (pe != cudaSuccess) return fail(h, PMH_ERR_CUDA, "occupancy: %s", cudaGetErrorString(pe));
     if (!fits) return fail(h, PMH_ERR_UNSUPPORTED, "m = %u does not fit in shared memory", m);
+    // grid mode only when every family's grid kernel can be resident (items it
+    // takes are skipped by the ordinary kernels)
+    for (int j = 0; j < plan.nfam && p.gctl; j++)
+        if (plan.ggrid[j] <= 0) { p.gctl = nullptr; p.gstate = nullptr; p.gsig = nullptr; }
+    h->last_launches = launch_count(plan, p.gctl != nullptr);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (st) CUDA_TRY(h, cudaStreamIsCapturing(st, &cs));
     if (!h->use_graph || cs != cudaStreamCaptureStatusNone || !st) {

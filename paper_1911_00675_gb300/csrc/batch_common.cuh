@@ -107,13 +107,24 @@ static __global__ void queue_starts(unsigned int *meta) {
         for (int f = 0; f < 4; ++f) meta[kQHead + f] = 0;
     }
 }
+// Items of sets with at least grid_min elements also go to the per-family grid
+// list (first kMaxGrid of them); their queue entries are then marked skipped.
 static __global__ void queue_scatter(const int64_t *off, int64_t num_sets, int32_t nv, FamOfVariant fv,
-                                     unsigned int *meta, uint64_t *queue) {
+                                     unsigned int *meta, uint64_t *queue, GridCtl *gctl, int64_t grid_min) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < num_sets * nv; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = i % num_sets;
         const int64_t v = i / num_sets;
-        const unsigned int pos = atomicAdd(&meta[kQStart + (fv.f[v] - 1) * 64 + queue_bucket(off, s)], 1u);
-        queue[pos] = ((uint64_t)v << 40) | (uint64_t)s;
+        const int f = fv.f[v] - 1;
+        const unsigned int pos = atomicAdd(&meta[kQStart + f * 64 + queue_bucket(off, s)], 1u);
+        uint64_t item = ((uint64_t)v << 40) | (uint64_t)s;
+        if (gctl && off[s + 1] - off[s] >= grid_min && off[s + 1] - off[s] <= (int64_t)PMH_MAX_SET_ELEMENTS) {
+            const unsigned int slot = atomicAdd(&gctl->count[f], 1u);
+            if (slot < (unsigned int)kMaxGrid) {
+                gctl->list[f][slot] = item;
+                item |= kSkipBit;
+            }
+        }
+        queue[pos] = item;
     }
 }
 
@@ -172,6 +183,8 @@ struct Plan {
     int64_t qbase[4], qlen[4];
     LaunchShape shape[4];
     int grid[4];
+    LaunchShape gshape[4];   // grid-mode kernel (blocks_per_sm = 0: grid mode off for this family)
+    int ggrid[4];
 };
 
 // Returns cudaSuccess and sets *fits = false when m does not fit in shared memory.
@@ -205,6 +218,11 @@ inline cudaError_t plan_batch(int sm_count, int precision, uint32_t m, const int
         out->qlen[j] = items;
         out->shape[j] = shape;
         out->grid[j] = grid;
+        LaunchShape gs{};
+        e = grid_shape_any(f32, f, m, &gs);
+        if (e != cudaSuccess) return e;
+        out->gshape[j] = gs;
+        out->ggrid[j] = sm_count * gs.blocks_per_sm;
         base += items;
     }
     return cudaSuccess;
@@ -226,7 +244,9 @@ inline cudaError_t enqueue_batch(SketchParams p, const Plan &plan, int precision
     if ((e = cudaMemsetAsync(qmeta, 0, kQMetaWords * sizeof(unsigned int), st)) != cudaSuccess) return e;
     queue_count<<<qg, qb, 0, st>>>(p.offsets, p.num_sets, p.num_variants, fv, qmeta);
     queue_starts<<<1, 32, 0, st>>>(qmeta);
-    queue_scatter<<<qg, qb, 0, st>>>(p.offsets, p.num_sets, p.num_variants, fv, qmeta, queue);
+    if (p.gctl && (e = cudaMemsetAsync(p.gctl, 0, sizeof(unsigned int) * 4, st)) != cudaSuccess) return e;
+    queue_scatter<<<qg, qb, 0, st>>>(p.offsets, p.num_sets, p.num_variants, fv, qmeta, queue, p.gctl, p.grid_min);
+    if (p.gctl) grid_init_kernel<<<4 * kMaxGrid, 256, 0, st>>>(p.gctl, p.gstate, p.gsig, p.m, precision == PMH_FP32_RECHECK);
     const int sg = (int)std::max<int64_t>(1, std::min<int64_t>(p.num_sets, (int64_t)sm_count * 8));
     set_stats_kernel<<<sg, 256, 0, st>>>(p.offsets, p.weights, p.num_sets, stats);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -238,16 +258,36 @@ inline cudaError_t enqueue_batch(SketchParams p, const Plan &plan, int precision
         p.head = qmeta + kQHead + (plan.fam[j] - 1);
         e = sketch_launch_any(precision == PMH_FP32_RECHECK, plan.fam[j], plan.shape[j], plan.grid[j], p, st);
         if (e != cudaSuccess) return e;
+        if (p.gctl && plan.ggrid[j] > 0) {
+            e = grid_launch_any(precision == PMH_FP32_RECHECK, plan.fam[j], plan.gshape[j], plan.ggrid[j], p, st);
+            if (e != cudaSuccess) return e;
+        }
     }
     if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
+// Work-only parameters of a sketch call: first-round threshold
+// T = m (ln m + t_c) / sum(w) (t_c_grid for grid items), number of finite
+// threshold rounds, and the set size from which grid mode is used (<= 0: off).
+struct Thresholds {
+    double t_c = 4.0;
+    double t_c_grid = 8.0;
+    int rounds = 5;
+    int64_t grid_min = kGridMinDefault;
+};
+
+// Kernel launches of one enqueue_batch call (fixed by the plan).
+inline int launch_count(const Plan &plan, bool grid) {
+    int n = 4 + plan.nfam + (grid ? 1 : 0);
+    for (int j = 0; j < plan.nfam; j++) n += (grid && plan.ggrid[j] > 0) ? 1 : 0;
+    return n;
+}
+
 // Fills the fields of SketchParams common to both entry points.
 inline void fill_params(SketchParams *p, const uint64_t *ids, const double *weights, const int64_t *offsets,
                         int64_t num_sets, uint32_t m, const int32_t *variants, int32_t nv, uint64_t seed,
-                        uint64_t *out_ids, double *out_q, int32_t *set_status, uint64_t *counters, float t_c,
-                        int rounds) {
+                        uint64_t *out_ids, double *out_q, int32_t *set_status, uint64_t *counters, const Thresholds &th) {
     std::memset(p, 0, sizeof(*p));
     p->ids = ids;
     p->weights = weights;
@@ -261,9 +301,25 @@ inline void fill_params(SketchParams *p, const uint64_t *ids, const double *weig
     p->out_q = out_q;
     p->status = set_status;
     p->counters = (unsigned long long *)counters;
-    p->t_factor = (float)(std::log((double)m) + t_c);
-    p->rounds = rounds;
+    p->t_factor = (float)(std::log((double)m) + th.t_c);
+    p->rounds = th.rounds;
     p->cap_points = (uint32_t)(64.0 * m * std::log((double)m + 1.0)) + 4096;
+    p->t_factor_grid = (float)(std::log((double)m) + th.t_c_grid);
+    p->grid_min = th.grid_min;
+    p->gctl = nullptr;
+    p->gstate = nullptr;
+    p->gsig = nullptr;
+}
+
+// Device bytes of the grid-mode workspace for signature size m.
+inline size_t grid_scratch_bytes(uint32_t m) {
+    return align16(sizeof(GridCtl)) + align16(sizeof(GridState) * 4 * kMaxGrid) + (size_t)4 * kMaxGrid * m * 16;
+}
+inline void bind_grid_scratch(SketchParams *p, void *base) {
+    unsigned char *b = (unsigned char *)base;
+    p->gctl = (GridCtl *)b;
+    p->gstate = (GridState *)(b + align16(sizeof(GridCtl)));
+    p->gsig = b + align16(sizeof(GridCtl)) + align16(sizeof(GridState) * 4 * kMaxGrid);
 }
 
 }  // namespace pmh

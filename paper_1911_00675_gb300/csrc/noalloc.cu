@@ -108,8 +108,10 @@ extern "C" pmh_status pmh_sketch_batch_noalloc(const uint64_t *ids, const double
         ds.table_m = m;
     }
     SketchParams p;
+    Thresholds th;
+    th.grid_min = 0;   // grid mode needs workspace sized by m: off here
     fill_params(&p, ids, weights, offsets, num_sets, m, variants, num_variants, seed, out_ids, out_q, set_status,
-                counters, 4.0f, 5);
+                counters, th);
     p.tab = tab;
     Plan plan;
     bool fits = true;

@@ -40,4 +40,29 @@ cudaError_t sketch_launch<PMH_F32, PMH_FAM>(const LaunchShape &s, int grid, cons
     return cudaGetLastError();
 }
 
+template <>
+cudaError_t grid_shape<PMH_F32, PMH_FAM>(uint32_t m, LaunchShape *out) {
+    SmemLayout L(1, 8, m, PMH_F32, PMH_FAM == 2 || PMH_FAM == 4);
+    out->cta_team = true;
+    out->block = 256;
+    out->smem = L.total;
+    out->blocks_per_sm = 0;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (L.total > (size_t)optin) return cudaSuccess;
+    auto kern = grid_kernel<PMH_F32, PMH_FAM>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->blocks_per_sm, kern, 256, L.total);
+}
+
+template <>
+cudaError_t grid_launch<PMH_F32, PMH_FAM>(const LaunchShape &s, int grid, const SketchParams &p, cudaStream_t st) {
+    grid_kernel<PMH_F32, PMH_FAM><<<grid, s.block, s.smem, st>>>(p);
+    return cudaGetLastError();
+}
+
 }  // namespace pmh

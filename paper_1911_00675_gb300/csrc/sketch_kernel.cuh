@@ -54,6 +54,34 @@ struct __align__(16) Rec64 {
     unsigned long long id;
 };
 
+// Grid mode: items of sets with at least SketchParams::grid_min elements are
+// processed by every CTA of a launch (chunks of kGridChunkMin..kGridChunk
+// elements, about four per CTA), each CTA with its own shared signature,
+// merged into a global one per item.
+constexpr int64_t kGridMinDefault = 1ll << 20;
+constexpr uint32_t kGridChunk = 1u << 16;
+constexpr uint32_t kGridChunkMin = 1u << 11;
+constexpr int kMaxGrid = 16;            // grid items per family and call (further ones use one team)
+constexpr int kGridCont = 1024;         // contender records per grid item
+constexpr uint64_t kSkipBit = 1ull << 63;   // queue entry taken by grid mode
+
+struct GridState {
+    unsigned int next_chunk;
+    unsigned int done;             // CTAs finished with the item
+    unsigned int bound32;          // shared stop bound (float bits, scaled)
+    int status;
+    unsigned long long bound64;    // FP64 path: shared stop bound (double bits)
+    int cont_n;
+    int pad;
+    unsigned int cont_k[kGridCont];
+    unsigned int cont_e[kGridCont];
+};
+
+struct GridCtl {
+    unsigned int count[4];         // grid-eligible items per family (entries beyond kMaxGrid stay in the team queue)
+    unsigned long long list[4][kMaxGrid];
+};
+
 // Per-set statistics (one entry per set, computed once for all variants).
 struct SetStat {
     double wsum;   // sum of the positive weights
@@ -82,6 +110,12 @@ struct SketchParams {
     float t_factor;               // ln m + c
     int rounds;                   // finite-T rounds before the T = +inf round
     uint32_t cap_points;          // iteration cap (with replacement)
+    // grid mode (null when disabled)
+    GridCtl *gctl;
+    GridState *gstate;            // [4][kMaxGrid]
+    void *gsig;                   // [4][kMaxGrid][m] records of 16 bytes
+    float t_factor_grid;          // ln m + c for grid items (larger c: a failed round costs a full pass)
+    int64_t grid_min;             // sets with at least this many elements use grid mode
 };
 
 struct TeamShared {
@@ -138,6 +172,8 @@ struct Ctx {
     int64_t beg;
     uint32_t n;
     int sigma;
+    unsigned int *gbound32;        // grid mode: the item's bound shared by all CTAs (float bits), else null
+    unsigned long long *gbound64;  //   and its FP64 bound (double bits)
 };
 
 __device__ __forceinline__ float ld_volatile(const float *p) { return *(volatile const float *)p; }
@@ -468,41 +504,45 @@ __device__ __noinline__ double exact_h(Ctx<F32> c, uint32_t e, uint32_t k) {
 
 // FP32 path: re-evaluates every logged contender (and the holder of its
 // component) exactly in FP64 and installs the lexicographic (value, id)
-// minimum.  Runs in one warp of the team.  Returns the number of exact
+// minimum in `sig`.  Runs in one warp.  Returns the number of exact
 // evaluations.
 template <int FAM>
-__device__ __noinline__ uint32_t resolve_contenders(Ctx<true> c) {
+__device__ __noinline__ uint32_t resolve_list(Ctx<true> c, const uint32_t *ck, const uint32_t *ce, int ncont,
+                                              uint64_t *sig) {
     const SketchParams &P = *c.p;
-    TeamShared *ts = c.ts;
     const int lane = threadIdx.x & 31;
     uint32_t evals = 0;
-    const int ncont_all = ld_volatile(&ts->cont_n);
-    if (ncont_all > kMaxCont) { if (lane == 0) ts->status = PMH_ERR_ITER_LIMIT; }
-    const int ncont = min(ncont_all, kMaxCont);
-    uint64_t *sig = (uint64_t *)c.sig;
     for (int a = 0; a < ncont; ++a) {
-        const uint32_t k = ts->cont_k[a];
+        const uint32_t k = ck[a];
         bool seen = false;
-        for (int b = 0; b < a; ++b) seen |= (ts->cont_k[b] == k);
+        for (int b = 0; b < a; ++b) seen |= (ck[b] == k);
         if (seen) continue;
-        const uint64_t hk = sig[k];
+        const uint64_t hk = ld_volatile(&sig[k]);
         uint32_t best_e = (uint32_t)(hk & 0xFFFFFFFFu);
         double best_x = exact_h<FAM, true>(c, best_e, k);
         uint64_t best_id = P.ids[c.beg + best_e];
         evals++;
         for (int b = a; b < ncont; ++b) {
-            if (ts->cont_k[b] != k) continue;
-            const uint32_t ce = ts->cont_e[b];
-            if (ce == best_e) continue;
-            double x = exact_h<FAM, true>(c, ce, k);
+            if (ck[b] != k) continue;
+            const uint32_t e = ce[b];
+            if (e == best_e) continue;
+            double x = exact_h<FAM, true>(c, e, k);
             evals++;
-            uint64_t cid = P.ids[c.beg + ce];
-            if (x < best_x || (x == best_x && cid < best_id)) { best_x = x; best_id = cid; best_e = ce; }
+            uint64_t cid = P.ids[c.beg + e];
+            if (x < best_x || (x == best_x && cid < best_id)) { best_x = x; best_id = cid; best_e = e; }
         }
         if (lane == 0) sig[k] = (hk & 0xFFFFFFFF00000000ull) | best_e;
         __syncwarp();
     }
     return evals;
+}
+
+template <int FAM>
+__device__ __forceinline__ uint32_t resolve_contenders(Ctx<true> &c) {
+    TeamShared *ts = c.ts;
+    const int ncont_all = ld_volatile(&ts->cont_n);
+    if (ncont_all > kMaxCont) { if ((threadIdx.x & 31) == 0) ts->status = PMH_ERR_ITER_LIMIT; }
+    return resolve_list<FAM>(c, ts->cont_k, ts->cont_e, min(ncont_all, kMaxCont), (uint64_t *)c.sig);
 }
 
 // ------------------------------------------------------------ survivors
@@ -680,6 +720,100 @@ __device__ __forceinline__ void team_sync() {
     if (CTA_TEAM) __syncthreads(); else __syncwarp();
 }
 
+// One pass over the elements [lo, hi) of the current item with the team's
+// current bound: filter, compacted survivors, q_max refreshes.  Every warp of
+// the team takes 64-element steps.
+template <int FAM, bool F32, bool CTA_TEAM>
+__device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
+    const SketchParams &P = *c.p;
+    const int lane = threadIdx.x & 31;
+    const int tw = CTA_TEAM ? (threadIdx.x >> 5) : 0;
+    const int team_warps = CTA_TEAM ? (blockDim.x >> 5) : 1;
+    TeamShared *ts = c.ts;
+    WarpShared *ws = c.ws;
+    const float te_lo = (FAM >= 3) ? P.tab.te_lo : 1.0f;
+    if (lane == 0) ws->sb_n = 0;
+    __syncwarp();
+    bool refreshed = false;
+    int steps = 0;
+    for (uint32_t base = lo + tw * 64; base < hi; base += team_warps * 64) {
+        if (c.gbound32 && (steps++ & 15) == 0) {
+            // grid mode: adopt the bound published by the other CTAs of this item
+            if (lane == 0) {
+                atomic_min_pos_float(&ts->bound32, __uint_as_float(ld_volatile((const int *)c.gbound32)));
+                if constexpr (!F32)
+                    atomic_min_pos_double(&ts->bound64, __longlong_as_double((long long)ld_volatile((const uint64_t *)c.gbound64)));
+            }
+            __syncwarp();
+        }
+        // filter two elements per lane: the log-free lower bound of the first point
+        bool surv[2];
+        uint64_t key[2];
+        uint32_t ev[2];
+        bool valid[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t e = base + 32 * h + lane;
+            ev[h] = e;
+            surv[h] = false;
+            key[h] = 0;
+            valid[h] = false;
+            if (e < hi) {
+                const double w = P.weights[c.beg + e];
+                if (weight_positive(w)) {
+                    valid[h] = true;
+                    key[h] = mix64(P.ids[c.beg + e] ^ P.mixed_seed);
+                    const float xlo = winv_scaled(w, c.sigma) * unif_lo(value_word(key[h], 1)) * te_lo;
+                    surv[h] = !(xlo * (1.0f - 8.0f * 0x1p-24f) > ld_volatile(&ts->bound32));
+                }
+            }
+        }
+        int n = ws->sb_n;
+        unsigned nvalid = 0, nsurv = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const unsigned msk = __ballot_sync(kFull, surv[h]);
+            if (surv[h]) {
+                const int pos = n + __popc(msk & ((1u << lane) - 1u));
+                if (pos < kSurvCap) {   // always true: n <= kSurvBatch - 1 before the two appends of <= 32
+                    ws->sb_e[pos] = ev[h];
+                    ws->sb_key[pos] = key[h];
+                } else {
+                    ts->status = PMH_ERR_ITER_LIMIT;
+                }
+            }
+            n = min(n + __popc(msk), kSurvCap);
+            nsurv += __popc(msk);
+            nvalid += popc_ballot(valid[h]);
+        }
+        count(c, PMH_CNT_ELEMENTS, nvalid);
+        count(c, PMH_CNT_PREFILTERED, nvalid - nsurv);
+        __syncwarp();
+        bool any_win = false;
+        if (n >= kSurvBatch) {
+            any_win = process_survivors<FAM, F32>(c, n);
+            n = 0;
+        }
+        if (lane == 0) ws->sb_n = n;
+        __syncwarp();
+        // refresh q_max once everything is filled
+        const int uf = __shfl_sync(kFull, lane == 0 ? ld_volatile(&ts->unfilled) : 1, 0);
+        if (uf == 0 && (!refreshed || any_win)) {
+            refresh_bound<F32>(c);
+            refreshed = true;
+            if (c.gbound32 && lane == 0) {   // grid mode: publish this CTA's q_max bound
+                atomicMin((int *)c.gbound32, __float_as_int(ld_volatile(&ts->bound32)));
+                if constexpr (!F32) atomicMin(c.gbound64, (unsigned long long)__double_as_longlong(ld_volatile(&ts->bound64)));
+            }
+        }
+    }
+    {
+        const int rest = ws->sb_n;
+        __syncwarp();
+        if (rest > 0) process_survivors<FAM, F32>(c, rest);
+    }
+}
+
 // ------------------------------------------------------------ one item
 template <int FAM, bool F32, bool CTA_TEAM>
 __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
@@ -734,7 +868,6 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
     t_ph = clock64();
 
     // ---- rounds
-    const float te_lo = (FAM >= 3) ? P.tab.te_lo : 1.0f;
     for (int round = 0; round <= P.rounds; ++round) {
         if (leader) {
             if (round < P.rounds && !isinf(ts->t_s)) {
@@ -746,72 +879,8 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
             }
         }
         if (round > 0) count(c, PMH_CNT_ROUNDS, leader);
-        if (lane == 0) ws->sb_n = 0;
         team_sync<CTA_TEAM>();
-        bool refreshed = false;
-        for (uint32_t base = tw * 64; base < c.n; base += team_warps * 64) {
-            // filter two elements per lane: the log-free lower bound of the first point
-            bool surv[2];
-            uint64_t key[2];
-            uint32_t ev[2];
-            bool valid[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t e = base + 32 * h + lane;
-                ev[h] = e;
-                surv[h] = false;
-                key[h] = 0;
-                valid[h] = false;
-                if (e < c.n) {
-                    const double w = P.weights[c.beg + e];
-                    if (weight_positive(w)) {
-                        valid[h] = true;
-                        key[h] = mix64(P.ids[c.beg + e] ^ P.mixed_seed);
-                        const float xlo = winv_scaled(w, c.sigma) * unif_lo(value_word(key[h], 1)) * te_lo;
-                        surv[h] = !(xlo * (1.0f - 8.0f * 0x1p-24f) > ld_volatile(&ts->bound32));
-                    }
-                }
-            }
-            int n = ws->sb_n;
-            unsigned nvalid = 0, nsurv = 0;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const unsigned msk = __ballot_sync(kFull, surv[h]);
-                if (surv[h]) {
-                    const int pos = n + __popc(msk & ((1u << lane) - 1u));
-                    if (pos < kSurvCap) {   // always true: n <= kSurvBatch - 1 before the two appends of <= 32
-                        ws->sb_e[pos] = ev[h];
-                        ws->sb_key[pos] = key[h];
-                    } else {
-                        ts->status = PMH_ERR_ITER_LIMIT;
-                    }
-                }
-                n = min(n + __popc(msk), kSurvCap);
-                nsurv += __popc(msk);
-                nvalid += popc_ballot(valid[h]);
-            }
-            count(c, PMH_CNT_ELEMENTS, nvalid);
-            count(c, PMH_CNT_PREFILTERED, nvalid - nsurv);
-            __syncwarp();
-            bool any_win = false;
-            if (n >= kSurvBatch) {
-                any_win = process_survivors<FAM, F32>(c, n);
-                n = 0;
-            }
-            if (lane == 0) ws->sb_n = n;
-            __syncwarp();
-            // refresh q_max once everything is filled
-            const int uf = __shfl_sync(kFull, lane == 0 ? ld_volatile(&ts->unfilled) : 1, 0);
-            if (uf == 0 && (!refreshed || any_win)) {
-                refresh_bound<F32>(c);
-                refreshed = true;
-            }
-        }
-        {
-            const int rest = ws->sb_n;
-            __syncwarp();
-            if (rest > 0) process_survivors<FAM, F32>(c, rest);
-        }
+        run_range<FAM, F32, CTA_TEAM>(c, 0, c.n);
         team_sync<CTA_TEAM>();
         count(c, PMH_CNT_CYC_FIRST, (unsigned long long)(clock64() - t_ph));
         t_ph = clock64();
@@ -859,6 +928,256 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
     count(c, PMH_CNT_CYC_FINISH, (unsigned long long)(clock64() - t_ph));
 }
 
+// ------------------------------------------------------------ grid mode
+// Merges a CTA-local FP32 key into the item's global signature (atomicMin),
+// logging both sides as contenders when they are within the error bound of
+// each other (same rule as an offer).
+__device__ __forceinline__ void merge_key_global(uint64_t *gsig, uint32_t k, uint64_t key, GridState *g) {
+    const uint64_t cur = ld_volatile(&gsig[k]);
+    const float x32 = __uint_as_float((uint32_t)(key >> 32));
+    if (cur != kEmptyKey && __uint_as_float((uint32_t)(cur >> 32)) < x32 * (1.0f - 2.0f * kEta)) return;
+    const uint64_t old = atomicMin((unsigned long long *)&gsig[k], (unsigned long long)key);
+    if (old == kEmptyKey) return;
+    const float xo = __uint_as_float((uint32_t)(old >> 32));
+    const uint32_t e = (uint32_t)(key & 0xFFFFFFFFu), eo = (uint32_t)(old & 0xFFFFFFFFu);
+    if (eo != e && fabsf(x32 - xo) <= kEta * (x32 + xo)) {
+        const int at = atomicAdd(&g->cont_n, 2);
+        if (at + 1 < kGridCont) {
+            g->cont_k[at] = k; g->cont_e[at] = e;
+            g->cont_k[at + 1] = k; g->cont_e[at + 1] = eo;
+        }
+    }
+}
+
+// Merges a CTA-local (q, id) record into the item's global FP64 signature
+// (lexicographic minimum by 128-bit CAS).
+__device__ __forceinline__ void merge_rec_global(Rec64 *gsig, uint32_t k, Rec64 r, GridState *g) {
+    if (isinf(r.q)) return;
+    Rec64 expected;
+    expected.q = ld_volatile(&gsig[k].q);
+    if (r.q > expected.q) return;
+    expected.id = ld_volatile((const uint64_t *)&gsig[k].id);
+    for (int it = 0; it < kCasLimit; ++it) {
+        if (!(r.q < expected.q || (r.q == expected.q && r.id < expected.id))) return;
+        Rec64 old = atomicCAS(&gsig[k], expected, r);
+        if (__double_as_longlong(old.q) == __double_as_longlong(expected.q) && old.id == expected.id) return;
+        expected = old;
+    }
+    g->status = PMH_ERR_ITER_LIMIT;
+}
+
+// Finalisation by the last CTA of a grid item: exact resolution of the logged
+// contenders (FP32), write-out, and a single-CTA rerun with growing
+// thresholds if a component is still empty (probability ~e^-c per item).
+template <int FAM, bool F32>
+__device__ void grid_finalize(Ctx<F32> &c, GridState *g, void *gsig_v, int item_v, int64_t set) {
+    const SketchParams &P = *c.p;
+    const uint32_t m = P.m;
+    const int lane = threadIdx.x & 31;
+    const int tw = threadIdx.x >> 5;
+    const int team_warps = blockDim.x >> 5;
+    const int64_t out_row = (int64_t)item_v * P.num_sets + set;
+    TeamShared *ts = c.ts;
+    int st = ld_volatile(&g->status);
+    if constexpr (F32) {
+        uint64_t *gsig = (uint64_t *)gsig_v;
+        const int nc = ld_volatile(&g->cont_n);
+        if (nc > kGridCont && st == PMH_OK) st = PMH_ERR_ITER_LIMIT;
+        if (tw == 0 && nc > 0 && st == PMH_OK) {
+            const uint32_t ev = resolve_list<FAM>(c, g->cont_k, g->cont_e, min(nc, kGridCont), gsig);
+            count(c, PMH_CNT_RESOLVED, ev);
+        }
+    }
+    __syncthreads();
+    // a component left empty: redo the item in this CTA with growing thresholds
+    int empty = 0;
+    for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
+        if constexpr (F32) empty |= __ldcg(&((const unsigned long long *)gsig_v)[k]) == kEmptyKey;
+        else empty |= isinf(__ldcg(&((const Rec64 *)gsig_v)[k].q));
+    }
+    empty = __syncthreads_or(empty);
+    if (empty && st == PMH_OK) {
+        c.gbound32 = nullptr;
+        c.gbound64 = nullptr;
+        process_item<FAM, F32, true>(c, item_v, set);
+        return;
+    }
+    if constexpr (F32) {
+        // L2 loads: other CTAs wrote the global signature
+        const unsigned long long *gsig = (const unsigned long long *)gsig_v;
+        for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
+            const uint64_t key = __ldcg(&gsig[k]);
+            P.out_ids[out_row * m + k] = (key == kEmptyKey || st != PMH_OK) ? 0 : P.ids[c.beg + (uint32_t)(key & 0xFFFFFFFFu)];
+        }
+        if (P.out_q) {
+            for (uint32_t k = tw; k < m; k += team_warps) {
+                const uint64_t key = __ldcg(&gsig[k]);
+                double q = __longlong_as_double(0x7FF0000000000000ll);
+                if (key != kEmptyKey && st == PMH_OK) q = exact_h<FAM, F32>(c, (uint32_t)(key & 0xFFFFFFFFu), k);
+                if (lane == 0) P.out_q[out_row * m + k] = q;
+            }
+        }
+    } else {
+        const Rec64 *gsig = (const Rec64 *)gsig_v;
+        for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
+            Rec64 r;
+            r.q = __ldcg(&gsig[k].q);
+            r.id = __ldcg((const unsigned long long *)&gsig[k].id);
+            const bool ok = st == PMH_OK && !isinf(r.q);
+            P.out_ids[out_row * m + k] = ok ? r.id : 0;
+            if (P.out_q) P.out_q[out_row * m + k] = ok ? r.q : __longlong_as_double(0x7FF0000000000000ll);
+        }
+    }
+    if (threadIdx.x == 0 && P.status) P.status[out_row] = st;
+    (void)ts;
+}
+
+// One CTA's share of a grid item: chunks of the item's elements with a local
+// signature, then the merge into the global signature; the last CTA to
+// finish finalises the item.
+template <int FAM, bool F32>
+__device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int item_v, int64_t set) {
+    const SketchParams &P = *c.p;
+    const uint32_t m = P.m;
+    TeamShared *ts = c.ts;
+    const bool leader = threadIdx.x == 0;
+    const SetStat st0 = P.stats[set];
+    const bool live = !st0.bad && st0.npos > 0;
+    for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
+        if constexpr (F32) ((uint64_t *)c.sig)[k] = kEmptyKey;
+        else { ((Rec64 *)c.sig)[k].q = __longlong_as_double(0x7FF0000000000000ll); ((Rec64 *)c.sig)[k].id = 0; }
+    }
+    if (leader) {
+        ts->status = PMH_OK;
+        ts->unfilled = (int)m;
+        ts->cont_n = 0;
+        int sigma = 0;
+        float t_s = __int_as_float(0x7F800000);
+        const double T = (double)m * (double)P.t_factor_grid / st0.wsum;
+        if (live && T > 0.0 && T < 1e300) {
+            int ex;
+            const double fr = frexp(T, &ex);
+            t_s = (float)(2.0 * fr);
+            sigma = -(ex - 1);
+        }
+        ts->sigma = sigma;
+        ts->t_s = t_s;
+        ts->bound32 = t_s;
+        ts->bound64 = isinf(t_s) ? __longlong_as_double(0x7FF0000000000000ll) : ldexp((double)t_s, -sigma);
+        if (st0.bad && g->status == PMH_OK) g->status = PMH_ERR_BAD_WEIGHT;
+    }
+    __syncthreads();
+    c.sigma = ts->sigma;
+    c.gbound32 = &g->bound32;
+    c.gbound64 = &g->bound64;
+    if (live) {
+        uint64_t chunk = (uint64_t)c.n / (4ull * gridDim.x);
+        chunk = chunk < kGridChunkMin ? kGridChunkMin : (chunk > kGridChunk ? kGridChunk : chunk);
+        for (;;) {
+            if (leader) ts->item_idx = (int)atomicAdd(&g->next_chunk, 1u);
+            __syncthreads();
+            const uint64_t lo = (uint64_t)(uint32_t)ts->item_idx * chunk;
+            __syncthreads();
+            if (lo >= c.n) break;
+            const uint32_t hi = (uint32_t)min((uint64_t)c.n, lo + chunk);
+            run_range<FAM, F32, true>(c, (uint32_t)lo, hi);
+            __syncthreads();
+        }
+        // merge the local signature into the item's global one
+        for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
+            if constexpr (F32) {
+                const uint64_t key = ((const uint64_t *)c.sig)[k];
+                if (key != kEmptyKey) merge_key_global((uint64_t *)gsig_v, k, key, g);
+            } else {
+                merge_rec_global((Rec64 *)gsig_v, k, ((const Rec64 *)c.sig)[k], g);
+            }
+        }
+        if (leader) {
+            // local contenders join the item's list
+            const int nl = ts->cont_n;
+            if (nl > kMaxCont) g->status = PMH_ERR_ITER_LIMIT;
+            const int nk = min(nl, kMaxCont);
+            if (nk > 0) {
+                const int at = atomicAdd(&g->cont_n, nk);
+                for (int j = 0; j < nk && at + j < kGridCont; ++j) { g->cont_k[at + j] = ts->cont_k[j]; g->cont_e[at + j] = ts->cont_e[j]; }
+            }
+            if (ts->status != PMH_OK) g->status = ts->status;
+        }
+    }
+    __syncthreads();
+    __threadfence();
+    if (leader) ts->item_idx = (atomicAdd(&g->done, 1u) == gridDim.x - 1) ? 1 : 0;
+    __syncthreads();
+    const bool last = ts->item_idx == 1;
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        grid_finalize<FAM, F32>(c, g, gsig_v, item_v, set);
+    }
+    c.gbound32 = nullptr;
+    c.gbound64 = nullptr;
+}
+
+// Persistent grid-mode kernel of one family: every CTA takes part in every
+// grid item of that family, in list order.
+template <bool F32, int FAM>
+__global__ void __launch_bounds__(256, 2) grid_kernel(SketchParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr bool kPerm = (FAM == 2 || FAM == 4);
+    constexpr int NW = 8;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    if (!p.gctl) return;
+    const int count_all = (int)ld_volatile((const int *)&p.gctl->count[FAM - 1]);
+    const int nitems = min(count_all, kMaxGrid);
+    if (nitems == 0) return;
+    SmemLayout L(1, NW, p.m, F32, kPerm);
+    Ctx<F32> c;
+    c.p = &p;
+    c.ts = (TeamShared *)(smem + L.team_off);
+    c.sig = smem + L.sig_off;
+    c.ws = (WarpShared *)(smem + L.warp_off + (size_t)warp * align16(sizeof(WarpShared)));
+    c.perm = kPerm ? (uint16_t *)(smem + L.perm_off + (size_t)warp * perm_bytes(p.m)) : nullptr;
+    c.fy = kPerm ? (uint32_t *)(smem + L.perm_off + (size_t)warp * perm_bytes(p.m) + align16((size_t)p.m * 2)) : nullptr;
+    c.gbound32 = nullptr;
+    c.gbound64 = nullptr;
+    if (lane < PMH_NUM_COUNTERS) c.ws->cnt[lane] = 0;
+    __syncwarp();
+    for (int j = 0; j < nitems; ++j) {
+        const uint64_t it = p.gctl->list[FAM - 1][j];
+        const int v = (int)(it >> 40);
+        const int64_t set = (int64_t)(it & ((1ull << 40) - 1));
+        const int slot = (FAM - 1) * kMaxGrid + j;
+        c.beg = p.offsets[set];
+        c.n = (uint32_t)(p.offsets[set + 1] - c.beg);
+        grid_participate<FAM, F32>(c, &p.gstate[slot], (unsigned char *)p.gsig + (size_t)slot * p.m * 16, v, set);
+        __syncthreads();
+    }
+    __syncwarp();
+    if (p.counters && lane < PMH_NUM_COUNTERS && c.ws->cnt[lane]) atomicAdd(&p.counters[lane], c.ws->cnt[lane]);
+}
+
+// Resets the state and global signature of the grid items of this call.
+static __global__ void grid_init_kernel(GridCtl *ctl, GridState *gs, void *gsig, uint32_t m, int f32) {
+    const int slot = blockIdx.x;   // [4][kMaxGrid]
+    const int fam = slot / kMaxGrid, j = slot % kMaxGrid;
+    if (j >= min((int)ctl->count[fam], kMaxGrid)) return;
+    GridState *g = &gs[slot];
+    if (threadIdx.x == 0) {
+        g->next_chunk = 0;
+        g->done = 0;
+        g->bound32 = 0x7F800000u;
+        g->status = PMH_OK;
+        g->bound64 = 0x7FF0000000000000ull;
+        g->cont_n = 0;
+    }
+    unsigned char *sig = (unsigned char *)gsig + (size_t)slot * m * 16;
+    for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
+        if (f32) ((uint64_t *)sig)[k] = kEmptyKey;
+        else { ((Rec64 *)sig)[k].q = __longlong_as_double(0x7FF0000000000000ll); ((Rec64 *)sig)[k].id = 0; }
+    }
+}
+
 // ------------------------------------------------------------ kernel
 template <bool F32, int NW, bool CTA_TEAM, int FAM>
 __global__ void __launch_bounds__(NW * 32, CTA_TEAM ? 2 : 5) sketch_kernel(SketchParams p) {
@@ -877,6 +1196,8 @@ __global__ void __launch_bounds__(NW * 32, CTA_TEAM ? 2 : 5) sketch_kernel(Sketc
     c.ws = (WarpShared *)(smem + L.warp_off + (size_t)warp * align16(sizeof(WarpShared)));
     c.perm = kPerm ? (uint16_t *)(smem + L.perm_off + (size_t)warp * perm_bytes(p.m)) : nullptr;
     c.fy = kPerm ? (uint32_t *)(smem + L.perm_off + (size_t)warp * perm_bytes(p.m) + align16((size_t)p.m * 2)) : nullptr;
+    c.gbound32 = nullptr;
+    c.gbound64 = nullptr;
     if (lane < PMH_NUM_COUNTERS) c.ws->cnt[lane] = 0;
     __syncwarp();
     const bool team_leader = CTA_TEAM ? (threadIdx.x == 0) : (lane == 0);
@@ -887,6 +1208,7 @@ __global__ void __launch_bounds__(NW * 32, CTA_TEAM ? 2 : 5) sketch_kernel(Sketc
         team_sync<CTA_TEAM>();
         if (qi >= p.queue_len) break;
         const uint64_t it = p.queue[qi];
+        if (it & kSkipBit) continue;     // processed in grid mode
         const int v = (int)(it >> 40);
         const int64_t set = (int64_t)(it & ((1ull << 40) - 1));
         const int64_t b = p.offsets[set], e = p.offsets[set + 1];

@@ -23,7 +23,8 @@ FP64, FP32_RECHECK = 0, 1
 COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "rounds", "deep", "prefiltered",
             "cyc_pass0", "cyc_first", "cyc_deep", "cyc_refresh", "cyc_finish", "items", "cyc_surv", "reserved15")
 EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_sketch_batch_noalloc",
-           "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge")
+           "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_last_launches", "pmh_set_thresholds",
+           "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge")
 
 _lib = None
 _lock = threading.Lock()
@@ -60,6 +61,10 @@ def load(path: str = LIB_PATH):
             lib.pmh_set_profiling.argtypes = [vp, i32]
             lib.pmh_last_kernel_ms.restype = i32
             lib.pmh_last_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+            lib.pmh_last_launches.restype = i32
+            lib.pmh_last_launches.argtypes = [vp, ctypes.POINTER(i32)]
+            lib.pmh_set_thresholds.restype = i32
+            lib.pmh_set_thresholds.argtypes = [vp, ctypes.c_double, ctypes.c_double, i32, i64]
             lib.pmh_estimate_allpairs.restype = i32
             lib.pmh_estimate_allpairs.argtypes = [vp, vp, i64, u32, i32, vp, vp]
             lib.pmh_estimate_pairs.restype = i32
@@ -153,6 +158,16 @@ class Handle:
     # -- pmh_set_profiling / pmh_last_kernel_ms ------------------------------
     def set_profiling(self, enable: bool = True):
         self._raise(load().pmh_set_profiling(self._h, 1 if enable else 0))
+
+    def last_launches(self) -> int:
+        """Kernels launched by the most recent sketch_batch call."""
+        n = ctypes.c_int32()
+        self._raise(load().pmh_last_launches(self._h, ctypes.byref(n)))
+        return n.value
+
+    def set_thresholds(self, t_c: float = 4.0, t_c_grid: float = 8.0, rounds: int = 5, grid_min: int = 1 << 20):
+        """Work-only tuning of later sketch_batch calls (results never depend on it)."""
+        self._raise(load().pmh_set_thresholds(self._h, float(t_c), float(t_c_grid), int(rounds), int(grid_min)))
 
     def last_kernel_ms(self):
         """(queue build ms, sketch kernel ms) of the last profiled pmh_sketch_batch call."""

@@ -19,11 +19,9 @@ import torch
 
 import oracle
 from paper_1911_00675_gb300 import workloads as W
+from parity_util import NEAR_REL, Q_RTOL, VARS, check_sets, run, to_dev  # noqa: F401
 
 pytestmark = pytest.mark.gpu
-VARS = ["1", "1a", "2", "3", "3a", "4"]
-NEAR_REL = 1e-12
-Q_RTOL = 1e-10
 
 
 @pytest.fixture(scope="module")
@@ -31,42 +29,6 @@ def H():
     from paper_1911_00675_gb300 import build, pmh
     build.build()
     return pmh.Handle(0)
-
-
-def to_dev(batch):
-    dev = torch.device("cuda", 0)
-    ids = torch.from_numpy(batch.ids.view(np.int64).copy()).to(dev)
-    w = torch.from_numpy(np.ascontiguousarray(batch.weights)).to(dev)
-    off = torch.from_numpy(np.ascontiguousarray(batch.offsets)).to(dev)
-    return ids, w, off
-
-
-def run(H, batch, variants, precision, with_q=True, seed=0, counters=None):
-    from paper_1911_00675_gb300 import pmh
-    ids, w, off = to_dev(batch)
-    z, q, st = H.sketch_batch(ids, w, off, batch.m, variants, precision, seed, with_q=with_q, counters=counters)
-    torch.cuda.synchronize()
-    return (pmh.to_u64(z), q.cpu().numpy() if q is not None else None, st.cpu().numpy())
-
-
-def check_sets(batch, variant, z, q, sets, seed=0, stats=None):
-    """Compares GPU rows z[s], q[s] with the oracle for the listed sets."""
-    m = batch.m
-    for s in sets:
-        ids, w = batch.set(s)
-        qo, zo, _ = oracle.sketch(variant, ids, w, m, seed=seed)
-        diff = np.nonzero(z[s] != zo)[0]
-        if len(diff):
-            flags, _ = oracle.near_ties(variant, ids, w, m, seed, qo, zo, NEAR_REL)
-            assert flags[diff].all(), f"set {s} variant {variant}: {len(diff)} unflagged id mismatches, e.g. k={diff[:5]}"
-            if stats is not None:
-                stats["near"] += int(flags.sum())
-        if stats is not None:
-            stats["components"] += m
-        if q is not None:
-            fin = np.isfinite(qo)
-            assert np.array_equal(np.isfinite(q[s]), fin)
-            np.testing.assert_allclose(q[s][fin], qo[fin], rtol=Q_RTOL, atol=0)
 
 
 SIZES = [0, 1, 2, 3, 5, 31, 32, 33, 64, 100, 257, 1000, 3001]
