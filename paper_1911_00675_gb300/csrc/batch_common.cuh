@@ -129,42 +129,88 @@ static __global__ void queue_scatter(const int64_t *off, int64_t num_sets, int32
 }
 
 // Per-set statistics, computed once per set for all variants: the weight sum
-// (FP64; it only sets the threshold T), the number of positive weights, and a
-// bad-weight flag (negative, NaN, +-inf, or a subnormal whose reciprocal
-// overflows).  One block per set, grid-stride over sets.
+// (it only sets the threshold T, so a ~1e-3 relative error is harmless), the
+// number of positive weights, and a bad-weight flag (negative, NaN, +-inf, or
+// a subnormal whose reciprocal overflows).  One block per set, grid-stride
+// over sets, four loads in flight per thread.
+//
+// The sum avoids FP64 arithmetic (a slow pipe on this GPU): each thread keeps
+// an FP32 accumulator `acc` scaled by 2^-(me-1023), me = the largest biased
+// FP64 exponent it has seen; a weight enters as the FP32 number with its top
+// 23 mantissa bits and exponent shifted by -me (integer operations only), and
+// a larger exponent rescales acc by a power of two.  Weights below 2^-126 of
+// the running maximum (and subnormals) add nothing.
+struct ScaledSum {
+    int me = -1000;   // running maximum biased exponent (none yet)
+    float acc = 0.0f;
+};
+__device__ __forceinline__ float pow2f(int d) {   // 2^d for d in [-126, 0], else 0 below
+    return d >= -126 ? __int_as_float((127 + d) << 23) : 0.0f;
+}
+__device__ __forceinline__ void scaled_add(ScaledSum &s, uint64_t bits) {
+    const int ex = (int)(bits >> 52) & 0x7FF;
+    if (ex > s.me) {
+        s.acc = __fmul_rn(s.acc, pow2f(s.me - ex));
+        s.me = ex;
+    }
+    const int d = ex - s.me;
+    if (d >= -126) s.acc = __fadd_rn(s.acc, __int_as_float(((127 + d) << 23) | (int)((bits >> 29) & 0x7FFFFFu)));
+}
+__device__ __forceinline__ void scaled_merge(ScaledSum &s, int me2, float acc2) {
+    const int M = max(s.me, me2);
+    s.acc = __fadd_rn(__fmul_rn(s.acc, pow2f(s.me - M)), __fmul_rn(acc2, pow2f(me2 - M)));
+    s.me = M;
+}
+
 static __global__ void __launch_bounds__(256) set_stats_kernel(const int64_t *off, const double *w, int64_t num_sets,
                                                                SetStat *out) {
-    __shared__ double ssum[8];
-    __shared__ int snp[8], sbad[8];
+    __shared__ float sacc[8];
+    __shared__ int sme[8], snp[8], sbad[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long *wb = (const unsigned long long *)w;
     for (int64_t s = blockIdx.x; s < num_sets; s += gridDim.x) {
         const int64_t b = off[s], e = off[s + 1];
-        double sum = 0.0;
+        ScaledSum sum;
         int np = 0, bad = 0;
-        for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-            const double x = w[i];
-            const uint64_t bits = (uint64_t)__double_as_longlong(x);
-            const int ex = (int)(bits >> 52) & 0x7FF;
-            const bool neg = (bits >> 63) != 0;
-            if (ex == 0x7FF || (neg && (bits << 1) != 0)) { bad = 1; continue; }
-            if (neg || (bits << 1) == 0) continue;
-            if (ex == 0 && isinf(__drcp_rn(x))) { bad = 1; continue; }
-            sum += x;
-            np++;
+        for (int64_t i0 = b + threadIdx.x; i0 < e; i0 += 4 * (int64_t)blockDim.x) {
+            uint64_t bits[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = i0 + (int64_t)u * blockDim.x;
+                bits[u] = i < e ? (uint64_t)__ldcs(wb + i) : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t x = bits[u];
+                const int ex = (int)(x >> 52) & 0x7FF;
+                const bool neg = (x >> 63) != 0;
+                const bool zero = (x << 1) == 0;
+                if (ex == 0x7FF || (neg && !zero)) { bad = 1; continue; }
+                if (zero) continue;
+                if (ex == 0) {   // subnormal: counted, adds nothing to the sum; bad if 1/w overflows
+                    if (isinf(__drcp_rn(__longlong_as_double((long long)x)))) bad = 1;
+                    else np++;
+                    continue;
+                }
+                scaled_add(sum, x);
+                np++;
+            }
         }
         for (int o = 16; o; o >>= 1) {
-            sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+            const int me2 = __shfl_xor_sync(0xFFFFFFFFu, sum.me, o);
+            const float acc2 = __shfl_xor_sync(0xFFFFFFFFu, sum.acc, o);
+            scaled_merge(sum, me2, acc2);
             np += __shfl_xor_sync(0xFFFFFFFFu, np, o);
             bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, o);
         }
-        if (lane == 0) { ssum[warp] = sum; snp[warp] = np; sbad[warp] = bad; }
+        if (lane == 0) { sacc[warp] = sum.acc; sme[warp] = sum.me; snp[warp] = np; sbad[warp] = bad; }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double S = 0.0;
+            ScaledSum S;
             int N = 0, B = 0;
-            for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { S += ssum[j]; N += snp[j]; B |= sbad[j]; }
+            for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { scaled_merge(S, sme[j], sacc[j]); N += snp[j]; B |= sbad[j]; }
             SetStat r;
-            r.wsum = S;
+            r.wsum = S.me < 0 ? 0.0 : ldexp((double)S.acc, S.me - 1023);
             r.npos = N;
             r.bad = B;
             out[s] = r;

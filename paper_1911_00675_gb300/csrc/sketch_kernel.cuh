@@ -563,6 +563,7 @@ __device__ __forceinline__ uint32_t resolve_contenders(Ctx<true> &c) {
 // Long sequences go to warp-cooperative deep mode instead; so does a
 // sequence that outgrows the lane-sequential cap (the FP32 running sum's error
 // bound holds for at most kSeqCap terms, the write list has kFyCap entries).
+constexpr int kPrefSteps = 4;  // filter: L2 prefetch distance in 64-element steps of a warp
 constexpr int kSeqCap = 32;   // lane-sequential points (ProbMinHash1/2/4)
 constexpr int kSeqCap3 = 64;  // lane-sequential points (ProbMinHash3)
 
@@ -745,6 +746,17 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
                     atomic_min_pos_double(&ts->bound64, __longlong_as_double((long long)ld_volatile((const uint64_t *)c.gbound64)));
             }
             __syncwarp();
+        }
+        // L2 prefetch of this warp's step kPrefSteps ahead (ids and weights: up to
+        // five 128-byte lines each), so that its loads find L2 instead of HBM
+        {
+            const uint32_t pb = base + (uint32_t)(kPrefSteps * team_warps * 64);
+            const int pl = lane < 5 ? lane : lane - 5;
+            const uint32_t pe = pb + (uint32_t)min(pl * 16, 63);
+            if (lane < 10 && pe < hi) {
+                const void *a = lane < 5 ? (const void *)(P.ids + c.beg + pe) : (const void *)(P.weights + c.beg + pe);
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+            }
         }
         // filter two elements per lane: the log-free lower bound of the first point
         bool surv[2];
@@ -1121,7 +1133,7 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
 // Persistent grid-mode kernel of one family: every CTA takes part in every
 // grid item of that family, in list order.
 template <bool F32, int FAM>
-__global__ void __launch_bounds__(256, 2) grid_kernel(SketchParams p) {
+__global__ void __launch_bounds__(256, 2) grid_kernel(const __grid_constant__ SketchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool kPerm = (FAM == 2 || FAM == 4);
     constexpr int NW = 8;
@@ -1180,7 +1192,7 @@ static __global__ void grid_init_kernel(GridCtl *ctl, GridState *gs, void *gsig,
 
 // ------------------------------------------------------------ kernel
 template <bool F32, int NW, bool CTA_TEAM, int FAM>
-__global__ void __launch_bounds__(NW * 32, CTA_TEAM ? 2 : 5) sketch_kernel(SketchParams p) {
+__global__ void __launch_bounds__(NW * 32, CTA_TEAM ? 2 : 5) sketch_kernel(const __grid_constant__ SketchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool kPerm = (FAM == 2 || FAM == 4);
     const int warp = threadIdx.x >> 5;
