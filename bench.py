@@ -41,6 +41,7 @@ OPS_KEY = 20            # element key: mix(id ^ mix(seed))
 OPS_FIRST_REJECT = 26   # value word (20) + log-free lower bound and compare (6)
 OPS_POINT = 60          # value word (20) + label word (20) + logarithm (~10) + scale/compare (5) + offer (5)
 LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes issue one instruction per clock
+OPS_PAIR_COMPONENT = 3  # equal-component count: two 32-bit compares and one add per component pair
 
 
 def parse():
@@ -54,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="wall budget of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the per-kernel measurements beside the headline (huge set, all-pairs counts)")
     return ap.parse_args()
 
 
@@ -100,6 +103,86 @@ def oracle_throughput(batch, seconds, cores, rng_seed=1):
         el = time.perf_counter() - t0
         pool.terminate()
     return done_elems / el, done_elems, done_tasks, el
+
+
+# ------------------------------------------------------------------ peaks
+def measured_peaks():
+    """HBM GB/s and SM clock measured on this GPU type (MEASURED_PEAKS.json), else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "basis": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "basis": "fallback"}
+
+
+def alu_peak(n_sms, sm_mhz):
+    return n_sms * LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ secondary kernels
+def secondary(h, dev, n_sms, sm_mhz, peaks, steps=3):
+    """Per-kernel measurements beside the headline: grid mode on one huge set (HBM-bound) and the
+    all-pairs equal-component count (integer-ALU-bound).  Device time by CUDA events on the stream."""
+    import numpy as np
+    import torch
+    from paper_1911_00675_gb300 import pmh
+    from paper_1911_00675_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    # huge set: 1e8 elements, lognormal(0, 2) weights, m = 4096, ProbMinHash3a, every SM on the one set
+    b5 = W.batch_c5()
+    ids5 = torch.from_numpy(b5.ids.view(np.int64)).to(dev)
+    w5 = torch.from_numpy(b5.weights).to(dev)
+    off5 = torch.from_numpy(b5.offsets).to(dev)
+    del b5
+    z5 = torch.empty((1, 1, 4096), dtype=torch.int64, device=dev)
+    st5 = torch.empty((1, 1), dtype=torch.int32, device=dev)
+    n5 = ids5.numel()
+    res = {}
+    for prec, name, k in ((pmh.FP32_RECHECK, "fp32", steps), (pmh.FP64, "fp64", 1)):
+        ms = timed(lambda: h.sketch_batch(ids5, w5, off5, 4096, ["3a"], prec, 0, out_ids=z5, status=st5), k)
+        res[name] = {"ms": ms, "elements_per_s": n5 / (ms * 1e-3), "status_ok": bool((st5 == 0).all().item())}
+    byt = 16 * n5 + 8 * 4096
+    a = byt / (res["fp32"]["ms"] * 1e-3) / 1e9
+    out["huge_set"] = {"workload": "one set, n=1e8, lognormal(0,2) weights, m=4096, ProbMinHash3a, grid mode",
+                       **res, "roofline": {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                           "frac": a / peaks["hbm_gbs"], "algorithmic_bytes": byt,
+                                           "peak_basis": peaks["basis"]}}
+    del ids5, w5, off5
+
+    # all-pairs counts over 16,384 ProbMinHash3a signatures (m = 1024) of 512 perturbed families
+    b4 = W.batch_c4_sets()
+    ids4 = torch.from_numpy(b4.ids.view(np.int64)).to(dev)
+    w4 = torch.from_numpy(b4.weights).to(dev)
+    off4 = torch.from_numpy(b4.offsets).to(dev)
+    z4, _, st4 = h.sketch_batch(ids4, w4, off4, 1024, ["3a"], pmh.FP32_RECHECK, 0)
+    z4 = z4[0].contiguous()
+    del ids4, w4, off4
+    S4 = z4.shape[0]
+    counts = torch.empty((S4, S4), dtype=torch.int16, device=dev)
+    ms = timed(lambda: h.estimate_allpairs(z4, upper_only=True, counts=counts), steps)
+    pairs = S4 * (S4 + 1) // 2
+    ops = pairs * 1024 * OPS_PAIR_COMPONENT
+    a = ops / (ms * 1e-3) / 1e12
+    pk = alu_peak(n_sms, sm_mhz)
+    out["allpairs"] = {"workload": "16,384 ProbMinHash3a signatures, m=1024, upper triangle with diagonal",
+                       "ms": ms, "pairs_per_s": pairs / (ms * 1e-3),
+                       "roofline": {"bound": "alu", "achieved": a, "peak": pk, "unit": "Tops/s (32-bit lane ops)",
+                                    "frac": a / pk, "ops_per_launch": ops}}
+    return out
 
 
 # ------------------------------------------------------------------ clocks
@@ -322,6 +405,18 @@ def main():
                 "kernel_ms": k_avg, "ops_per_launch": per_launch_ops,
                 "peak_basis": f"{n_sms} SMs x {LANES_PER_SM_CLK} lane-ops/clk x {sm_mhz:.0f} MHz (median under load)"}
 
+    # ---------------- queue build + set statistics: one read of offsets (x3) and weights
+    peaks = measured_peaks()
+    q_avg = statistics.mean(queue_ms)
+    q_bytes = 8 * n_elem + 3 * 8 * (S + 1) + 8 * S * len(VARIANTS)
+    qa = q_bytes / (q_avg * 1e-3) / 1e9
+    queue_roof = {"bound": "hbm", "achieved": qa, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": qa / peaks["hbm_gbs"],
+                  "algorithmic_bytes": q_bytes, "ms": q_avg, "peak_basis": peaks["basis"]}
+
+    sec = None
+    if not args.no_secondary:
+        sec = secondary(h, dev, n_sms, sm_mhz, peaks)
+
     # ---------------- CPU baseline (rank 0, N=1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -347,6 +442,8 @@ def main():
             "counters": c,
             "queue_build_ms": statistics.mean(queue_ms),
             "roofline": roofline,
+            "queue_build_roofline": queue_roof,
+            "secondary": sec,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,   # as reported by the library for each call
