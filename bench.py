@@ -413,9 +413,9 @@ def main():
     queue_roof = {"bound": "hbm", "achieved": qa, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": qa / peaks["hbm_gbs"],
                   "algorithmic_bytes": q_bytes, "ms": q_avg, "peak_basis": peaks["basis"]}
 
-    sec = None
+    sec_res = None
     if not args.no_secondary:
-        sec = secondary(h, dev, n_sms, sm_mhz, peaks)
+        sec_res = secondary(h, dev, n_sms, sm_mhz, peaks)
 
     # ---------------- CPU baseline (rank 0, N=1 only)
     cpu = None
@@ -443,7 +443,7 @@ def main():
             "queue_build_ms": statistics.mean(queue_ms),
             "roofline": roofline,
             "queue_build_roofline": queue_roof,
-            "secondary": sec,
+            "secondary": sec_res,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,   # as reported by the library for each call

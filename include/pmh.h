@@ -178,6 +178,44 @@ pmh_status pmh_set_profiling(pmh_handle h, int32_t enable);
 pmh_status pmh_last_kernel_ms(pmh_handle h, float *queue_ms, float *sketch_ms);
 
 /*
+ * Team shapes of the persistent sketch kernel (no counterpart in the paper:
+ * how GPU threads share one item).  A team of warps shares one signature in
+ * shared memory and sketches one (set, variant) item at a time:
+ *   PMH_SHAPE_WARP  4 warps per block, each warp its own team
+ *   PMH_SHAPE_CTA8  8 warps per block, one team
+ *   PMH_SHAPE_QUAD  4 warps per block, one team (register budget for 8 blocks/SM)
+ *   PMH_SHAPE_PAIR  8 warps per block, teams of 2 warps
+ *   PMH_SHAPE_QUAD8 8 warps per block, teams of 4 warps
+ *   PMH_SHAPE_QUAD8L the same with the register budget for 5 blocks/SM
+ * All shapes return identical results.
+ *
+ * pmh_set_team_shape(h, family, shape): family 1..4 (ProbMinHash1/1a, 2,
+ * 3/3a, 4) or 0 for all; shape one of the above, or -1 to let the handle
+ * choose.  A shape whose shared memory does not fit falls back to the default
+ * rule (warp teams when 12 warps per SM fit, else CTA8).
+ *
+ * pmh_set_autotune(h, enable): with enable = 1 (the default), the first
+ * pmh_sketch_batch for a new (m, precision, family, log2 of the item count)
+ * runs the batch once per shape on the caller's stream, waits for it, and keeps
+ * the fastest shape per family for later calls; not during stream capture
+ * (the default rule applies there).  enable = 0 uses the default rule;
+ * enable = -1 also forgets the shapes chosen so far and keeps tuning on.
+ *
+ * pmh_last_team_shapes(h, shapes): host int32[4], the shape each family used
+ * in the most recent call (-1 for families it did not have).
+ * Errors: PMH_ERR_INVALID_ARG for a NULL handle or pointer or values out of range.
+ */
+#define PMH_SHAPE_WARP 0
+#define PMH_SHAPE_CTA8 1
+#define PMH_SHAPE_QUAD 2
+#define PMH_SHAPE_PAIR 3
+#define PMH_SHAPE_QUAD8 4
+#define PMH_SHAPE_QUAD8L 5
+pmh_status pmh_set_team_shape(pmh_handle h, int32_t family, int32_t shape);
+pmh_status pmh_set_autotune(pmh_handle h, int32_t enable);
+pmh_status pmh_last_team_shapes(pmh_handle h, int32_t *shapes);
+
+/*
  * pmh_last_launches -- number of kernels the most recent pmh_sketch_batch on
  * `h` launched (queue build, statistics, per-family sketch kernels and, when
  * grid mode is on, its reset kernel and per-family grid kernels).

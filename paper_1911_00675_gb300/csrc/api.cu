@@ -30,7 +30,18 @@ struct GraphKey {
     int32_t variants[8];
     int32_t num_variants, precision, profiling;
     uint64_t seed;
+    int32_t kinds[4];
     bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(*this)) == 0; }
+};
+
+// Autotuning key: the batch shape as the host sees it (the set sizes live on
+// the device), per family.
+struct TuneKey {
+    uint32_t m;
+    int32_t precision, family, items_log2;
+    bool operator<(const TuneKey &o) const {
+        return std::memcmp(this, &o, sizeof(*this)) < 0;
+    }
 };
 
 }  // namespace
@@ -56,6 +67,11 @@ struct pmh_handle_s {
     // planner knobs (tunable)
     Thresholds th;
     int last_launches = 0;
+    int force_shape[4] = {-1, -1, -1, -1};   // per family: TeamShape, or -1
+    int last_shape[4] = {-1, -1, -1, -1};    // shapes of the most recent call (-1: family absent)
+    bool autotune = true;
+    std::map<TuneKey, int> tuned;            // best TeamShape per key
+    cudaEvent_t tev[3 + 4] = {};             // autotuning: queue/sketch brackets + one per family
     // profiling events
     bool profiling = false;
     bool prof_recorded = false;
@@ -179,6 +195,7 @@ extern "C" void pmh_destroy(pmh_handle h) {
     cudaDeviceSynchronize();
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     for (int i = 0; i < 3; i++) if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    for (int i = 0; i < 7; i++) if (h->tev[i]) cudaEventDestroy(h->tev[i]);
     for (auto &kv : h->tables) cudaFree(kv.second.dev);
     if (h->queue) cudaFree(h->queue);
     if (h->qmeta) cudaFree(h->qmeta);
@@ -213,6 +230,33 @@ extern "C" pmh_status pmh_set_thresholds(pmh_handle h, double t_c, double t_c_gr
     return PMH_OK;
 }
 
+extern "C" pmh_status pmh_set_team_shape(pmh_handle h, int32_t family, int32_t shape) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    if (family < 0 || family > 4) return fail(h, PMH_ERR_INVALID_ARG, "family %d outside [0, 4]", family);
+    if (shape < -1 || shape >= kNumShapes) return fail(h, PMH_ERR_INVALID_ARG, "shape %d outside [-1, %d]", shape, kNumShapes - 1);
+    for (int f = 1; f <= 4; f++)
+        if (family == 0 || family == f) h->force_shape[f - 1] = shape;
+    h->graph_valid = false;
+    return PMH_OK;
+}
+
+extern "C" pmh_status pmh_set_autotune(pmh_handle h, int32_t enable) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    h->autotune = enable != 0;
+    if (enable < 0) h->tuned.clear();
+    h->graph_valid = false;
+    return PMH_OK;
+}
+
+extern "C" pmh_status pmh_last_team_shapes(pmh_handle h, int32_t *shapes) {
+    if (!h || !shapes) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    for (int f = 0; f < 4; f++) shapes[f] = h->last_shape[f];
+    return PMH_OK;
+}
+
 extern "C" pmh_status pmh_last_launches(pmh_handle h, int32_t *launches) {
     if (!h || !launches) return PMH_ERR_INVALID_ARG;
     h->err.clear();
@@ -230,6 +274,46 @@ extern "C" pmh_status pmh_last_kernel_ms(pmh_handle h, float *queue_ms, float *s
     CUDA_TRY(h, cudaEventElapsedTime(&b, h->ev[1], h->ev[2]));
     if (queue_ms) *queue_ms = a;
     if (sketch_ms) *sketch_ms = b;
+    return PMH_OK;
+}
+
+// Times every team shape on this batch (one full run each, on `st`, blocking)
+// and records the fastest per family.  All runs write the same results.
+static pmh_status autotune_shapes(pmh_handle h, SketchParams p, uint32_t m, const int32_t *variants,
+                                  int32_t num_variants, int64_t num_sets, int precision, cudaStream_t st,
+                                  int *kinds, const TuneKey *tkey) {
+    if (!h->tev[0])
+        for (int i = 0; i < 7; i++) CUDA_TRY(h, cudaEventCreate(&h->tev[i]));
+    float best[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+    int best_kind[4] = {-1, -1, -1, -1};
+    for (int cand = 0; cand < kNumShapes; cand++) {
+        int ck[4];
+        for (int f = 0; f < 4; f++) ck[f] = kinds[f] >= 0 ? kinds[f] : cand;
+        Plan plan;
+        bool fits = true;
+        cudaError_t e = plan_batch(h->sm_count, precision, m, variants, num_variants, num_sets, ck, &plan, &fits);
+        if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
+        if (!fits) continue;
+        SketchParams q = p;
+        for (int j = 0; j < plan.nfam && q.gctl; j++)
+            if (plan.ggrid[j] <= 0) { q.gctl = nullptr; q.gstate = nullptr; q.gsig = nullptr; }
+        e = enqueue_batch(q, plan, precision, h->sm_count, h->queue, h->qmeta, h->stats, st, h->tev, h->tev + 3);
+        if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(e));
+        CUDA_TRY(h, cudaEventSynchronize(h->tev[2]));
+        for (int j = 0; j < plan.nfam; j++) {
+            const int f = plan.fam[j] - 1;
+            if (kinds[f] >= 0 || plan.shape[j].kind != cand) continue;   // forced, or the candidate did not fit
+            float ms = 0.0f;
+            CUDA_TRY(h, cudaEventElapsedTime(&ms, j == 0 ? h->tev[1] : h->tev[3 + j - 1], h->tev[3 + j]));
+            if (ms < best[f]) { best[f] = ms; best_kind[f] = cand; }
+        }
+    }
+    for (int f = 0; f < 4; f++)
+        if (kinds[f] < 0 && best_kind[f] >= 0) {
+            kinds[f] = best_kind[f];
+            h->tuned[tkey[f]] = best_kind[f];
+        }
+    h->graph_valid = false;
     return PMH_OK;
 }
 
@@ -273,9 +357,32 @@ extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const 
     p.tab = tab;
     if (h->th.grid_min > 0) bind_grid_scratch(&p, h->grid);
     (void)has_perm;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (st) CUDA_TRY(h, cudaStreamIsCapturing(st, &cs));
+    // team shape per family: forced, else tuned, else (tuning off or impossible) the default rule
+    int kinds[4];
+    TuneKey tkey[4];
+    bool need_tune = false;
+    {
+        int64_t per_fam[4] = {0, 0, 0, 0};
+        for (int v = 0; v < num_variants; v++) per_fam[family_of(variants[v]) - 1] += num_sets;
+        for (int f = 0; f < 4; f++) {
+            tkey[f] = TuneKey{m, precision, f + 1, per_fam[f] > 0 ? 63 - __builtin_clzll((unsigned long long)per_fam[f]) : -1};
+            kinds[f] = h->force_shape[f];
+            if (kinds[f] < 0 && per_fam[f] > 0) {
+                auto it = h->tuned.find(tkey[f]);
+                if (it != h->tuned.end()) kinds[f] = it->second;
+                else need_tune = true;
+            }
+        }
+    }
+    if (need_tune && h->autotune && cs == cudaStreamCaptureStatusNone) {
+        rc = autotune_shapes(h, p, m, variants, num_variants, num_sets, precision, st, kinds, tkey);
+        if (rc) return rc;
+    }
     Plan plan;
     bool fits = true;
-    cudaError_t pe = plan_batch(h->sm_count, precision, m, variants, num_variants, num_sets, &plan, &fits);
+    cudaError_t pe = plan_batch(h->sm_count, precision, m, variants, num_variants, num_sets, kinds, &plan, &fits);
     if (pe != cudaSuccess) return fail(h, PMH_ERR_CUDA, "occupancy: %s", cudaGetErrorString(pe));
     if (!fits) return fail(h, PMH_ERR_UNSUPPORTED, "m = %u does not fit in shared memory", m);
     // grid mode only when every family's grid kernel can be resident (items it
@@ -283,8 +390,8 @@ extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const 
     for (int j = 0; j < plan.nfam && p.gctl; j++)
         if (plan.ggrid[j] <= 0) { p.gctl = nullptr; p.gstate = nullptr; p.gsig = nullptr; }
     h->last_launches = launch_count(plan, p.gctl != nullptr);
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (st) CUDA_TRY(h, cudaStreamIsCapturing(st, &cs));
+    for (int f = 0; f < 4; f++) h->last_shape[f] = -1;
+    for (int j = 0; j < plan.nfam; j++) h->last_shape[plan.fam[j] - 1] = plan.shape[j].kind;
     if (!h->use_graph || cs != cudaStreamCaptureStatusNone || !st) {
         h->prof_recorded = h->profiling;
         return enqueue_sketch(h, p, plan, precision, st);
@@ -296,6 +403,7 @@ extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const 
     for (int v = 0; v < num_variants; v++) key.variants[v] = variants[v];
     key.num_variants = num_variants; key.precision = precision; key.seed = seed;
     key.profiling = h->profiling ? 1 : 0;
+    for (int f = 0; f < 4; f++) key.kinds[f] = kinds[f];
     h->prof_recorded = h->profiling;
     if (!(h->graph_valid && h->gkey == key)) {
         if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }

@@ -234,8 +234,11 @@ struct Plan {
 };
 
 // Returns cudaSuccess and sets *fits = false when m does not fit in shared memory.
+// kinds[f-1]: team shape for family f (TeamShape), or -1 for the default
+// rule: teams of 2 warps when 16 warps per SM fit, else warp teams when 12
+// fit, else CTA teams of 8 (the autotuner picks among all shapes).
 inline cudaError_t plan_batch(int sm_count, int precision, uint32_t m, const int32_t *variants, int nv,
-                              int64_t num_sets, Plan *out, bool *fits) {
+                              int64_t num_sets, const int *kinds, Plan *out, bool *fits) {
     const bool f32 = precision == PMH_FP32_RECHECK;
     int64_t per_fam[4] = {0, 0, 0, 0};
     for (int v = 0; v < nv; v++) per_fam[family_of(variants[v]) - 1] += num_sets;
@@ -245,19 +248,31 @@ inline cudaError_t plan_batch(int sm_count, int precision, uint32_t m, const int
     for (int f = 1; f <= 4; f++) {
         const int64_t items = per_fam[f - 1];
         if (items == 0) continue;
-        LaunchShape warp_s{}, cta_s{};
-        cudaError_t e = sketch_shape_any(f32, f, false, m, false, &warp_s);
-        if (e != cudaSuccess) return e;
-        LaunchShape shape = warp_s;
-        if (warp_s.blocks_per_sm * 4 < 12) {
-            e = sketch_shape_any(f32, f, true, m, false, &cta_s);
+        LaunchShape shape{};
+        cudaError_t e;
+        const int want = kinds ? kinds[f - 1] : -1;
+        if (want >= 0 && want < kNumShapes) {
+            e = sketch_shape_any(f32, f, want, m, &shape);
             if (e != cudaSuccess) return e;
-            if (cta_s.blocks_per_sm > 0) shape = cta_s;
+        }
+        if (shape.blocks_per_sm <= 0) {
+            LaunchShape pair_s{}, warp_s{}, cta_s{};
+            e = sketch_shape_any(f32, f, kShapePair, m, &pair_s);
+            if (e != cudaSuccess) return e;
+            e = sketch_shape_any(f32, f, kShapeWarp, m, &warp_s);
+            if (e != cudaSuccess) return e;
+            shape = pair_s.blocks_per_sm * 8 >= 16 ? pair_s : warp_s;
+            if (shape.blocks_per_sm * (shape.block / 32) < 12) {
+                e = sketch_shape_any(f32, f, kShapeCta8, m, &cta_s);
+                if (e != cudaSuccess) return e;
+                if (cta_s.blocks_per_sm > 0) shape = cta_s;
+            }
         }
         if (shape.blocks_per_sm <= 0) { *fits = false; return cudaSuccess; }
         int grid = sm_count * shape.blocks_per_sm;
-        const int64_t teams_needed = shape.cta_team ? items : (items + 3) / 4;
-        if (teams_needed < grid) grid = (int)std::max<int64_t>(1, teams_needed);
+        const int teams_per_block = shape.block / 32 / shape.team_warps;
+        const int64_t blocks_needed = (items + teams_per_block - 1) / teams_per_block;
+        if (blocks_needed < grid) grid = (int)std::max<int64_t>(1, blocks_needed);
         const int j = out->nfam++;
         out->fam[j] = f;
         out->qbase[j] = base;
@@ -276,9 +291,11 @@ inline cudaError_t plan_batch(int sm_count, int precision, uint32_t m, const int
 
 // Enqueues queue build, set statistics and one persistent kernel per family
 // on `st`.  `ev` (optional) receives records before the queue build, before
-// the sketch kernels and after them.
+// the sketch kernels and after them; `fam_ev` (optional) one record after
+// each family's kernels, in plan order.
 inline cudaError_t enqueue_batch(SketchParams p, const Plan &plan, int precision, int sm_count, uint64_t *queue,
-                                 unsigned int *qmeta, SetStat *stats, cudaStream_t st, cudaEvent_t *ev) {
+                                 unsigned int *qmeta, SetStat *stats, cudaStream_t st, cudaEvent_t *ev,
+                                 cudaEvent_t *fam_ev = nullptr) {
     const int64_t items = p.num_sets * p.num_variants;
     FamOfVariant fv{};
     for (int v = 0; v < p.num_variants; v++) fv.f[v] = family_of(p.variants[v]);
@@ -308,6 +325,7 @@ inline cudaError_t enqueue_batch(SketchParams p, const Plan &plan, int precision
             e = grid_launch_any(precision == PMH_FP32_RECHECK, plan.fam[j], plan.gshape[j], plan.ggrid[j], p, st);
             if (e != cudaSuccess) return e;
         }
+        if (fam_ev && (e = cudaEventRecord(fam_ev[j], st)) != cudaSuccess) return e;
     }
     if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
     return cudaSuccess;

@@ -115,7 +115,7 @@ extern "C" pmh_status pmh_sketch_batch_noalloc(const uint64_t *ids, const double
     p.tab = tab;
     Plan plan;
     bool fits = true;
-    e = plan_batch(ds.sm_count, precision, m, variants, num_variants, num_sets, &plan, &fits);
+    e = plan_batch(ds.sm_count, precision, m, variants, num_variants, num_sets, nullptr, &plan, &fits);
     if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
     if (!fits) return fail_na(PMH_ERR_UNSUPPORTED, "m = %u does not fit in shared memory", m);
     // enqueue_batch clears the queue metadata; the queue and the statistics are rewritten in full

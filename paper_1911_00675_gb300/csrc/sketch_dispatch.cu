@@ -3,20 +3,20 @@
 
 namespace pmh {
 
-cudaError_t sketch_shape_any(bool f32, int fam, bool cta_team, uint32_t m, bool has_perm, LaunchShape *out) {
+cudaError_t sketch_shape_any(bool f32, int fam, int kind, uint32_t m, LaunchShape *out) {
     if (f32) {
         switch (fam) {
-            case 1: return sketch_shape<true, 1>(cta_team, m, has_perm, out);
-            case 2: return sketch_shape<true, 2>(cta_team, m, has_perm, out);
-            case 3: return sketch_shape<true, 3>(cta_team, m, has_perm, out);
-            default: return sketch_shape<true, 4>(cta_team, m, has_perm, out);
+            case 1: return sketch_shape<true, 1>(kind, m, out);
+            case 2: return sketch_shape<true, 2>(kind, m, out);
+            case 3: return sketch_shape<true, 3>(kind, m, out);
+            default: return sketch_shape<true, 4>(kind, m, out);
         }
     }
     switch (fam) {
-        case 1: return sketch_shape<false, 1>(cta_team, m, has_perm, out);
-        case 2: return sketch_shape<false, 2>(cta_team, m, has_perm, out);
-        case 3: return sketch_shape<false, 3>(cta_team, m, has_perm, out);
-        default: return sketch_shape<false, 4>(cta_team, m, has_perm, out);
+        case 1: return sketch_shape<false, 1>(kind, m, out);
+        case 2: return sketch_shape<false, 2>(kind, m, out);
+        case 3: return sketch_shape<false, 3>(kind, m, out);
+        default: return sketch_shape<false, 4>(kind, m, out);
     }
 }
 

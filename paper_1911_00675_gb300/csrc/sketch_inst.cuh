@@ -5,14 +5,13 @@
 namespace pmh {
 
 namespace {
-template <bool CTA>
-cudaError_t shape_impl(uint32_t m, bool has_perm, LaunchShape *out) {
-    constexpr int NW = CTA ? 8 : 4;
-    const int teams = CTA ? 1 : NW;
-    (void)has_perm;
-    SmemLayout L(teams, NW, m, PMH_F32, PMH_FAM == 2 || PMH_FAM == 4);
-    out->cta_team = CTA;
+template <int S>
+cudaError_t shape_impl(uint32_t m, LaunchShape *out) {
+    constexpr int NW = shape_nw(S), TW = shape_tw(S), MINB = shape_minb(S);
+    SmemLayout L(NW / TW, NW, m, PMH_F32, PMH_FAM == 2 || PMH_FAM == 4);
+    out->kind = S;
     out->block = NW * 32;
+    out->team_warps = TW;
     out->smem = L.total;
     out->blocks_per_sm = 0;
     int dev = 0, optin = 0;
@@ -21,30 +20,48 @@ cudaError_t shape_impl(uint32_t m, bool has_perm, LaunchShape *out) {
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     if (L.total > (size_t)optin) return cudaSuccess;
-    auto kern = sketch_kernel<PMH_F32, NW, CTA, PMH_FAM>;
+    auto kern = sketch_kernel<PMH_F32, NW, TW, MINB, PMH_FAM>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->blocks_per_sm, kern, NW * 32, L.total);
 }
+template <int S>
+void launch_impl(const LaunchShape &s, int grid, const SketchParams &p, cudaStream_t st) {
+    sketch_kernel<PMH_F32, shape_nw(S), shape_tw(S), shape_minb(S), PMH_FAM><<<grid, s.block, s.smem, st>>>(p);
+}
 }  // namespace
 
 template <>
-cudaError_t sketch_shape<PMH_F32, PMH_FAM>(bool cta_team, uint32_t m, bool has_perm, LaunchShape *out) {
-    return cta_team ? shape_impl<true>(m, has_perm, out) : shape_impl<false>(m, has_perm, out);
+cudaError_t sketch_shape<PMH_F32, PMH_FAM>(int kind, uint32_t m, LaunchShape *out) {
+    switch (kind) {
+        case kShapeWarp: return shape_impl<kShapeWarp>(m, out);
+        case kShapeCta8: return shape_impl<kShapeCta8>(m, out);
+        case kShapeQuad: return shape_impl<kShapeQuad>(m, out);
+        case kShapePair: return shape_impl<kShapePair>(m, out);
+        case kShapeQuad8: return shape_impl<kShapeQuad8>(m, out);
+        default: return shape_impl<kShapeQuad8L>(m, out);
+    }
 }
 
 template <>
 cudaError_t sketch_launch<PMH_F32, PMH_FAM>(const LaunchShape &s, int grid, const SketchParams &p, cudaStream_t st) {
-    if (s.cta_team) sketch_kernel<PMH_F32, 8, true, PMH_FAM><<<grid, s.block, s.smem, st>>>(p);
-    else sketch_kernel<PMH_F32, 4, false, PMH_FAM><<<grid, s.block, s.smem, st>>>(p);
+    switch (s.kind) {
+        case kShapeWarp: launch_impl<kShapeWarp>(s, grid, p, st); break;
+        case kShapeCta8: launch_impl<kShapeCta8>(s, grid, p, st); break;
+        case kShapeQuad: launch_impl<kShapeQuad>(s, grid, p, st); break;
+        case kShapePair: launch_impl<kShapePair>(s, grid, p, st); break;
+        case kShapeQuad8: launch_impl<kShapeQuad8>(s, grid, p, st); break;
+        default: launch_impl<kShapeQuad8L>(s, grid, p, st); break;
+    }
     return cudaGetLastError();
 }
 
 template <>
 cudaError_t grid_shape<PMH_F32, PMH_FAM>(uint32_t m, LaunchShape *out) {
     SmemLayout L(1, 8, m, PMH_F32, PMH_FAM == 2 || PMH_FAM == 4);
-    out->cta_team = true;
+    out->kind = kShapeCta8;
     out->block = 256;
+    out->team_warps = 8;
     out->smem = L.total;
     out->blocks_per_sm = 0;
     int dev = 0, optin = 0;

@@ -716,20 +716,27 @@ __device__ bool process_survivors(Ctx<F32> &c, int n) {
 }
 
 // ------------------------------------------------------------ team helpers
-template <bool CTA_TEAM>
+// Barrier of a team of TW warps: the warp itself, or named barrier 1 + team
+// index over the team's TW * 32 threads (barrier 0 stays free for
+// __syncthreads).
+template <int TW>
 __device__ __forceinline__ void team_sync() {
-    if (CTA_TEAM) __syncthreads(); else __syncwarp();
+    if constexpr (TW == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x >> 5) / TW), "n"(TW * 32) : "memory");
+    }
 }
 
 // One pass over the elements [lo, hi) of the current item with the team's
 // current bound: filter, compacted survivors, q_max refreshes.  Every warp of
 // the team takes 64-element steps.
-template <int FAM, bool F32, bool CTA_TEAM>
+template <int FAM, bool F32, int TW>
 __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
     const SketchParams &P = *c.p;
     const int lane = threadIdx.x & 31;
-    const int tw = CTA_TEAM ? (threadIdx.x >> 5) : 0;
-    const int team_warps = CTA_TEAM ? (blockDim.x >> 5) : 1;
+    const int tw = (int)(threadIdx.x >> 5) % TW;
+    constexpr int team_warps = TW;
     TeamShared *ts = c.ts;
     WarpShared *ws = c.ws;
     const float te_lo = (FAM >= 3) ? P.tab.te_lo : 1.0f;
@@ -827,13 +834,13 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
 }
 
 // ------------------------------------------------------------ one item
-template <int FAM, bool F32, bool CTA_TEAM>
+template <int FAM, bool F32, int TW>
 __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
     const SketchParams &P = *c.p;
     const uint32_t m = P.m;
     const int lane = threadIdx.x & 31;
-    const int tw = CTA_TEAM ? (threadIdx.x >> 5) : 0;
-    const int team_warps = CTA_TEAM ? (blockDim.x >> 5) : 1;
+    const int tw = (int)(threadIdx.x >> 5) % TW;
+    constexpr int team_warps = TW;
     const int tt = tw * 32 + lane;
     const int team_threads = team_warps * 32;
     TeamShared *ts = c.ts;
@@ -865,7 +872,7 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
         ts->sigma = sigma;
         ts->t_s = t_s;
     }
-    team_sync<CTA_TEAM>();
+    team_sync<TW>();
     c.sigma = ts->sigma;
     if (st0.bad || st0.npos == 0) {
         // bad weights or empty set: zero ids, +inf q
@@ -891,15 +898,15 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
             }
         }
         if (round > 0) count(c, PMH_CNT_ROUNDS, leader);
-        team_sync<CTA_TEAM>();
-        run_range<FAM, F32, CTA_TEAM>(c, 0, c.n);
-        team_sync<CTA_TEAM>();
+        team_sync<TW>();
+        run_range<FAM, F32, TW>(c, 0, c.n);
+        team_sync<TW>();
         count(c, PMH_CNT_CYC_FIRST, (unsigned long long)(clock64() - t_ph));
         t_ph = clock64();
         if (ld_volatile(&ts->unfilled) == 0 || ld_volatile(&ts->status) != PMH_OK) break;
-        team_sync<CTA_TEAM>();
+        team_sync<TW>();
     }
-    team_sync<CTA_TEAM>();
+    team_sync<TW>();
 
     // ---- FP32: resolve contenders exactly
     if constexpr (F32) {
@@ -908,7 +915,7 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
             count(c, PMH_CNT_RESOLVED, ev);
         }
     }
-    team_sync<CTA_TEAM>();
+    team_sync<TW>();
 
     // ---- write out
     const int st = ld_volatile(&ts->status);
@@ -1011,7 +1018,7 @@ __device__ void grid_finalize(Ctx<F32> &c, GridState *g, void *gsig_v, int item_
     if (empty && st == PMH_OK) {
         c.gbound32 = nullptr;
         c.gbound64 = nullptr;
-        process_item<FAM, F32, true>(c, item_v, set);
+        process_item<FAM, F32, 8>(c, item_v, set);
         return;
     }
     if constexpr (F32) {
@@ -1092,7 +1099,7 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
             __syncthreads();
             if (lo >= c.n) break;
             const uint32_t hi = (uint32_t)min((uint64_t)c.n, lo + chunk);
-            run_range<FAM, F32, true>(c, (uint32_t)lo, hi);
+            run_range<FAM, F32, 8>(c, (uint32_t)lo, hi);
             __syncthreads();
         }
         // merge the local signature into the item's global one
@@ -1191,14 +1198,18 @@ static __global__ void grid_init_kernel(GridCtl *ctl, GridState *gs, void *gsig,
 }
 
 // ------------------------------------------------------------ kernel
-template <bool F32, int NW, bool CTA_TEAM, int FAM>
-__global__ void __launch_bounds__(NW * 32, CTA_TEAM ? 2 : 5) sketch_kernel(const __grid_constant__ SketchParams p) {
+// NW warps per block in teams of TW warps (TW = 1: every warp sketches its own
+// items; TW = NW: the whole block shares one signature); MINB = the blocks per
+// SM the register budget is sized for.
+template <bool F32, int NW, int TW, int MINB, int FAM>
+__global__ void __launch_bounds__(NW * 32, MINB) sketch_kernel(const __grid_constant__ SketchParams p) {
+    static_assert(NW % TW == 0 && NW / TW <= 15, "teams must tile the block (named barriers 1..15)");
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool kPerm = (FAM == 2 || FAM == 4);
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int teams = CTA_TEAM ? 1 : NW;
-    const int team = CTA_TEAM ? 0 : warp;
+    constexpr int teams = NW / TW;
+    const int team = warp / TW;
     SmemLayout L(teams, NW, p.m, F32, kPerm);
     TeamShared *ts = (TeamShared *)(smem + L.team_off + (size_t)team * align16(sizeof(TeamShared)));
     Ctx<F32> c;
@@ -1212,12 +1223,13 @@ __global__ void __launch_bounds__(NW * 32, CTA_TEAM ? 2 : 5) sketch_kernel(const
     c.gbound64 = nullptr;
     if (lane < PMH_NUM_COUNTERS) c.ws->cnt[lane] = 0;
     __syncwarp();
-    const bool team_leader = CTA_TEAM ? (threadIdx.x == 0) : (lane == 0);
+    const int tt = (warp % TW) * 32 + lane;   // thread index within the team
+    const bool team_leader = tt == 0;
     for (;;) {
         if (team_leader) ts->item_idx = (int)atomicAdd(p.head, 1u);
-        team_sync<CTA_TEAM>();
+        team_sync<TW>();
         const int64_t qi = ts->item_idx;
-        team_sync<CTA_TEAM>();
+        team_sync<TW>();
         if (qi >= p.queue_len) break;
         const uint64_t it = p.queue[qi];
         if (it & kSkipBit) continue;     // processed in grid mode
@@ -1227,9 +1239,7 @@ __global__ void __launch_bounds__(NW * 32, CTA_TEAM ? 2 : 5) sketch_kernel(const
         const int64_t out_row = (int64_t)v * p.num_sets + set;
         if (e < b || e - b > (int64_t)PMH_MAX_SET_ELEMENTS) {
             const int code = e < b ? PMH_ERR_INVALID_ARG : PMH_ERR_UNSUPPORTED;
-            const int tt = CTA_TEAM ? threadIdx.x : lane;
-            const int nthr = CTA_TEAM ? blockDim.x : 32;
-            for (uint32_t k = tt; k < p.m; k += nthr) {
+            for (uint32_t k = tt; k < p.m; k += TW * 32) {
                 p.out_ids[out_row * p.m + k] = 0;
                 if (p.out_q) p.out_q[out_row * p.m + k] = __longlong_as_double(0x7FF0000000000000ll);
             }
@@ -1238,8 +1248,8 @@ __global__ void __launch_bounds__(NW * 32, CTA_TEAM ? 2 : 5) sketch_kernel(const
         }
         c.beg = b;
         c.n = (uint32_t)(e - b);
-        process_item<FAM, F32, CTA_TEAM>(c, v, set);
-        team_sync<CTA_TEAM>();
+        process_item<FAM, F32, TW>(c, v, set);
+        team_sync<TW>();
     }
     __syncwarp();
     if (p.counters && lane < PMH_NUM_COUNTERS && c.ws->cnt[lane]) atomicAdd(&p.counters[lane], c.ws->cnt[lane]);

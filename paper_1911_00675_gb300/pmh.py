@@ -20,10 +20,12 @@ OK, ERR_INVALID_ARG, ERR_BAD_WEIGHT, ERR_ITER_LIMIT, ERR_CUDA, ERR_NO_MEMORY, ER
 V1, V1A, V2, V3, V3A, V4 = range(6)
 VARIANTS = {"1": V1, "1a": V1A, "2": V2, "3": V3, "3a": V3A, "4": V4}
 FP64, FP32_RECHECK = 0, 1
+SHAPE_WARP, SHAPE_CTA8, SHAPE_QUAD, SHAPE_PAIR, SHAPE_QUAD8, SHAPE_QUAD8L = range(6)
 COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "rounds", "deep", "prefiltered",
             "cyc_pass0", "cyc_first", "cyc_deep", "cyc_refresh", "cyc_finish", "items", "cyc_surv", "reserved15")
 EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_sketch_batch_noalloc",
            "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_last_launches", "pmh_set_thresholds",
+           "pmh_set_team_shape", "pmh_set_autotune", "pmh_last_team_shapes",
            "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge")
 
 _lib = None
@@ -63,6 +65,12 @@ def load(path: str = LIB_PATH):
             lib.pmh_last_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
             lib.pmh_last_launches.restype = i32
             lib.pmh_last_launches.argtypes = [vp, ctypes.POINTER(i32)]
+            lib.pmh_set_team_shape.restype = i32
+            lib.pmh_set_team_shape.argtypes = [vp, i32, i32]
+            lib.pmh_set_autotune.restype = i32
+            lib.pmh_set_autotune.argtypes = [vp, i32]
+            lib.pmh_last_team_shapes.restype = i32
+            lib.pmh_last_team_shapes.argtypes = [vp, ctypes.POINTER(i32)]
             lib.pmh_set_thresholds.restype = i32
             lib.pmh_set_thresholds.argtypes = [vp, ctypes.c_double, ctypes.c_double, i32, i64]
             lib.pmh_estimate_allpairs.restype = i32
@@ -164,6 +172,18 @@ class Handle:
         n = ctypes.c_int32()
         self._raise(load().pmh_last_launches(self._h, ctypes.byref(n)))
         return n.value
+
+    def set_team_shape(self, family: int = 0, shape: int = -1):
+        """Pins the team shape of a family (1..4, 0 = all); -1 lets the handle choose."""
+        self._raise(load().pmh_set_team_shape(self._h, int(family), int(shape)))
+
+    def set_autotune(self, enable: int = 1):
+        self._raise(load().pmh_set_autotune(self._h, int(enable)))
+
+    def last_team_shapes(self):
+        arr = (ctypes.c_int32 * 4)()
+        self._raise(load().pmh_last_team_shapes(self._h, arr))
+        return list(arr)
 
     def set_thresholds(self, t_c: float = 4.0, t_c_grid: float = 8.0, rounds: int = 5, grid_min: int = 1 << 20):
         """Work-only tuning of later sketch_batch calls (results never depend on it)."""

@@ -153,3 +153,34 @@ def test_c2_full_sampled(H):
 @pytest.mark.slow
 def test_c3_full_sampled(H):
     _sampled_parity(H, W.batch_c3(), ["2", "4"], 10)
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5], ids=["warp", "cta8", "quad", "pair", "quad8", "quad8l"])
+def test_every_team_shape_matches_oracle(H, shape):
+    # how warps share an item changes nothing in the result (Eq. signature_def is per item)
+    b = W.random_batch(500 + shape, [0, 1, 2, 33, 64, 65, 130, 700, 2500], 256, "lognormal")
+    H.set_team_shape(0, shape)
+    try:
+        for precision in (0, 1):
+            z, q, st = run(H, b, VARS, precision, with_q=True, seed=6)
+            assert (st == 0).all()
+            assert H.last_team_shapes() == [shape] * 4
+            for vi, v in enumerate(VARS):
+                check_sets(b, v, z[vi], q[vi], range(b.num_sets), seed=6)
+    finally:
+        H.set_team_shape(0, -1)
+
+
+def test_autotune_picks_a_shape_and_keeps_results(H):
+    b = W.random_batch(510, [5, 50, 500, 5000], 128, "uniform")
+    H.set_autotune(-1)
+    z1, q1, _ = run(H, b, ["1", "2", "3a", "4"], 1, seed=1)      # tunes: one run per shape, then the call
+    shapes = H.last_team_shapes()
+    assert all(0 <= s <= 5 for s in shapes)
+    z2, q2, _ = run(H, b, ["1", "2", "3a", "4"], 1, seed=1)      # cached choice
+    assert H.last_team_shapes() == shapes
+    assert np.array_equal(z1, z2) and np.array_equal(q1, q2)
+    H.set_autotune(0)
+    z3, q3, _ = run(H, b, ["1", "2", "3a", "4"], 1, seed=1)      # default rule
+    assert np.array_equal(z1, z3) and np.array_equal(q1, q3)
+    H.set_autotune(1)
