@@ -80,7 +80,14 @@ inline uint64_t host_mix64(uint64_t z) {
 // each family sorted by decreasing floor(log2(n+1)) (largest sets first).
 // Meta layout: [0, 256) histogram per (family, bucket), [256, 512) running
 // starts, [512, 516) per-family head counters of the persistent kernels.
-constexpr int kQHist = 0, kQStart = 256, kQHead = 512, kQMetaWords = 520;
+// [516] counts the sets whose statistics are split over all blocks; [520, ...)
+// lists them (u64 set indices, kBigCap of them).
+constexpr int kQHist = 0, kQStart = 256, kQHead = 512, kQBigCount = 516, kQBigList = 520;
+constexpr int kBigCap = 1024;
+constexpr int kQMetaWords = kQBigList + 2 * kBigCap;
+constexpr int kQMetaClearWords = kQBigList;     // words cleared per call
+constexpr int64_t kStatChunk = 65536;           // elements per statistics chunk
+constexpr int64_t kStatBig = 4 * kStatChunk;    // sets longer than this are split over all blocks
 
 struct FamOfVariant {
     int f[8];
@@ -162,60 +169,121 @@ __device__ __forceinline__ void scaled_merge(ScaledSum &s, int me2, float acc2) 
     s.me = M;
 }
 
-static __global__ void __launch_bounds__(256) set_stats_kernel(const int64_t *off, const double *w, int64_t num_sets,
-                                                               SetStat *out) {
+// Statistics of the elements [b, e) of one set by one block; the totals are
+// valid in thread 0.
+struct StatPart {
+    ScaledSum sum;
+    unsigned int np = 0;
+    int bad = 0;
+};
+__device__ __forceinline__ StatPart block_stats(const unsigned long long *wb, int64_t b, int64_t e) {
     __shared__ float sacc[8];
-    __shared__ int sme[8], snp[8], sbad[8];
+    __shared__ int sme[8], sbad[8];
+    __shared__ unsigned int snp[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    StatPart r;
+    for (int64_t i0 = b + threadIdx.x; i0 < e; i0 += 4 * (int64_t)blockDim.x) {
+        uint64_t bits[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + (int64_t)u * blockDim.x;
+            bits[u] = i < e ? (uint64_t)__ldcs(wb + i) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t x = bits[u];
+            const int ex = (int)(x >> 52) & 0x7FF;
+            const bool neg = (x >> 63) != 0;
+            const bool zero = (x << 1) == 0;
+            if (ex == 0x7FF || (neg && !zero)) { r.bad = 1; continue; }
+            if (zero) continue;
+            if (ex == 0) {   // subnormal: counted, adds nothing to the sum; bad if 1/w overflows
+                if (isinf(__drcp_rn(__longlong_as_double((long long)x)))) r.bad = 1;
+                else r.np++;
+                continue;
+            }
+            scaled_add(r.sum, x);
+            r.np++;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        const int me2 = __shfl_xor_sync(0xFFFFFFFFu, r.sum.me, o);
+        const float acc2 = __shfl_xor_sync(0xFFFFFFFFu, r.sum.acc, o);
+        scaled_merge(r.sum, me2, acc2);
+        r.np += __shfl_xor_sync(0xFFFFFFFFu, r.np, o);
+        r.bad |= __shfl_xor_sync(0xFFFFFFFFu, r.bad, o);
+    }
+    if (lane == 0) { sacc[warp] = r.sum.acc; sme[warp] = r.sum.me; snp[warp] = r.np; sbad[warp] = r.bad; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        StatPart t;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { scaled_merge(t.sum, sme[j], sacc[j]); t.np += snp[j]; t.bad |= sbad[j]; }
+        r = t;
+    }
+    __syncthreads();
+    return r;
+}
+__device__ __forceinline__ double scaled_value(const ScaledSum &s) {
+    return s.me < 0 ? 0.0 : ldexp((double)s.acc, s.me - 1023);
+}
+
+// Pass 1: one block per set, grid-stride over sets.  A set longer than
+// kStatBig is listed (up to kBigCap of them) and only its first chunk is
+// summed here; pass 2 adds the rest with all blocks.
+static __global__ void __launch_bounds__(256) set_stats_kernel(const int64_t *off, const double *w, int64_t num_sets,
+                                                               SetStat *out, unsigned int *meta) {
+    __shared__ int s_listed;
     const unsigned long long *wb = (const unsigned long long *)w;
     for (int64_t s = blockIdx.x; s < num_sets; s += gridDim.x) {
         const int64_t b = off[s], e = off[s + 1];
-        ScaledSum sum;
-        int np = 0, bad = 0;
-        for (int64_t i0 = b + threadIdx.x; i0 < e; i0 += 4 * (int64_t)blockDim.x) {
-            uint64_t bits[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t i = i0 + (int64_t)u * blockDim.x;
-                bits[u] = i < e ? (uint64_t)__ldcs(wb + i) : 0ull;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint64_t x = bits[u];
-                const int ex = (int)(x >> 52) & 0x7FF;
-                const bool neg = (x >> 63) != 0;
-                const bool zero = (x << 1) == 0;
-                if (ex == 0x7FF || (neg && !zero)) { bad = 1; continue; }
-                if (zero) continue;
-                if (ex == 0) {   // subnormal: counted, adds nothing to the sum; bad if 1/w overflows
-                    if (isinf(__drcp_rn(__longlong_as_double((long long)x)))) bad = 1;
-                    else np++;
-                    continue;
-                }
-                scaled_add(sum, x);
-                np++;
-            }
-        }
-        for (int o = 16; o; o >>= 1) {
-            const int me2 = __shfl_xor_sync(0xFFFFFFFFu, sum.me, o);
-            const float acc2 = __shfl_xor_sync(0xFFFFFFFFu, sum.acc, o);
-            scaled_merge(sum, me2, acc2);
-            np += __shfl_xor_sync(0xFFFFFFFFu, np, o);
-            bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, o);
-        }
-        if (lane == 0) { sacc[warp] = sum.acc; sme[warp] = sum.me; snp[warp] = np; sbad[warp] = bad; }
-        __syncthreads();
+        int64_t end = e;
         if (threadIdx.x == 0) {
-            ScaledSum S;
-            int N = 0, B = 0;
-            for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { scaled_merge(S, sme[j], sacc[j]); N += snp[j]; B |= sbad[j]; }
-            SetStat r;
-            r.wsum = S.me < 0 ? 0.0 : ldexp((double)S.acc, S.me - 1023);
-            r.npos = N;
-            r.bad = B;
-            out[s] = r;
+            s_listed = 0;
+            if (e - b > kStatBig) {
+                const unsigned int slot = atomicAdd(&meta[kQBigCount], 1u);
+                if (slot < (unsigned int)kBigCap) {
+                    ((unsigned long long *)(meta + kQBigList))[slot] = (unsigned long long)s;
+                    s_listed = 1;
+                }
+            }
         }
         __syncthreads();
+        if (s_listed) end = b + kStatChunk;
+        const StatPart r = block_stats(wb, b, end);
+        if (threadIdx.x == 0) {
+            SetStat o;
+            o.wsum = scaled_value(r.sum);
+            o.npos = r.np;
+            o.bad = r.bad;
+            out[s] = o;
+        }
+    }
+}
+
+// Pass 2: the chunks after the first of every listed set, numbered across the
+// listed sets and dealt round-robin to all blocks; partial results are added
+// atomically (one FP64 add per chunk).
+static __global__ void __launch_bounds__(256) set_stats_big_kernel(const int64_t *off, const double *w, SetStat *out,
+                                                                   const unsigned int *meta) {
+    const unsigned long long *wb = (const unsigned long long *)w;
+    const int nbig = min((int)meta[kQBigCount], kBigCap);
+    const int64_t G = gridDim.x;
+    int64_t base = 0;   // global number of the entry's chunk 1
+    for (int j = 0; j < nbig; ++j) {
+        const int64_t s = (int64_t)((const unsigned long long *)(meta + kQBigList))[j];
+        const int64_t b = off[s], e = off[s + 1];
+        const int64_t nch = (e - b + kStatChunk - 1) / kStatChunk;
+        const int64_t first = 1 + (((int64_t)blockIdx.x - base) % G + G) % G;   // (base + c - 1) = blockIdx.x mod G
+        base += nch - 1;
+        for (int64_t c = first; c < nch; c += G) {
+            const int64_t cb = b + c * kStatChunk;
+            const StatPart r = block_stats(wb, cb, min(e, cb + kStatChunk));
+            if (threadIdx.x == 0) {
+                atomicAdd(&out[s].wsum, scaled_value(r.sum));
+                atomicAdd(&out[s].npos, r.np);
+                if (r.bad) atomicOr(&out[s].bad, 1);
+            }
+        }
     }
 }
 
@@ -304,14 +372,15 @@ inline cudaError_t enqueue_batch(SketchParams p, const Plan &plan, int precision
     if (qg < 1) qg = 1;
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(qmeta, 0, kQMetaWords * sizeof(unsigned int), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(qmeta, 0, kQMetaClearWords * sizeof(unsigned int), st)) != cudaSuccess) return e;
     queue_count<<<qg, qb, 0, st>>>(p.offsets, p.num_sets, p.num_variants, fv, qmeta);
     queue_starts<<<1, 32, 0, st>>>(qmeta);
     if (p.gctl && (e = cudaMemsetAsync(p.gctl, 0, sizeof(unsigned int) * 4, st)) != cudaSuccess) return e;
     queue_scatter<<<qg, qb, 0, st>>>(p.offsets, p.num_sets, p.num_variants, fv, qmeta, queue, p.gctl, p.grid_min);
     if (p.gctl) grid_init_kernel<<<4 * kMaxGrid, 256, 0, st>>>(p.gctl, p.gstate, p.gsig, p.m, precision == PMH_FP32_RECHECK);
     const int sg = (int)std::max<int64_t>(1, std::min<int64_t>(p.num_sets, (int64_t)sm_count * 8));
-    set_stats_kernel<<<sg, 256, 0, st>>>(p.offsets, p.weights, p.num_sets, stats);
+    set_stats_kernel<<<sg, 256, 0, st>>>(p.offsets, p.weights, p.num_sets, stats, qmeta);
+    set_stats_big_kernel<<<sm_count * 8, 256, 0, st>>>(p.offsets, p.weights, stats, qmeta);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     p.stats = stats;
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
@@ -343,7 +412,7 @@ struct Thresholds {
 
 // Kernel launches of one enqueue_batch call (fixed by the plan).
 inline int launch_count(const Plan &plan, bool grid) {
-    int n = 4 + plan.nfam + (grid ? 1 : 0);
+    int n = 5 + plan.nfam + (grid ? 1 : 0);
     for (int j = 0; j < plan.nfam; j++) n += (grid && plan.ggrid[j] > 0) ? 1 : 0;
     return n;
 }

@@ -85,7 +85,7 @@ struct GridCtl {
 // Per-set statistics (one entry per set, computed once for all variants).
 struct SetStat {
     double wsum;   // sum of the positive weights
-    int npos;      // elements with w > 0
+    uint32_t npos; // elements with w > 0 (a set has < 2^32 elements)
     int bad;       // a weight is negative, NaN, infinite, or has no finite reciprocal
 };
 
@@ -383,6 +383,7 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
     if (!EXACT) count(c, PMH_CNT_DEEP, 1);
     double carry64 = 0.0;
     float c_hi = 0.0f, c_lo = 0.0f;
+    bool refreshed = false;
     const uint32_t limit = (FAM == 2 || FAM == 4) ? m : P.cap_points;
 #pragma unroll 1
     for (uint32_t base = 1;; base += 32) {
@@ -489,9 +490,14 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
         }
         if (base + 31 >= limit && (FAM == 2 || FAM == 4)) return 0.0;
         if ((FAM == 1 || FAM == 2) && last_beyond) return 0.0;
-        // keep q_max fresh while expanding (after groups that changed a minimum)
+        // keep q_max fresh while expanding: after groups that changed a minimum, and
+        // once as soon as the signature is full (another warp of the team may have
+        // filled it, and this element's later points may never win again)
         const int uf = __shfl_sync(kFull, lane == 0 ? ld_volatile(&c.ts->unfilled) : 1, 0);
-        if (uf == 0 && any_win) refresh_bound<F32>(c);
+        if (uf == 0 && (any_win || !refreshed)) {
+            refresh_bound<F32>(c);
+            refreshed = true;
+        }
     }
 }
 

@@ -72,11 +72,14 @@ def test_grid_finalize_rerun_when_components_stay_empty(H):
         H.set_thresholds()
 
 
+@pytest.mark.parametrize("shape", [0, 3, 1], ids=["warp", "pair", "cta8"])
 @pytest.mark.parametrize("t_c,rounds", [(0.02, 5), (0.02, 0), (0.5, 1), (30.0, 5)])
-def test_threshold_schedule_does_not_change_results(H, t_c, rounds):
+def test_threshold_schedule_does_not_change_results(H, t_c, rounds, shape):
     # t_c is given as ln m + t_c: tiny first thresholds force retry rounds; rounds=0
-    # goes straight to the unbounded loop of the paper's algorithms
+    # goes straight to the unbounded loop of the paper's algorithms, where a team's
+    # bound stays infinite until its signature is full
     m = 300
+    H.set_team_shape(0, shape)
     H.set_thresholds(t_c=t_c - np.log(m), rounds=rounds, grid_min=0)
     try:
         b = W.random_batch(34, [1, 2, 7, 100, 999, 5000], m, "lognormal")
@@ -87,6 +90,7 @@ def test_threshold_schedule_does_not_change_results(H, t_c, rounds):
                 check_sets(b, v, z[vi], q[vi], range(b.num_sets), seed=9)
     finally:
         H.set_thresholds()
+        H.set_team_shape(0, -1)
 
 
 def test_more_grid_items_than_slots(H):
@@ -122,10 +126,10 @@ def test_launch_count_reported(H):
     b = W.random_batch(37, [10, 20], 64, "uniform")
     H.set_thresholds(grid_min=0)
     run(H, b, ["1", "2", "3", "4"], 1)
-    assert H.last_launches() == 4 + 4                     # queue (3) + statistics + one per family
+    assert H.last_launches() == 5 + 4                     # queue (3) + statistics (2) + one per family
     H.set_thresholds()
     run(H, b, ["1", "3a"], 1)
-    assert H.last_launches() == 4 + 2 + 1 + 2             # + grid reset + one grid kernel per family
+    assert H.last_launches() == 5 + 2 + 1 + 2             # + grid reset + one grid kernel per family
 
 
 @pytest.mark.slow
