@@ -365,33 +365,29 @@ def main():
     torch.cuda.synchronize()
     c = dict(zip(pmh.COUNTERS, cnt.cpu().tolist()))
 
-    # ---------------- e2e: host buffers in, signatures back, every step
+    # ---------------- e2e: host buffers in, signatures back, every step, through the host-buffer C-ABI
+    # call (pinned host memory; the library pipelines copy-in, sketch and copy-out over chunks of sets)
     e2e = None
     if not args.no_e2e:
         out_h = torch.empty(out32.shape, dtype=torch.int64).pin_memory()
-        ids_d, w_d, off_d = torch.empty_like(ids), torch.empty_like(w), torch.empty_like(off)
 
         def e2e_step():
-            ids_d.copy_(ids_h, non_blocking=True)
-            w_d.copy_(w_h, non_blocking=True)
-            off_d.copy_(off_h, non_blocking=True)
-            h.sketch_batch(ids_d, w_d, off_d, m, VARIANTS, pmh.FP32_RECHECK, 0, out_ids=out32, status=st32)
-            out_h.copy_(out32, non_blocking=True)
+            h.sketch_batch_host(ids_h, w_h, off_h, m, VARIANTS, pmh.FP32_RECHECK, 0, out_ids=out_h, with_status=False)
 
         for _ in range(2):
             e2e_step()
         barrier()
         ksteps = max(3, args.steps // 2)
-        e0.record(stream)
+        t0 = time.perf_counter()
         for _ in range(ksteps):
             e2e_step()
-        e1.record(stream)
         barrier()
-        te = max_over_ranks(e0.elapsed_time(e1) / ksteps)
+        te = max_over_ranks((time.perf_counter() - t0) * 1e3 / ksteps)
+        identical_e2e = bool(torch.equal(out_h, out32.cpu()))
         h2d = ids_h.numel() * 8 + w_h.numel() * 8 + off_h.numel() * 8
         d2h = out_h.numel() * 8
         e2e = {"value": work * world / (te * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": te}
+               "ms_per_step": te, "timing": "host wall clock around the blocking call", "identical_output": identical_e2e}
 
     # ---------------- roofline of the dominant kernel (the persistent sketch kernel)
     k_avg = statistics.mean(kernel_ms)

@@ -139,6 +139,36 @@ pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const double *wei
                             int32_t *set_status, uint64_t *counters, void *stream);
 
 /*
+ * pmh_sketch_batch_host -- pmh_sketch_batch on HOST buffers: the same batch,
+ * variants, precision, seed and results (identical values), with ids,
+ * weights, offsets and the outputs in host memory.
+ *
+ * The call splits the sets into `chunks` contiguous ranges by work (the first
+ * range gets half the share of the others; chunks <= 0: automatic, 2 for
+ * batches of 2^22 elements or more, else 1) and pipelines them on internal
+ * streams: host->device copy of a range's elements; the sketch of the range,
+ * alternating between two compute streams so that one range's kernels fill
+ * the SMs another range leaves idle; device->host copy of each variant
+ * family's rows as soon as that family is done.  Copies overlap the kernels when the host
+ * buffers are page-locked (cudaHostAlloc / cudaHostRegister / pinned tensors);
+ * pageable buffers work but do not overlap.  It returns when every result is
+ * in host memory.
+ *
+ *   offsets   host int64[num_sets + 1], non-decreasing, offsets[0] >= 0; the
+ *             call reads ids / weights [0, offsets[num_sets]).
+ *   out_ids   host uint64[num_variants * num_sets * m] (same layout as on the
+ *             device); out_q, set_status optional (NULL).
+ * Device workspace (a copy of the inputs and two chunks of outputs) stays
+ * with the handle for later calls.  Errors: as pmh_sketch_batch, plus
+ * PMH_ERR_INVALID_ARG for decreasing or negative offsets (checked on the
+ * host).  Not for use while a stream capture is active on this thread.
+ */
+pmh_status pmh_sketch_batch_host(pmh_handle h, const uint64_t *ids, const double *weights, const int64_t *offsets,
+                                 int64_t num_sets, uint32_t m, const int32_t *variants, int32_t num_variants,
+                                 int32_t precision, uint64_t seed, uint64_t *out_ids, double *out_q,
+                                 int32_t *set_status, int32_t chunks);
+
+/*
  * pmh_sketch_batch_noalloc -- pmh_sketch_batch for callers that cannot
  * allocate GPU memory: code that runs under another runtime's fixed memory
  * budget, inside a framework that forbids cudaMalloc on its hot path, or

@@ -46,19 +46,36 @@ struct TuneKey {
 
 }  // namespace
 
+// Device workspace of one sketch call in flight: work queue, queue metadata,
+// per-set statistics, grid-mode state.
+struct Workspace {
+    uint64_t *queue = nullptr;
+    int64_t queue_cap = 0;
+    unsigned int *qmeta = nullptr;   // histogram, running starts, per-family heads, big-set list
+    SetStat *stats = nullptr;
+    int64_t stats_cap = 0;
+    void *grid = nullptr;
+    size_t grid_bytes = 0;
+};
+
+// Buffers and streams of pmh_sketch_batch_host.
+struct HostPipe {
+    void *ids = nullptr, *w = nullptr, *off = nullptr;
+    size_t ids_cap = 0, w_cap = 0, off_cap = 0;
+    void *z[2] = {nullptr, nullptr}, *q[2] = {nullptr, nullptr}, *st[2] = {nullptr, nullptr};
+    size_t z_cap[2] = {0, 0}, q_cap[2] = {0, 0}, st_cap[2] = {0, 0};
+    cudaStream_t s[4] = {nullptr, nullptr, nullptr, nullptr};   // copy in, compute (two), copy out
+    std::vector<cudaEvent_t> ev;
+};
+
 struct pmh_handle_s {
     int device = 0;
     int sm_count = 0;
     std::string err;
     std::map<uint32_t, TableBuf> tables;
-    // work queue
-    uint64_t *queue = nullptr;
-    int64_t queue_cap = 0;
-    unsigned int *qmeta = nullptr;   // histogram, running starts, per-family heads
-    SetStat *stats = nullptr;        // per-set statistics
-    int64_t stats_cap = 0;
-    void *grid = nullptr;            // grid-mode workspace (huge sets)
-    size_t grid_bytes = 0;
+    // per-stream workspaces: [0] for pmh_sketch_batch (and its graph), [1] for the
+    // second compute stream of pmh_sketch_batch_host
+    Workspace ws[2];
     cudaStream_t cap_stream = nullptr;
     bool graph_valid = false;
     GraphKey gkey{};
@@ -67,6 +84,8 @@ struct pmh_handle_s {
     // planner knobs (tunable)
     Thresholds th;
     int last_launches = 0;
+    int last_chunks = 0;
+    HostPipe hp;
     int force_shape[4] = {-1, -1, -1, -1};   // per family: TeamShape, or -1
     int last_shape[4] = {-1, -1, -1, -1};    // shapes of the most recent call (-1: family absent)
     bool autotune = true;
@@ -113,54 +132,61 @@ static pmh_status get_tables(pmh_handle h, uint32_t m, Tables *out) {
     return PMH_OK;
 }
 
-static pmh_status ensure_queue(pmh_handle h, int64_t items) {
-    if (!h->qmeta) CUDA_TRY(h, cudaMalloc(&h->qmeta, kQMetaWords * sizeof(unsigned int)));
-    if (items > h->queue_cap) {
-        if (h->queue) cudaFree(h->queue);
-        h->queue = nullptr;
-        h->queue_cap = 0;
+static pmh_status ensure_queue(pmh_handle h, Workspace &w, int64_t items) {
+    if (!w.qmeta) CUDA_TRY(h, cudaMalloc(&w.qmeta, kQMetaWords * sizeof(unsigned int)));
+    if (items > w.queue_cap) {
+        if (w.queue) cudaFree(w.queue);
+        w.queue = nullptr;
+        w.queue_cap = 0;
         int64_t cap = items < 1024 ? 1024 : items;
-        cudaError_t e = cudaMalloc(&h->queue, (size_t)cap * sizeof(uint64_t));
+        cudaError_t e = cudaMalloc(&w.queue, (size_t)cap * sizeof(uint64_t));
         if (e != cudaSuccess) return fail(h, PMH_ERR_NO_MEMORY, "queue allocation (%lld items): %s", (long long)cap, cudaGetErrorString(e));
-        h->queue_cap = cap;
+        w.queue_cap = cap;
         h->graph_valid = false;
     }
     return PMH_OK;
 }
 
-static pmh_status ensure_grid(pmh_handle h, uint32_t m) {
+static pmh_status ensure_grid(pmh_handle h, Workspace &w, uint32_t m) {
     const size_t need = grid_scratch_bytes(m);
-    if (need > h->grid_bytes) {
-        if (h->grid) cudaFree(h->grid);
-        h->grid = nullptr;
-        h->grid_bytes = 0;
-        cudaError_t e = cudaMalloc(&h->grid, need);
+    if (need > w.grid_bytes) {
+        if (w.grid) cudaFree(w.grid);
+        w.grid = nullptr;
+        w.grid_bytes = 0;
+        cudaError_t e = cudaMalloc(&w.grid, need);
         if (e != cudaSuccess) return fail(h, PMH_ERR_NO_MEMORY, "grid workspace (%zu bytes): %s", need, cudaGetErrorString(e));
-        h->grid_bytes = need;
+        w.grid_bytes = need;
         h->graph_valid = false;
     }
     return PMH_OK;
 }
 
-static pmh_status ensure_stats(pmh_handle h, int64_t num_sets) {
-    if (num_sets > h->stats_cap) {
-        if (h->stats) cudaFree(h->stats);
-        h->stats = nullptr;
-        h->stats_cap = 0;
+static pmh_status ensure_stats(pmh_handle h, Workspace &w, int64_t num_sets) {
+    if (num_sets > w.stats_cap) {
+        if (w.stats) cudaFree(w.stats);
+        w.stats = nullptr;
+        w.stats_cap = 0;
         int64_t cap = num_sets < 1024 ? 1024 : num_sets;
-        cudaError_t e = cudaMalloc(&h->stats, (size_t)cap * sizeof(SetStat));
+        cudaError_t e = cudaMalloc(&w.stats, (size_t)cap * sizeof(SetStat));
         if (e != cudaSuccess) return fail(h, PMH_ERR_NO_MEMORY, "set statistics (%lld sets): %s", (long long)cap, cudaGetErrorString(e));
-        h->stats_cap = cap;
+        w.stats_cap = cap;
         h->graph_valid = false;
     }
     return PMH_OK;
 }
 
-// Enqueues the whole batch on `st` with the handle's workspace.
-static pmh_status enqueue_sketch(pmh_handle h, const SketchParams &p, const Plan &plan, int precision,
-                                 cudaStream_t st) {
-    cudaError_t e = enqueue_batch(p, plan, precision, h->sm_count, h->queue, h->qmeta, h->stats, st,
-                                  h->profiling ? h->ev : nullptr);
+static pmh_status ensure_workspace(pmh_handle h, Workspace &w, int64_t num_sets, int64_t items, uint32_t m) {
+    pmh_status rc = ensure_queue(h, w, items);
+    if (!rc) rc = ensure_stats(h, w, num_sets);
+    if (!rc) rc = ensure_grid(h, w, m);
+    return rc;
+}
+
+// Enqueues the whole batch on `st` with workspace `w`.
+static pmh_status enqueue_sketch(pmh_handle h, Workspace &w, const SketchParams &p, const Plan &plan, int precision,
+                                 cudaStream_t st, cudaEvent_t *fam_ev) {
+    cudaError_t e = enqueue_batch(p, plan, precision, h->sm_count, w.queue, w.qmeta, w.stats, st,
+                                  h->profiling ? h->ev : nullptr, fam_ev);
     if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "sketch launch: %s", cudaGetErrorString(e));
     return PMH_OK;
 }
@@ -197,10 +223,16 @@ extern "C" void pmh_destroy(pmh_handle h) {
     for (int i = 0; i < 3; i++) if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     for (int i = 0; i < 7; i++) if (h->tev[i]) cudaEventDestroy(h->tev[i]);
     for (auto &kv : h->tables) cudaFree(kv.second.dev);
-    if (h->queue) cudaFree(h->queue);
-    if (h->qmeta) cudaFree(h->qmeta);
-    if (h->stats) cudaFree(h->stats);
-    if (h->grid) cudaFree(h->grid);
+    for (Workspace &w : h->ws) {
+        if (w.queue) cudaFree(w.queue);
+        if (w.qmeta) cudaFree(w.qmeta);
+        if (w.stats) cudaFree(w.stats);
+        if (w.grid) cudaFree(w.grid);
+    }
+    for (void *ptr : {h->hp.ids, h->hp.w, h->hp.off, h->hp.z[0], h->hp.z[1], h->hp.q[0], h->hp.q[1], h->hp.st[0], h->hp.st[1]})
+        if (ptr) cudaFree(ptr);
+    for (int i = 0; i < 4; i++) if (h->hp.s[i]) cudaStreamDestroy(h->hp.s[i]);
+    for (cudaEvent_t e : h->hp.ev) cudaEventDestroy(e);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
@@ -279,7 +311,7 @@ extern "C" pmh_status pmh_last_kernel_ms(pmh_handle h, float *queue_ms, float *s
 
 // Times every team shape on this batch (one full run each, on `st`, blocking)
 // and records the fastest per family.  All runs write the same results.
-static pmh_status autotune_shapes(pmh_handle h, SketchParams p, uint32_t m, const int32_t *variants,
+static pmh_status autotune_shapes(pmh_handle h, Workspace &w, SketchParams p, uint32_t m, const int32_t *variants,
                                   int32_t num_variants, int64_t num_sets, int precision, cudaStream_t st,
                                   int *kinds, const TuneKey *tkey) {
     if (!h->tev[0])
@@ -297,7 +329,7 @@ static pmh_status autotune_shapes(pmh_handle h, SketchParams p, uint32_t m, cons
         SketchParams q = p;
         for (int j = 0; j < plan.nfam && q.gctl; j++)
             if (plan.ggrid[j] <= 0) { q.gctl = nullptr; q.gstate = nullptr; q.gsig = nullptr; }
-        e = enqueue_batch(q, plan, precision, h->sm_count, h->queue, h->qmeta, h->stats, st, h->tev, h->tev + 3);
+        e = enqueue_batch(q, plan, precision, h->sm_count, w.queue, w.qmeta, w.stats, st, h->tev, h->tev + 3);
         if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(e));
         CUDA_TRY(h, cudaEventSynchronize(h->tev[2]));
         for (int j = 0; j < plan.nfam; j++) {
@@ -317,12 +349,9 @@ static pmh_status autotune_shapes(pmh_handle h, SketchParams p, uint32_t m, cons
     return PMH_OK;
 }
 
-extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const double *weights, const int64_t *offsets,
-                                       int64_t num_sets, uint32_t m, const int32_t *variants, int32_t num_variants,
-                                       int32_t precision, uint64_t seed, uint64_t *out_ids, double *out_q,
-                                       int32_t *set_status, uint64_t *counters, void *stream) {
-    if (!h) return PMH_ERR_INVALID_ARG;
-    h->err.clear();
+// Argument checks shared by the device and the host-buffer entry points.
+static pmh_status check_sketch_args(pmh_handle h, int64_t num_sets, uint32_t m, const int32_t *variants,
+                                    int32_t num_variants, int32_t precision) {
     if (num_sets < 0) return fail(h, PMH_ERR_INVALID_ARG, "num_sets < 0");
     if (num_sets >= (1ll << 40)) return fail(h, PMH_ERR_UNSUPPORTED, "num_sets >= 2^40");
     if (num_variants >= 1 && num_variants <= 8 && num_sets * num_variants > 0x7FFFFFFFll - (1ll << 24))
@@ -337,26 +366,30 @@ extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const 
             return fail(h, PMH_ERR_INVALID_ARG, "variant %d requires m >= 2", variants[v]);
         has_perm |= (variants[v] == PMH_V2 || variants[v] == PMH_V4);
     }
-    if (num_sets == 0) return PMH_OK;
-    if (!ids || !weights || !offsets || !out_ids) return fail(h, PMH_ERR_INVALID_ARG, "NULL ids/weights/offsets/out_ids");
+    (void)has_perm;
+    return PMH_OK;
+}
+
+// The sketch of a CSR batch already in device memory, enqueued on `st`
+// (replayed from a cached CUDA graph when allow_graph and the arguments repeat).
+static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, const double *weights,
+                                const int64_t *offsets, int64_t num_sets, uint32_t m, const int32_t *variants,
+                                int32_t num_variants, int32_t precision, uint64_t seed, uint64_t *out_ids,
+                                double *out_q, int32_t *set_status, uint64_t *counters, cudaStream_t st,
+                                bool allow_graph, cudaEvent_t *fam_ev) {
     CUDA_TRY(h, cudaSetDevice(h->device));
-    cudaStream_t st = (cudaStream_t)stream;
+    Workspace &w = h->ws[wsi];
     Tables tab;
     pmh_status rc = get_tables(h, m, &tab);
     if (rc) return rc;
-    rc = ensure_queue(h, num_sets * num_variants);
-    if (rc) return rc;
-    rc = ensure_stats(h, num_sets);
-    if (rc) return rc;
-    rc = ensure_grid(h, m);
+    rc = ensure_workspace(h, w, num_sets, num_sets * num_variants, m);
     if (rc) return rc;
 
     SketchParams p;
     fill_params(&p, ids, weights, offsets, num_sets, m, variants, num_variants, seed, out_ids, out_q, set_status, counters,
                 h->th);
     p.tab = tab;
-    if (h->th.grid_min > 0) bind_grid_scratch(&p, h->grid);
-    (void)has_perm;
+    if (h->th.grid_min > 0) bind_grid_scratch(&p, w.grid);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (st) CUDA_TRY(h, cudaStreamIsCapturing(st, &cs));
     // team shape per family: forced, else tuned, else (tuning off or impossible) the default rule
@@ -377,7 +410,7 @@ extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const 
         }
     }
     if (need_tune && h->autotune && cs == cudaStreamCaptureStatusNone) {
-        rc = autotune_shapes(h, p, m, variants, num_variants, num_sets, precision, st, kinds, tkey);
+        rc = autotune_shapes(h, w, p, m, variants, num_variants, num_sets, precision, st, kinds, tkey);
         if (rc) return rc;
     }
     Plan plan;
@@ -392,9 +425,9 @@ extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const 
     h->last_launches = launch_count(plan, p.gctl != nullptr);
     for (int f = 0; f < 4; f++) h->last_shape[f] = -1;
     for (int j = 0; j < plan.nfam; j++) h->last_shape[plan.fam[j] - 1] = plan.shape[j].kind;
-    if (!h->use_graph || cs != cudaStreamCaptureStatusNone || !st) {
+    if (!allow_graph || wsi != 0 || fam_ev || !h->use_graph || cs != cudaStreamCaptureStatusNone || !st) {
         h->prof_recorded = h->profiling;
-        return enqueue_sketch(h, p, plan, precision, st);
+        return enqueue_sketch(h, w, p, plan, precision, st, fam_ev);
     }
 
     GraphKey key{};
@@ -409,7 +442,7 @@ extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const 
         if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
         h->graph_valid = false;
         CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_sketch(h, p, plan, precision, h->cap_stream);
+        rc = enqueue_sketch(h, w, p, plan, precision, h->cap_stream, nullptr);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
         if (rc) { if (g) cudaGraphDestroy(g); return rc; }
@@ -421,6 +454,164 @@ extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const 
         h->graph_valid = true;
     }
     CUDA_TRY(h, cudaGraphLaunch(h->gexec, st));
+    return PMH_OK;
+}
+
+extern "C" pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const double *weights, const int64_t *offsets,
+                                       int64_t num_sets, uint32_t m, const int32_t *variants, int32_t num_variants,
+                                       int32_t precision, uint64_t seed, uint64_t *out_ids, double *out_q,
+                                       int32_t *set_status, uint64_t *counters, void *stream) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    pmh_status rc = check_sketch_args(h, num_sets, m, variants, num_variants, precision);
+    if (rc) return rc;
+    if (num_sets == 0) return PMH_OK;
+    if (!ids || !weights || !offsets || !out_ids) return fail(h, PMH_ERR_INVALID_ARG, "NULL ids/weights/offsets/out_ids");
+    return sketch_device(h, 0, ids, weights, offsets, num_sets, m, variants, num_variants, precision, seed, out_ids,
+                         out_q, set_status, counters, (cudaStream_t)stream, true, nullptr);
+}
+
+// ------------------------------------------------------------------ host buffers
+// Device mirror of a host batch plus double-buffered chunk outputs, and the
+// three streams of the copy / compute / copy-back pipeline.
+static pmh_status ensure_dev(pmh_handle h, void **ptr, size_t *cap, size_t need, const char *what) {
+    if (need <= *cap) return PMH_OK;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(ptr, need);
+    if (e != cudaSuccess) return fail(h, PMH_ERR_NO_MEMORY, "%s (%zu bytes): %s", what, need, cudaGetErrorString(e));
+    *cap = need;
+    return PMH_OK;
+}
+
+// Contiguous set ranges by work (n + m H_m ln(n+1) per set, the element
+// hashing plus the early-stop points of Sec. ProbMinHash1): the first range
+// gets half the share of the others, so that the first kernels start after a
+// shorter copy.
+static void chunk_bounds(const int64_t *off, int64_t num_sets, uint32_t m, int k, std::vector<int64_t> *b) {
+    double hm = 0.0;
+    for (uint32_t i = 1; i <= m; i++) hm += 1.0 / i;
+    std::vector<double> cum((size_t)num_sets + 1, 0.0);
+    for (int64_t s = 0; s < num_sets; s++) {
+        const double n = (double)(off[s + 1] - off[s]);
+        cum[s + 1] = cum[s] + n + m * hm * std::log1p(n);
+    }
+    b->assign(1, 0);
+    int64_t s = 0;
+    const double shares = 2.0 * k - 1.0;   // weights 1, 2, 2, ..., 2
+    for (int c = 1; c < k; c++) {
+        const double t = cum[num_sets] * (2.0 * c - 1.0) / shares;
+        while (s < num_sets && cum[s + 1] < t) s++;
+        if (s > b->back()) b->push_back(s);
+    }
+    if (b->back() != num_sets) b->push_back(num_sets);
+}
+
+extern "C" pmh_status pmh_sketch_batch_host(pmh_handle h, const uint64_t *ids, const double *weights,
+                                            const int64_t *offsets, int64_t num_sets, uint32_t m,
+                                            const int32_t *variants, int32_t num_variants, int32_t precision,
+                                            uint64_t seed, uint64_t *out_ids, double *out_q, int32_t *set_status,
+                                            int32_t chunks) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    pmh_status rc = check_sketch_args(h, num_sets, m, variants, num_variants, precision);
+    if (rc) return rc;
+    if (num_sets == 0) return PMH_OK;
+    if (!ids || !weights || !offsets || !out_ids) return fail(h, PMH_ERR_INVALID_ARG, "NULL ids/weights/offsets/out_ids");
+    if (offsets[0] < 0) return fail(h, PMH_ERR_INVALID_ARG, "offsets[0] < 0");
+    for (int64_t s = 0; s < num_sets; s++)
+        if (offsets[s + 1] < offsets[s]) return fail(h, PMH_ERR_INVALID_ARG, "offsets decrease at set %lld", (long long)s);
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    const int64_t N = offsets[num_sets];
+    int k = chunks > 0 ? chunks : (N >= (1ll << 22) ? 2 : 1);
+    std::vector<int64_t> b;
+    chunk_bounds(offsets, num_sets, m, k, &b);
+    k = (int)b.size() - 1;
+    int64_t smax = 0;
+    for (int c = 0; c < k; c++) smax = std::max<int64_t>(smax, b[c + 1] - b[c]);
+    const int64_t V = num_variants;
+    // families present, in the order the sketch runs them (ascending)
+    int fam_rank[5] = {-1, -1, -1, -1, -1};
+    {
+        bool present[5] = {false, false, false, false, false};
+        for (int v = 0; v < num_variants; v++) present[family_of(variants[v])] = true;
+        int r = 0;
+        for (int f = 1; f <= 4; f++) if (present[f]) fam_rank[f] = r++;
+    }
+    // workspace for every chunk first: no allocation while the pipeline runs
+    Tables tab;
+    if ((rc = get_tables(h, m, &tab))) return rc;
+    for (Workspace &w : h->ws)
+        if ((rc = ensure_workspace(h, w, smax, smax * V, m))) return rc;
+    HostPipe &hp = h->hp;
+    if ((rc = ensure_dev(h, &hp.ids, &hp.ids_cap, (size_t)N * 8, "device ids"))) return rc;
+    if ((rc = ensure_dev(h, &hp.w, &hp.w_cap, (size_t)N * 8, "device weights"))) return rc;
+    if ((rc = ensure_dev(h, &hp.off, &hp.off_cap, (size_t)(num_sets + 1) * 8, "device offsets"))) return rc;
+    for (int i = 0; i < 2; i++) {
+        if ((rc = ensure_dev(h, &hp.z[i], &hp.z_cap[i], (size_t)(V * smax * m) * 8, "chunk ids"))) return rc;
+        if (out_q && (rc = ensure_dev(h, &hp.q[i], &hp.q_cap[i], (size_t)(V * smax * m) * 8, "chunk q"))) return rc;
+        if (set_status && (rc = ensure_dev(h, &hp.st[i], &hp.st_cap[i], (size_t)(V * smax) * 4, "chunk status"))) return rc;
+    }
+    if (!hp.s[0])
+        for (int i = 0; i < 4; i++) CUDA_TRY(h, cudaStreamCreateWithFlags(&hp.s[i], cudaStreamNonBlocking));
+    constexpr int kEvPerChunk = 6;   // inputs in, four families done, outputs out
+    while ((int)hp.ev.size() < kEvPerChunk * k) {
+        cudaEvent_t e;
+        CUDA_TRY(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        hp.ev.push_back(e);
+    }
+    cudaStream_t s_in = hp.s[0], s_out = hp.s[3];
+    unsigned char *dids = (unsigned char *)hp.ids, *dw = (unsigned char *)hp.w;
+    int64_t *doff = (int64_t *)hp.off;
+    auto ev_in = [&](int c) { return hp.ev[kEvPerChunk * c]; };
+    auto ev_fam = [&](int c) { return hp.ev.data() + kEvPerChunk * c + 1; };
+    auto ev_out = [&](int c) { return hp.ev[kEvPerChunk * c + 5]; };
+    // inputs: offsets, then each chunk's elements in place
+    CUDA_TRY(h, cudaMemcpyAsync(doff, offsets, (size_t)(num_sets + 1) * 8, cudaMemcpyHostToDevice, s_in));
+    for (int c = 0; c < k; c++) {
+        const int64_t e0 = c == 0 ? 0 : offsets[b[c]], e1 = offsets[b[c + 1]];
+        if (e1 > e0) {
+            CUDA_TRY(h, cudaMemcpyAsync(dids + e0 * 8, ids + e0, (size_t)(e1 - e0) * 8, cudaMemcpyHostToDevice, s_in));
+            CUDA_TRY(h, cudaMemcpyAsync(dw + e0 * 8, weights + e0, (size_t)(e1 - e0) * 8, cudaMemcpyHostToDevice, s_in));
+        }
+        CUDA_TRY(h, cudaEventRecord(ev_in(c), s_in));
+    }
+    // chunks alternate between two compute streams (each with its own workspace), so that one
+    // chunk's kernels fill the SMs the other's tail leaves idle; each family's rows go back as
+    // soon as that family's kernel is done
+    for (int c = 0; c < k; c++) {
+        const int64_t s0 = b[c], sc = b[c + 1] - b[c];
+        const int r = c & 1;
+        cudaStream_t s_run = hp.s[1 + r];
+        CUDA_TRY(h, cudaStreamWaitEvent(s_run, ev_in(c), 0));
+        if (c >= 2) CUDA_TRY(h, cudaStreamWaitEvent(s_run, ev_out(c - 2), 0));   // chunk outputs are double-buffered
+        rc = sketch_device(h, r, (const uint64_t *)dids, (const double *)dw, doff + s0, sc, m, variants, num_variants,
+                           precision, seed, (uint64_t *)hp.z[r], out_q ? (double *)hp.q[r] : nullptr,
+                           set_status ? (int32_t *)hp.st[r] : nullptr, nullptr, s_run, false, ev_fam(c));
+        if (rc) {
+            for (int i = 0; i < 4; i++) cudaStreamSynchronize(hp.s[i]);
+            return rc;
+        }
+        for (int f = 1; f <= 4; f++) {
+            if (fam_rank[f] < 0) continue;
+            CUDA_TRY(h, cudaStreamWaitEvent(s_out, ev_fam(c)[fam_rank[f]], 0));
+            for (int64_t v = 0; v < V; v++) {
+                if (family_of(variants[v]) != f) continue;
+                CUDA_TRY(h, cudaMemcpyAsync(out_ids + (v * num_sets + s0) * m, (const uint64_t *)hp.z[r] + v * sc * m,
+                                            (size_t)(sc * m) * 8, cudaMemcpyDeviceToHost, s_out));
+                if (out_q)
+                    CUDA_TRY(h, cudaMemcpyAsync(out_q + (v * num_sets + s0) * m, (const double *)hp.q[r] + v * sc * m,
+                                                (size_t)(sc * m) * 8, cudaMemcpyDeviceToHost, s_out));
+                if (set_status)
+                    CUDA_TRY(h, cudaMemcpyAsync(set_status + v * num_sets + s0, (const int32_t *)hp.st[r] + v * sc,
+                                                (size_t)sc * 4, cudaMemcpyDeviceToHost, s_out));
+            }
+        }
+        CUDA_TRY(h, cudaEventRecord(ev_out(c), s_out));
+    }
+    for (int i = 0; i < 4; i++) CUDA_TRY(h, cudaStreamSynchronize(hp.s[i]));
+    h->last_chunks = k;
     return PMH_OK;
 }
 

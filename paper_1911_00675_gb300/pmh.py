@@ -23,7 +23,8 @@ FP64, FP32_RECHECK = 0, 1
 SHAPE_WARP, SHAPE_CTA8, SHAPE_QUAD, SHAPE_PAIR, SHAPE_QUAD8, SHAPE_QUAD8L = range(6)
 COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "rounds", "deep", "prefiltered",
             "cyc_pass0", "cyc_first", "cyc_deep", "cyc_refresh", "cyc_finish", "items", "cyc_surv", "reserved15")
-EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_sketch_batch_noalloc",
+EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_sketch_batch_host",
+           "pmh_sketch_batch_noalloc",
            "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_last_launches", "pmh_set_thresholds",
            "pmh_set_team_shape", "pmh_set_autotune", "pmh_last_team_shapes",
            "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge")
@@ -56,6 +57,9 @@ def load(path: str = LIB_PATH):
             lib.pmh_sketch_batch.restype = i32
             lib.pmh_sketch_batch.argtypes = [vp, vp, vp, vp, i64, u32, ctypes.POINTER(i32), i32, i32, u64, vp, vp, vp,
                                              vp, vp]
+            lib.pmh_sketch_batch_host.restype = i32
+            lib.pmh_sketch_batch_host.argtypes = [vp, vp, vp, vp, i64, u32, ctypes.POINTER(i32), i32, i32, u64, vp, vp,
+                                                  vp, i32]
             lib.pmh_sketch_batch_noalloc.restype = i32
             lib.pmh_sketch_batch_noalloc.argtypes = [vp, vp, vp, i64, u32, ctypes.POINTER(i32), i32, i32, u64, vp, vp,
                                                      vp, vp, vp]
@@ -164,6 +168,31 @@ class Handle:
         return out_ids, out_q, status
 
     # -- pmh_set_profiling / pmh_last_kernel_ms ------------------------------
+    # -- pmh_sketch_batch_host ----------------------------------------------
+    def sketch_batch_host(self, ids, weights, offsets, m: int, variants=("1",), precision: int = FP32_RECHECK,
+                          seed: int = 0, out_ids=None, out_q=None, status=None, with_q: bool = False,
+                          with_status: bool = True, chunks: int = 0):
+        """Host-buffer sketch (CPU tensors, ideally pinned): returns (out_ids [V, S, m] int64 CPU tensor,
+        out_q or None, status or None).  The library copies, sketches and copies back in a pipeline."""
+        for t, name, dts in ((ids, "ids", _I64), (weights, "weights", (torch.float64,)), (offsets, "offsets", (torch.int64,))):
+            if t.is_cuda or t.dtype not in dts or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous CPU tensor of dtype {dts}")
+        vs = [VARIANTS[v] if isinstance(v, str) else int(v) for v in variants]
+        s = offsets.numel() - 1
+        pin = torch.cuda.is_available()
+        if out_ids is None:
+            out_ids = torch.empty((len(vs), s, m), dtype=torch.int64, pin_memory=pin)
+        if out_q is None and with_q:
+            out_q = torch.empty((len(vs), s, m), dtype=torch.float64, pin_memory=pin)
+        if status is None and with_status:
+            status = torch.empty((len(vs), s), dtype=torch.int32, pin_memory=pin)
+        arr = (ctypes.c_int32 * len(vs))(*vs)
+        rc = load().pmh_sketch_batch_host(self._h, _ptr(ids), _ptr(weights), _ptr(offsets), s, m, arr, len(vs),
+                                          int(precision), int(seed) & (2**64 - 1), _ptr(out_ids), _ptr(out_q),
+                                          _ptr(status), int(chunks))
+        self._raise(rc)
+        return out_ids, out_q, status
+
     def set_profiling(self, enable: bool = True):
         self._raise(load().pmh_set_profiling(self._h, 1 if enable else 0))
 
