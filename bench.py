@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="wall budget of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--team-shape", type=int, default=-1,
+                    help="pin the sketch kernels' team shape (0 warp, 1 cta8, 2 quad, 3 pair, 4 quad8, 5 quad8l); "
+                         "-1 = autotuned")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the per-kernel measurements beside the headline (huge set, all-pairs counts)")
     return ap.parse_args()
@@ -103,6 +106,29 @@ def oracle_throughput(batch, seconds, cores, rng_seed=1):
         el = time.perf_counter() - t0
         pool.terminate()
     return done_elems / el, done_elems, done_tasks, el
+
+
+# ------------------------------------------------------------------ host placement
+def bind_gpu_local_cpus(gpu_index):
+    """Restricts this process to the CPU cores attached to the GPU (its PCI device's local_cpulist),
+    so that pinned host buffers are first touched on the memory next to it.  Returns the core list
+    string, or None when the topology is not readable."""
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader", "-i", str(gpu_index)],
+                             capture_output=True, text=True, timeout=30).stdout.strip()
+        dom, rest = out.split(":", 1)
+        path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest.lower()}/local_cpulist"
+        with open(path) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        if cpus and cpus != set(range(os.cpu_count() or 0)):
+            os.sched_setaffinity(0, cpus)
+        return spec
+    except Exception:
+        return None
 
 
 # ------------------------------------------------------------------ peaks
@@ -242,7 +268,7 @@ def run_reference(args, rank, world):
     import numpy as np
     from paper_1911_00675_gb300 import workloads as W
     batch = W.batch_c2(num_sets=args.num_sets)
-    cores = os.cpu_count() or 1
+    cores = len(os.sched_getaffinity(0)) or 1
     per_step = max(2.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
     vals = []
     for step in range(args.warmup + args.steps):
@@ -279,6 +305,7 @@ def main():
     from paper_1911_00675_gb300 import build, pmh
     from paper_1911_00675_gb300 import workloads as W
 
+    local_cpus = bind_gpu_local_cpus(local)
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -303,6 +330,8 @@ def main():
     st32 = torch.empty((len(VARIANTS), S), dtype=torch.int32, device=dev)
     st64 = torch.empty_like(st32)
     h = pmh.Handle(local)
+    if args.team_shape >= 0:
+        h.set_team_shape(0, args.team_shape)
     stream = torch.cuda.current_stream()
 
     def step(prec, out, st):
@@ -387,7 +416,8 @@ def main():
         h2d = ids_h.numel() * 8 + w_h.numel() * 8 + off_h.numel() * 8
         d2h = out_h.numel() * 8
         e2e = {"value": work * world / (te * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": te, "timing": "host wall clock around the blocking call", "identical_output": identical_e2e}
+               "ms_per_step": te, "timing": "host wall clock around the blocking call", "identical_output": identical_e2e,
+               "host_cpus": local_cpus}
 
     # ---------------- roofline of the dominant kernel (the persistent sketch kernel)
     k_avg = statistics.mean(kernel_ms)
@@ -416,7 +446,7 @@ def main():
     # ---------------- CPU baseline (rank 0, N=1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cores = os.cpu_count() or 1
+        cores = len(os.sched_getaffinity(0)) or 1
         v, el, tasks, sec = oracle_throughput(batch, args.cpu_seconds, cores)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{tasks} random (set, variant) tasks, {el} elements, {sec:.1f} s wall on {cores} processes"}
@@ -431,6 +461,7 @@ def main():
                                    "variants 1,1a,2,3,3a,4 in one persistent launch",
                        "m": m, "num_sets": S, "elements_per_rank": n_elem, "variants": VARIANTS,
                        "precision": "fp32 candidates + fp64 recheck", "parallelism": f"weak x{world}",
+                       "team_shapes": h.last_team_shapes(),
                        "l2": f"inputs {(16 * n_elem + 8 * S) / 1e9:.2f} GB per step > 129 MB L2"},
             "fp64": {"value": work * world / (t64 * 1e-3), "ms_per_step": t64, "kernel_ms": statistics.mean(k64),
                      "speedup_fp32_vs_fp64": t64 / t32},

@@ -127,6 +127,7 @@ struct TeamShared {
     int sigma;
     double bound64;     // FP64 path: exact stop bound
     float t_s;          // T * 2^sigma
+    unsigned long long next;   // next unclaimed element of the current pass (warps claim 64 at a time)
     uint32_t cont_k[kMaxCont];
     uint32_t cont_e[kMaxCont];
 };
@@ -750,7 +751,15 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
     __syncwarp();
     bool refreshed = false;
     int steps = 0;
-    for (uint32_t base = lo + tw * 64; base < hi; base += team_warps * 64) {
+    (void)tw;
+    for (;;) {
+        // dynamic claim of the next 64 elements of the pass (ts->next starts at lo)
+        unsigned long long claim = 0;
+        if (lane == 0) claim = TW == 1 ? ts->next : atomicAdd(&ts->next, 64ull);
+        if (TW == 1 && lane == 0) ts->next = claim + 64ull;
+        claim = __shfl_sync(kFull, claim, 0);
+        if (claim >= (unsigned long long)hi) break;
+        const uint32_t base = (uint32_t)claim;
         if (c.gbound32 && (steps++ & 15) == 0) {
             // grid mode: adopt the bound published by the other CTAs of this item
             if (lane == 0) {
@@ -895,6 +904,7 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
     // ---- rounds
     for (int round = 0; round <= P.rounds; ++round) {
         if (leader) {
+            ts->next = 0ull;
             if (round < P.rounds && !isinf(ts->t_s)) {
                 ts->bound32 = ldexpf(ts->t_s, 2 * round);
                 ts->bound64 = ldexp((double)ts->t_s, 2 * round - c.sigma);
@@ -1099,7 +1109,11 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
         uint64_t chunk = (uint64_t)c.n / (4ull * gridDim.x);
         chunk = chunk < kGridChunkMin ? kGridChunkMin : (chunk > kGridChunk ? kGridChunk : chunk);
         for (;;) {
-            if (leader) ts->item_idx = (int)atomicAdd(&g->next_chunk, 1u);
+            if (leader) {
+                const unsigned int idx = atomicAdd(&g->next_chunk, 1u);
+                ts->item_idx = (int)idx;
+                ts->next = (unsigned long long)idx * chunk;
+            }
             __syncthreads();
             const uint64_t lo = (uint64_t)(uint32_t)ts->item_idx * chunk;
             __syncthreads();
