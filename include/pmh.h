@@ -199,13 +199,19 @@ pmh_status pmh_sketch_batch_noalloc(const uint64_t *ids, const double *weights, 
 /*
  * Profiling.  pmh_set_profiling(h, 1) makes every later pmh_sketch_batch on
  * `h` record CUDA events on its stream before the work-queue build, between
- * the queue build and the persistent sketch kernel, and after the kernel.
- * pmh_last_kernel_ms waits for the most recent such call to finish and
- * returns the two intervals in milliseconds (queue build, sketch kernel).
- * Returns PMH_ERR_INVALID_ARG if profiling was off for that call.
+ * the queue build and the sketch kernels, and after them (each call its own
+ * events from a ring of 256; profiled calls are launched directly, not from
+ * a CUDA graph; calls during a stream capture are not profiled).
+ * pmh_last_kernel_ms waits for the most recent call to finish and returns its
+ * two intervals in milliseconds (queue build, sketch kernels); it returns
+ * PMH_ERR_INVALID_ARG if that call was not profiled.
+ * pmh_kernel_ms_history returns the same pair for up to `max_calls` most
+ * recent profiled calls (oldest first) into host float arrays of that length
+ * (either may be NULL), waits for the newest, and stores the number in *count.
  */
 pmh_status pmh_set_profiling(pmh_handle h, int32_t enable);
 pmh_status pmh_last_kernel_ms(pmh_handle h, float *queue_ms, float *sketch_ms);
+pmh_status pmh_kernel_ms_history(pmh_handle h, int32_t max_calls, float *queue_ms, float *sketch_ms, int32_t *count);
 
 /*
  * Team shapes of the persistent sketch kernel (no counterpart in the paper:

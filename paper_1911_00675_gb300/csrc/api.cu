@@ -93,8 +93,11 @@ struct pmh_handle_s {
     cudaEvent_t tev[3 + 4] = {};             // autotuning: queue/sketch brackets + one per family
     // profiling events
     bool profiling = false;
-    bool prof_recorded = false;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool prof_recorded = false;        // the most recent call was profiled
+    // profiled calls take the next slot of a ring of event triplets (no graph replay for them)
+    static constexpr int kRing = 256;
+    std::vector<cudaEvent_t> ring;     // kRing * 3 events, created by pmh_set_profiling
+    int64_t prof_calls = 0;            // profiled calls so far (slot = (prof_calls - 1) % kRing)
 };
 
 void pmh::set_thread_error(const char *msg) { g_create_error = msg; }
@@ -184,9 +187,8 @@ static pmh_status ensure_workspace(pmh_handle h, Workspace &w, int64_t num_sets,
 
 // Enqueues the whole batch on `st` with workspace `w`.
 static pmh_status enqueue_sketch(pmh_handle h, Workspace &w, const SketchParams &p, const Plan &plan, int precision,
-                                 cudaStream_t st, cudaEvent_t *fam_ev) {
-    cudaError_t e = enqueue_batch(p, plan, precision, h->sm_count, w.queue, w.qmeta, w.stats, st,
-                                  h->profiling ? h->ev : nullptr, fam_ev);
+                                 cudaStream_t st, cudaEvent_t *prof_ev, cudaEvent_t *fam_ev) {
+    cudaError_t e = enqueue_batch(p, plan, precision, h->sm_count, w.queue, w.qmeta, w.stats, st, prof_ev, fam_ev);
     if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "sketch launch: %s", cudaGetErrorString(e));
     return PMH_OK;
 }
@@ -220,7 +222,7 @@ extern "C" void pmh_destroy(pmh_handle h) {
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
-    for (int i = 0; i < 3; i++) if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    for (cudaEvent_t e : h->ring) cudaEventDestroy(e);
     for (int i = 0; i < 7; i++) if (h->tev[i]) cudaEventDestroy(h->tev[i]);
     for (auto &kv : h->tables) cudaFree(kv.second.dev);
     for (Workspace &w : h->ws) {
@@ -243,8 +245,11 @@ extern "C" pmh_status pmh_set_profiling(pmh_handle h, int32_t enable) {
     if (!h) return PMH_ERR_INVALID_ARG;
     h->err.clear();
     CUDA_TRY(h, cudaSetDevice(h->device));
-    if (enable && !h->ev[0])
-        for (int i = 0; i < 3; i++) CUDA_TRY(h, cudaEventCreate(&h->ev[i]));
+    while (enable && (int)h->ring.size() < 3 * pmh_handle_s::kRing) {
+        cudaEvent_t e;
+        CUDA_TRY(h, cudaEventCreate(&e));
+        h->ring.push_back(e);
+    }
     h->profiling = enable != 0;
     return PMH_OK;
 }
@@ -299,13 +304,29 @@ extern "C" pmh_status pmh_last_launches(pmh_handle h, int32_t *launches) {
 extern "C" pmh_status pmh_last_kernel_ms(pmh_handle h, float *queue_ms, float *sketch_ms) {
     if (!h) return PMH_ERR_INVALID_ARG;
     h->err.clear();
-    if (!h->prof_recorded || !h->ev[0]) return fail(h, PMH_ERR_INVALID_ARG, "profiling was off for the last call");
-    CUDA_TRY(h, cudaEventSynchronize(h->ev[2]));
-    float a = 0.0f, b = 0.0f;
-    CUDA_TRY(h, cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
-    CUDA_TRY(h, cudaEventElapsedTime(&b, h->ev[1], h->ev[2]));
-    if (queue_ms) *queue_ms = a;
-    if (sketch_ms) *sketch_ms = b;
+    if (!h->prof_recorded || h->prof_calls == 0) return fail(h, PMH_ERR_INVALID_ARG, "profiling was off for the last call");
+    int32_t n = 0;
+    return pmh_kernel_ms_history(h, 1, queue_ms, sketch_ms, &n);
+}
+
+extern "C" pmh_status pmh_kernel_ms_history(pmh_handle h, int32_t max_calls, float *queue_ms, float *sketch_ms,
+                                            int32_t *count) {
+    if (!h || !count || max_calls < 0) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    const int64_t n = std::min<int64_t>({(int64_t)max_calls, h->prof_calls, (int64_t)pmh_handle_s::kRing});
+    *count = 0;
+    if (n == 0) return PMH_OK;
+    const int64_t last = (h->prof_calls - 1) % pmh_handle_s::kRing;
+    CUDA_TRY(h, cudaEventSynchronize(h->ring[3 * last + 2]));
+    for (int64_t j = 0; j < n; j++) {
+        const int64_t slot = (h->prof_calls - n + j) % pmh_handle_s::kRing;
+        float a = 0.0f, b = 0.0f;
+        CUDA_TRY(h, cudaEventElapsedTime(&a, h->ring[3 * slot], h->ring[3 * slot + 1]));
+        CUDA_TRY(h, cudaEventElapsedTime(&b, h->ring[3 * slot + 1], h->ring[3 * slot + 2]));
+        if (queue_ms) queue_ms[j] = a;
+        if (sketch_ms) sketch_ms[j] = b;
+    }
+    *count = (int32_t)n;
     return PMH_OK;
 }
 
@@ -425,24 +446,27 @@ static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, cons
     h->last_launches = launch_count(plan, p.gctl != nullptr);
     for (int f = 0; f < 4; f++) h->last_shape[f] = -1;
     for (int j = 0; j < plan.nfam; j++) h->last_shape[plan.fam[j] - 1] = plan.shape[j].kind;
-    if (!allow_graph || wsi != 0 || fam_ev || !h->use_graph || cs != cudaStreamCaptureStatusNone || !st) {
-        h->prof_recorded = h->profiling;
-        return enqueue_sketch(h, w, p, plan, precision, st, fam_ev);
+    cudaEvent_t *prof_ev = nullptr;
+    if (h->profiling && cs == cudaStreamCaptureStatusNone && (int)h->ring.size() == 3 * pmh_handle_s::kRing) {
+        prof_ev = h->ring.data() + 3 * (h->prof_calls % pmh_handle_s::kRing);
+        h->prof_calls++;
     }
+    h->prof_recorded = prof_ev != nullptr;
+    if (!allow_graph || wsi != 0 || fam_ev || prof_ev || !h->use_graph || cs != cudaStreamCaptureStatusNone || !st)
+        return enqueue_sketch(h, w, p, plan, precision, st, prof_ev, fam_ev);
 
     GraphKey key{};
     key.ids = ids; key.weights = weights; key.offsets = offsets; key.out_ids = out_ids; key.out_q = out_q;
     key.status = set_status; key.counters = counters; key.num_sets = num_sets; key.m = m;
     for (int v = 0; v < num_variants; v++) key.variants[v] = variants[v];
     key.num_variants = num_variants; key.precision = precision; key.seed = seed;
-    key.profiling = h->profiling ? 1 : 0;
+    key.profiling = 0;
     for (int f = 0; f < 4; f++) key.kinds[f] = kinds[f];
-    h->prof_recorded = h->profiling;
     if (!(h->graph_valid && h->gkey == key)) {
         if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
         h->graph_valid = false;
         CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_sketch(h, w, p, plan, precision, h->cap_stream, nullptr);
+        rc = enqueue_sketch(h, w, p, plan, precision, h->cap_stream, nullptr, nullptr);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
         if (rc) { if (g) cudaGraphDestroy(g); return rc; }

@@ -134,11 +134,11 @@ struct TeamShared {
 
 struct WarpShared {
     unsigned long long cnt[PMH_NUM_COUNTERS];   // work counters of this warp (lane 0 adds)
-    uint32_t dq[kSurvCap];     // deep-mode queue (element indices)
-    int dq_n;
+    int dq_n;                  // deep-mode queue length (the queue reuses sb_e, see process_survivors)
     int slot[32];              // Fisher-Yates scratch (deep mode)
     uint32_t sb_e[kSurvCap];   // prefilter survivors: element index
-    uint64_t sb_key[kSurvCap]; //   and stream key
+    uint64_t sb_key[kSurvCap]; //   stream key
+    float sb_winv[kSurvCap];   //   and scaled FP32 reciprocal weight
     int sb_n;
 };
 
@@ -605,9 +605,12 @@ __device__ bool process_survivors(Ctx<F32> &c, int n) {
                 const int j = next + rank;
                 e = ws->sb_e[j];
                 key = ws->sb_key[j];
-                const double w = P.weights[c.beg + e];
-                winv32 = winv_scaled(w, c.sigma);
-                if constexpr (!F32) { w_inv = __drcp_rn(w); id = P.ids[c.beg + e]; }
+                winv32 = ws->sb_winv[j];
+                if constexpr (!F32) {
+                    const double w = P.weights[c.beg + e];
+                    w_inv = __drcp_rn(w);
+                    id = P.ids[c.beg + e];
+                }
                 i = 1;
                 s32 = 0.0f;
                 x64 = 0.0;
@@ -616,6 +619,8 @@ __device__ bool process_survivors(Ctx<F32> &c, int n) {
             }
             next += min(__popc(idle), avail);
         }
+        // every taken slot has been read: the deep queue may now reuse sb_e[0, next)
+        __syncwarp();
         if (!__any_sync(kFull, has)) break;
         if (has) {
             bool done = false, to_deep = false;
@@ -702,8 +707,9 @@ __device__ bool process_survivors(Ctx<F32> &c, int n) {
                 i++;
             }
             if (to_deep) {
-                const int at = atomicAdd(&ws->dq_n, 1);   // at most one entry per survivor (n <= kSurvCap)
-                if (at < kSurvCap) ws->dq[at] = e;
+                // at most one entry per taken survivor, so at < next: the slot was read already
+                const int at = atomicAdd(&ws->dq_n, 1);
+                if (at < kSurvCap) ws->sb_e[at] = e;
                 done = true;
             }
             if (done) has = false;
@@ -715,7 +721,7 @@ __device__ bool process_survivors(Ctx<F32> &c, int n) {
     const int total_deep = min(ws->dq_n, kSurvCap);
     if (total_deep) {
         const long long td = clock64();
-        for (int j = 0; j < total_deep; ++j) deep<FAM, F32, false>(c, ws->dq[j], 0);
+        for (int j = 0; j < total_deep; ++j) deep<FAM, F32, false>(c, ws->sb_e[j], 0);
         count(c, PMH_CNT_CYC_DEEP, (unsigned long long)(clock64() - td));
     }
     count(c, PMH_CNT_CYC_SURV, (unsigned long long)(clock64() - t_sv));
@@ -784,6 +790,7 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
         bool surv[2];
         uint64_t key[2];
         uint32_t ev[2];
+        float winv[2];
         bool valid[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -791,13 +798,15 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
             ev[h] = e;
             surv[h] = false;
             key[h] = 0;
+            winv[h] = 0.0f;
             valid[h] = false;
             if (e < hi) {
                 const double w = P.weights[c.beg + e];
                 if (weight_positive(w)) {
                     valid[h] = true;
                     key[h] = mix64(P.ids[c.beg + e] ^ P.mixed_seed);
-                    const float xlo = winv_scaled(w, c.sigma) * unif_lo(value_word(key[h], 1)) * te_lo;
+                    winv[h] = winv_scaled(w, c.sigma);
+                    const float xlo = winv[h] * unif_lo(value_word(key[h], 1)) * te_lo;
                     surv[h] = !(xlo * (1.0f - 8.0f * 0x1p-24f) > ld_volatile(&ts->bound32));
                 }
             }
@@ -812,6 +821,7 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
                 if (pos < kSurvCap) {   // always true: n <= kSurvBatch - 1 before the two appends of <= 32
                     ws->sb_e[pos] = ev[h];
                     ws->sb_key[pos] = key[h];
+                    ws->sb_winv[pos] = winv[h];
                 } else {
                     ts->status = PMH_ERR_ITER_LIMIT;
                 }

@@ -25,7 +25,8 @@ COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "round
             "cyc_pass0", "cyc_first", "cyc_deep", "cyc_refresh", "cyc_finish", "items", "cyc_surv", "reserved15")
 EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_sketch_batch_host",
            "pmh_sketch_batch_noalloc",
-           "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_last_launches", "pmh_set_thresholds",
+           "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_kernel_ms_history", "pmh_last_launches",
+           "pmh_set_thresholds",
            "pmh_set_team_shape", "pmh_set_autotune", "pmh_last_team_shapes",
            "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge")
 
@@ -67,6 +68,9 @@ def load(path: str = LIB_PATH):
             lib.pmh_set_profiling.argtypes = [vp, i32]
             lib.pmh_last_kernel_ms.restype = i32
             lib.pmh_last_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+            lib.pmh_kernel_ms_history.restype = i32
+            lib.pmh_kernel_ms_history.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float),
+                                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32)]
             lib.pmh_last_launches.restype = i32
             lib.pmh_last_launches.argtypes = [vp, ctypes.POINTER(i32)]
             lib.pmh_set_team_shape.restype = i32
@@ -195,6 +199,14 @@ class Handle:
 
     def set_profiling(self, enable: bool = True):
         self._raise(load().pmh_set_profiling(self._h, 1 if enable else 0))
+
+    def kernel_ms_history(self, max_calls: int):
+        """(queue_ms list, sketch_ms list) of up to max_calls most recent profiled calls, oldest first."""
+        qa = (ctypes.c_float * max(1, max_calls))()
+        ka = (ctypes.c_float * max(1, max_calls))()
+        n = ctypes.c_int32()
+        self._raise(load().pmh_kernel_ms_history(self._h, int(max_calls), qa, ka, ctypes.byref(n)))
+        return list(qa[:n.value]), list(ka[:n.value])
 
     def last_launches(self) -> int:
         """Kernels launched by the most recent sketch_batch call."""

@@ -143,3 +143,22 @@ def test_c5_full_size(H, precision):
     stats = {"near": 0, "components": 0}
     check_sets(b, "3a", z[0], q[0], [0], seed=0, stats=stats)
     assert stats["near"] <= 4
+
+
+def test_profiling_history_records_each_call(H):
+    b = W.random_batch(38, [100, 2000, 5], 64, "uniform")
+    H.set_profiling(True)
+    try:
+        for _ in range(5):
+            run(H, b, ["1", "3"], 1)
+        q, k = H.kernel_ms_history(8)
+        assert len(q) == 5 and len(k) == 5
+        assert all(x > 0 for x in k) and all(x >= 0 for x in q)
+        q1, k1 = H.last_kernel_ms()
+        assert k1 == k[-1] and q1 == q[-1]
+    finally:
+        H.set_profiling(False)
+    run(H, b, ["1"], 1)
+    from paper_1911_00675_gb300 import pmh
+    with pytest.raises(pmh.PmhError):
+        H.last_kernel_ms()
