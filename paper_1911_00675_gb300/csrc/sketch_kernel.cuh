@@ -758,14 +758,19 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
     bool refreshed = false;
     int steps = 0;
     (void)tw;
+    // claim size: 64 elements, or less for short ranges so that every warp of the
+    // team gets a share of the survivors (about four claims per warp)
+    const unsigned long long csz = TW == 1 ? 64ull
+        : min(64ull, max(1ull, ((unsigned long long)(hi - lo) + 4ull * TW - 1ull) / (4ull * TW)));
     for (;;) {
-        // dynamic claim of the next 64 elements of the pass (ts->next starts at lo)
+        // dynamic claim of the next csz elements of the pass (ts->next starts at lo)
         unsigned long long claim = 0;
-        if (lane == 0) claim = TW == 1 ? ts->next : atomicAdd(&ts->next, 64ull);
-        if (TW == 1 && lane == 0) ts->next = claim + 64ull;
+        if (lane == 0) claim = TW == 1 ? ts->next : atomicAdd(&ts->next, csz);
+        if (TW == 1 && lane == 0) ts->next = claim + csz;
         claim = __shfl_sync(kFull, claim, 0);
         if (claim >= (unsigned long long)hi) break;
         const uint32_t base = (uint32_t)claim;
+        const uint32_t end = (uint32_t)min((unsigned long long)hi, claim + csz);
         if (c.gbound32 && (steps++ & 15) == 0) {
             // grid mode: adopt the bound published by the other CTAs of this item
             if (lane == 0) {
@@ -800,7 +805,7 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
             key[h] = 0;
             winv[h] = 0.0f;
             valid[h] = false;
-            if (e < hi) {
+            if (e < end) {
                 const double w = P.weights[c.beg + e];
                 if (weight_positive(w)) {
                     valid[h] = true;
