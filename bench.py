@@ -42,6 +42,10 @@ OPS_FIRST_REJECT = 26   # value word (20) + log-free lower bound and compare (6)
 OPS_POINT = 60          # value word (20) + label word (20) + logarithm (~10) + scale/compare (5) + offer (5)
 LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes issue one instruction per clock
 OPS_PAIR_COMPONENT = 3  # equal-component count: two 32-bit compares and one add per component pair
+# DRAM bytes (read + write) of the four family sketch kernels per element-variant, from the ncu
+# capture summarised in profiles/sketch_kernel_pair_c2_2000sets_full.md (same kernel source); the
+# traffic grows in proportion to the elements (one pass over ids and weights per family).
+TRAFFIC_BYTES_PER_ELEMENT_VARIANT = 13.34
 
 
 def parse():
@@ -426,7 +430,9 @@ def main():
     achieved = per_launch_ops / (k_avg * 1e-3) / 1e12
     peak = n_sms * LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (32-bit lane ops)",
-                "frac": achieved / peak, "traffic": None, "kernel": "pmh::sketch_kernel<FP32>",
+                "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_ELEMENT_VARIANT * work,
+                "traffic_basis": "ncu dram bytes per element-variant on a 2,000-set c2-shaped batch x this step's work",
+                "kernel": "pmh::sketch_kernel<FP32> (four family launches per step)",
                 "kernel_ms": k_avg, "ops_per_launch": per_launch_ops,
                 "peak_basis": f"{n_sms} SMs x {LANES_PER_SM_CLK} lane-ops/clk x {sm_mhz:.0f} MHz (median under load)"}
 
