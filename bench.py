@@ -417,7 +417,7 @@ def main():
     statuses_ok = bool((st32 == 0).all().item() and (st64 == 0).all().item())
 
     # ---------------- counters of one (untimed) step
-    cnt = torch.zeros(16, dtype=torch.int64, device=dev)
+    cnt = torch.zeros(len(pmh.COUNTERS), dtype=torch.int64, device=dev)
     h.sketch_batch(ids, w, off, m, VARIANTS, pmh.FP32_RECHECK, 0, out_ids=out32, status=st32, counters=cnt)
     torch.cuda.synchronize()
     c = dict(zip(pmh.COUNTERS, cnt.cpu().tolist()))

@@ -75,14 +75,16 @@ enum {
     PMH_CNT_DEEP = 6,         /* elements processed warp-cooperatively */
     PMH_CNT_PREFILTERED = 7,  /* elements rejected without evaluating a logarithm */
     /* SM clock cycles spent per phase, summed over warps (timers read by lane 0) */
-    PMH_CNT_CYC_PASS0 = 8,    /* weight validation and weight sum */
-    PMH_CNT_CYC_FIRST = 9,    /* first points and short sequences (lane per element) */
-    PMH_CNT_CYC_DEEP = 10,    /* warp-cooperative expansion of long sequences */
+    PMH_CNT_CYC_PASS0 = 8,    /* item setup: empty signature, threshold */
+    PMH_CNT_CYC_FIRST = 9,    /* threshold rounds: filter, survivors, deep mode, team barrier at their end */
+    PMH_CNT_CYC_DEEP = 10,    /* warp-cooperative expansion of long sequences (part of CYC_SURV) */
     PMH_CNT_CYC_REFRESH = 11, /* q_max refreshes */
     PMH_CNT_CYC_FINISH = 12,  /* contender resolution and write-out */
     PMH_CNT_ITEMS = 13,       /* items processed */
-    PMH_CNT_CYC_SURV = 14,    /* survivor processing and segments (includes deep mode) */
-    PMH_NUM_COUNTERS = 16
+    PMH_CNT_CYC_SURV = 14,    /* survivor expansion, lane-sequential and deep (part of CYC_FIRST) */
+    PMH_CNT_CYC_ITEM = 15,    /* whole items, from the queue fetch to the barrier after write-out */
+    PMH_CNT_CYC_WARP = 16,    /* warp lifetime in the sketch kernels (start to exit) */
+    PMH_NUM_COUNTERS = 20
 };
 
 /* Creates a handle bound to CUDA device `device` (the device is made current

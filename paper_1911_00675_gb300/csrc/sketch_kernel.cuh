@@ -144,10 +144,17 @@ struct WarpShared {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// ProbMinHash2/4 per-warp region: the dense permutation of deep mode (m x u16)
-// followed by the per-lane Fisher-Yates write lists (kFyCap x 32 x u32).
-constexpr int kFyCap = 32;
-__host__ __device__ inline size_t perm_bytes(uint32_t m) { return align16((size_t)m * 2) + (size_t)kFyCap * 32 * 4; }
+// ProbMinHash2/4 per-warp region, used in turn by the two expansion modes:
+// the per-lane Fisher-Yates write lists of lane-sequential expansion
+// (kFyCap x 32 x u32, live while a lane walks one element) and the dense
+// permutation of deep mode (m x u16, rebuilt for every element it expands).
+// A warp runs its deep elements only after its lane-sequential loop has ended,
+// so the two share the bytes.
+constexpr int kFyCap = 16;
+__host__ __device__ inline size_t perm_bytes(uint32_t m) {
+    const size_t dense = align16((size_t)m * 2), lists = (size_t)kFyCap * 32 * 4;
+    return dense > lists ? dense : lists;
+}
 
 struct SmemLayout {
     size_t team_off, sig_off, warp_off, perm_off, total;
@@ -583,7 +590,7 @@ __device__ bool process_survivors(Ctx<F32> &c, int n) {
     const int lane = threadIdx.x & 31;
     WarpShared *ws = c.ws;
     constexpr bool kPerm = (FAM == 2 || FAM == 4);
-    constexpr int kCap = (FAM == 3) ? kSeqCap3 : kSeqCap;
+    constexpr int kCap = (FAM == 3) ? kSeqCap3 : (kPerm ? kFyCap : kSeqCap);   // the write list bounds ProbMinHash2/4
     bool has = false, won = false;
     uint32_t e = 0, i = 0;
     uint64_t key = 0, id = 0;
@@ -1192,7 +1199,7 @@ __global__ void __launch_bounds__(256, 2) grid_kernel(const __grid_constant__ Sk
     c.sig = smem + L.sig_off;
     c.ws = (WarpShared *)(smem + L.warp_off + (size_t)warp * align16(sizeof(WarpShared)));
     c.perm = kPerm ? (uint16_t *)(smem + L.perm_off + (size_t)warp * perm_bytes(p.m)) : nullptr;
-    c.fy = kPerm ? (uint32_t *)(smem + L.perm_off + (size_t)warp * perm_bytes(p.m) + align16((size_t)p.m * 2)) : nullptr;
+    c.fy = kPerm ? (uint32_t *)(smem + L.perm_off + (size_t)warp * perm_bytes(p.m)) : nullptr;   // shares the bytes of perm
     c.gbound32 = nullptr;
     c.gbound64 = nullptr;
     if (lane < PMH_NUM_COUNTERS) c.ws->cnt[lane] = 0;
@@ -1253,14 +1260,16 @@ __global__ void __launch_bounds__(NW * 32, MINB) sketch_kernel(const __grid_cons
     c.sig = smem + L.sig_off + (size_t)team * p.m * (F32 ? 8 : 16);
     c.ws = (WarpShared *)(smem + L.warp_off + (size_t)warp * align16(sizeof(WarpShared)));
     c.perm = kPerm ? (uint16_t *)(smem + L.perm_off + (size_t)warp * perm_bytes(p.m)) : nullptr;
-    c.fy = kPerm ? (uint32_t *)(smem + L.perm_off + (size_t)warp * perm_bytes(p.m) + align16((size_t)p.m * 2)) : nullptr;
+    c.fy = kPerm ? (uint32_t *)(smem + L.perm_off + (size_t)warp * perm_bytes(p.m)) : nullptr;   // shares the bytes of perm
     c.gbound32 = nullptr;
     c.gbound64 = nullptr;
     if (lane < PMH_NUM_COUNTERS) c.ws->cnt[lane] = 0;
     __syncwarp();
     const int tt = (warp % TW) * 32 + lane;   // thread index within the team
     const bool team_leader = tt == 0;
+    const long long t_warp = clock64();
     for (;;) {
+        const long long t_item = clock64();
         if (team_leader) ts->item_idx = (int)atomicAdd(p.head, 1u);
         team_sync<TW>();
         const int64_t qi = ts->item_idx;
@@ -1285,7 +1294,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) sketch_kernel(const __grid_cons
         c.n = (uint32_t)(e - b);
         process_item<FAM, F32, TW>(c, v, set);
         team_sync<TW>();
+        count(c, PMH_CNT_CYC_ITEM, (unsigned long long)(clock64() - t_item));
     }
+    count(c, PMH_CNT_CYC_WARP, (unsigned long long)(clock64() - t_warp));
     __syncwarp();
     if (p.counters && lane < PMH_NUM_COUNTERS && c.ws->cnt[lane]) atomicAdd(&p.counters[lane], c.ws->cnt[lane]);
 }

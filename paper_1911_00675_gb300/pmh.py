@@ -22,7 +22,8 @@ VARIANTS = {"1": V1, "1a": V1A, "2": V2, "3": V3, "3a": V3A, "4": V4}
 FP64, FP32_RECHECK = 0, 1
 SHAPE_WARP, SHAPE_CTA8, SHAPE_QUAD, SHAPE_PAIR, SHAPE_QUAD8, SHAPE_QUAD8L = range(6)
 COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "rounds", "deep", "prefiltered",
-            "cyc_pass0", "cyc_first", "cyc_deep", "cyc_refresh", "cyc_finish", "items", "cyc_surv", "reserved15")
+            "cyc_pass0", "cyc_first", "cyc_deep", "cyc_refresh", "cyc_finish", "items", "cyc_surv", "cyc_item",
+            "cyc_warp", "reserved17", "reserved18", "reserved19")
 EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_sketch_batch_host",
            "pmh_sketch_batch_noalloc",
            "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_kernel_ms_history", "pmh_last_launches",
@@ -164,6 +165,8 @@ class Handle:
         _check(out_q, "out_q", (torch.float64,), dev)
         _check(status, "status", (torch.int32,), dev)
         _check(counters, "counters", _I64, dev)
+        if counters is not None and counters.numel() < len(COUNTERS):
+            raise ValueError(f"counters needs {len(COUNTERS)} entries")
         arr = (ctypes.c_int32 * len(vs))(*vs)
         rc = load().pmh_sketch_batch(self._h, _ptr(ids), _ptr(weights), _ptr(offsets), s, m, arr, len(vs),
                                      int(precision), int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out_ids), _ptr(out_q),
@@ -311,6 +314,8 @@ def sketch_batch_noalloc(ids, weights, offsets, m, variants=("1",), precision=FP
     _check(out_q, "out_q", (torch.float64,), dev)
     _check(status, "status", (torch.int32,), dev)
     _check(counters, "counters", _I64, dev)
+    if counters is not None and counters.numel() < len(COUNTERS):
+        raise ValueError(f"counters needs {len(COUNTERS)} entries")
     arr = (ctypes.c_int32 * len(vs))(*vs)
     with torch.cuda.device(dev):
         rc = load().pmh_sketch_batch_noalloc(_ptr(ids), _ptr(weights), _ptr(offsets), s, m, arr, len(vs),

@@ -106,7 +106,7 @@ def test_counters_and_repeat_calls(H):
     from paper_1911_00675_gb300 import pmh
     b = W.random_batch(12, [100, 2000, 5], 256, "uniform")
     ids, w, off = to_dev(b)
-    cnt = torch.zeros(16, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(len(pmh.COUNTERS), dtype=torch.int64, device="cuda")
     outs = []
     for _ in range(3):   # the second and third calls replay the cached graph
         z, _, st = H.sketch_batch(ids, w, off, 256, VARS, 1, 0, counters=cnt)
