@@ -1180,9 +1180,11 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
 }
 
 // Persistent grid-mode kernel of one family: every CTA takes part in every
-// grid item of that family, in list order.
+// grid item of that family, in list order.  Registers are budgeted for four
+// 8-warp CTAs per SM (32 warps): the filter that dominates a huge set is
+// latency bound, so warps count more than the few spills.
 template <bool F32, int FAM>
-__global__ void __launch_bounds__(256, 2) grid_kernel(const __grid_constant__ SketchParams p) {
+__global__ void __launch_bounds__(256, 4) grid_kernel(const __grid_constant__ SketchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool kPerm = (FAM == 2 || FAM == 4);
     constexpr int NW = 8;
