@@ -285,6 +285,16 @@ pmh_status pmh_last_launches(pmh_handle h, int32_t *launches);
 pmh_status pmh_set_thresholds(pmh_handle h, double t_c, double t_c_grid, int32_t rounds, int64_t grid_min);
 
 /*
+ * pmh_check_exp1 -- the FP32 Exp(1) variate of the candidate path, E(word) =
+ * -ln(1 - U), U = (word >> 11) 2^-53 (the inversion of Sec. "ProbMinHash1",
+ * exponential spacings), for each of n device words into device float out[n],
+ * on `stream`.  For verification of its error bound against FP64; the sketch
+ * kernels use the same inline function.  Errors: PMH_ERR_INVALID_ARG for
+ * n < 0 or NULL pointers with n > 0, PMH_ERR_CUDA if the launch fails.
+ */
+pmh_status pmh_check_exp1(const uint64_t *words, int64_t n, float *out, void *stream);
+
+/*
  * pmh_estimate_allpairs -- numerators of the J_P estimator (Eq. jaccard_estimator)
  * for every pair of signatures: counts[a*num_sigs + b] = #{k : sigs[a][k] == sigs[b][k]}.
  *

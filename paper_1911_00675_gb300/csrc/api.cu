@@ -639,6 +639,20 @@ extern "C" pmh_status pmh_sketch_batch_host(pmh_handle h, const uint64_t *ids, c
     return PMH_OK;
 }
 
+// ------------------------------------------------------------------ verification
+static __global__ void check_exp1_kernel(const uint64_t *__restrict__ w, int64_t n, float *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = exp1_32(w[i]);
+}
+
+extern "C" pmh_status pmh_check_exp1(const uint64_t *words, int64_t n, float *out, void *stream) {
+    if (n < 0 || (n > 0 && (!words || !out))) return PMH_ERR_INVALID_ARG;
+    if (n == 0) return PMH_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    check_exp1_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(words, n, out);
+    return cudaGetLastError() == cudaSuccess ? PMH_OK : PMH_ERR_CUDA;
+}
+
 // ------------------------------------------------------------------ estimation
 // All-pairs equal-component counts, Eq. jaccard_estimator.  64x64 tile of
 // pairs per CTA, 16 components per shared-memory stage, 4x4 pairs per thread

@@ -20,7 +20,7 @@ constexpr uint32_t kFull = 0xFFFFFFFFu;
 // Relative error bound of every FP32 point value against its canonical FP64
 // value: |x32 - x64| <= kEta * x32.  The sources (each in units u = 2^-24):
 // 1/w from a truncated mantissa and a correctly rounded reciprocal (3u),
-// Exp(1) via log1pf/logf (max 1 ulp each) with a truncated U (6u),
+// Exp(1) via the reduced-range log1p below with a rounded U or 1 - U (6u),
 // Exp(lambda;0,1) via log1pf with |U*expm1(-lambda)| <= 1/2 (12u), the table
 // entries and their products (<= 4u), the FP32 sums of the uncorrelated
 // families (a lane-sequential running sum of at most 32 positive terms, <= 31u;
@@ -119,12 +119,48 @@ __device__ __forceinline__ float u53_to_float(uint64_t k) {
     const uint32_t ex = (uint32_t)(63 - lz - 53 + 127);
     return __uint_as_float((ex << 23) | mant);
 }
-// Exp(1): for U < 1/2 log1pf(-U) keeps relative accuracy; otherwise V = 1-U is
-// formed exactly in integers before the conversion.
+// log1p(f) for f in [sqrt(1/2) - 1, sqrt(2) - 1] as f + f^2 r(f), r a degree-8
+// polynomial fitted to (log1p(f) - f) / f^2 by weighted least squares on
+// Chebyshev nodes of that interval (weights: relative error of the result;
+// csrc/fit_log1p.py).  FP32 Horner evaluation: at most 1.35 ulp from log1p(f)
+// over the interval (checked against FP64 on 2e6 points).
+__device__ __forceinline__ float log1p_reduced(float f) {
+    float r = -0.07473210990428925f;
+    r = __fmaf_rn(r, f, 0.128195121884346f);
+    r = __fmaf_rn(r, f, -0.1326199471950531f);
+    r = __fmaf_rn(r, f, 0.14196686446666718f);
+    r = __fmaf_rn(r, f, -0.16608595848083496f);
+    r = __fmaf_rn(r, f, 0.200011745095253f);
+    r = __fmaf_rn(r, f, -0.2500157654285431f);
+    r = __fmaf_rn(r, f, 0.3333333730697632f);
+    r = __fmaf_rn(r, f, -0.49999988079071045f);
+    return __fmaf_rn(__fmul_rn(f, f), r, f);
+}
+
+// Exp(1) = -ln(1 - U), U = (w >> 11) 2^-53, without branches: the lanes of a
+// warp evaluate different points, and a two-way branch would run both ways.
+// 1 - U = 2^e (1 + f) with f in [sqrt(1/2) - 1, sqrt(2) - 1):
+//   U < 1 - sqrt(1/2): e = 0, f = -U (U converted once to FP32);
+//   otherwise V = 1 - U is formed exactly in integers, converted once, and its
+//   exponent and mantissa give e and f (exactly).
+// -ln(1 - U) = -(e ln2 + log1p(f)), with ln2 split so that e * ln2_hi is exact.
+// Error: at most ~2.1 ulp of the result for the first case (conversion of U
+// 0.7, log1p 1.35) and ~4 ulp for the second (conversion of V 1.45, log1p
+// 1.4, two roundings 1.0), measured against FP64 by tests/test_math_gpu.py.
 __device__ __forceinline__ float exp1_32(uint64_t w) {
-    uint64_t k = w >> 11;
-    if (k < (1ull << 52)) return -log1pf(-u53_to_float(k));
-    return -logf(u53_to_float((1ull << 53) - k));
+    const uint64_t k = w >> 11;
+    const bool small = k < 2638147582215219ull;                // U < 1 - sqrt(1/2)
+    const float x = u53_to_float(small ? k : (1ull << 53) - k);
+    const uint32_t b = __float_as_uint(x);
+    int e = (int)(b >> 23) - 127;
+    uint32_t mb = (b & 0x7FFFFFu) | 0x3F800000u;                // mantissa in [1, 2)
+    const bool high = mb >= 0x3FB504F3u;                       // >= sqrt(2): halve it
+    mb -= high ? 0x00800000u : 0u;
+    e += high ? 1 : 0;
+    const float f = small ? -x : __fsub_rn(__uint_as_float(mb), 1.0f);
+    const float ef = small ? 0.0f : (float)e;
+    const float lp = log1p_reduced(f);
+    return -__fmaf_rn(ef, 0x1.62e4p-1f, __fmaf_rn(ef, 0x1.7f7d1cp-20f, lp));
 }
 __device__ __forceinline__ float texp_32(uint64_t w, float c, float inv) {
     float l = log1pf(__fmul_rn(u53_to_float(w >> 11), c));

@@ -29,7 +29,7 @@ EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "p
            "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_kernel_ms_history", "pmh_last_launches",
            "pmh_set_thresholds",
            "pmh_set_team_shape", "pmh_set_autotune", "pmh_last_team_shapes",
-           "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge")
+           "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge", "pmh_check_exp1")
 
 _lib = None
 _lock = threading.Lock()
@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
             lib.pmh_estimate_allpairs.argtypes = [vp, vp, i64, u32, i32, vp, vp]
             lib.pmh_estimate_pairs.restype = i32
             lib.pmh_estimate_pairs.argtypes = [vp, vp, vp, vp, vp, i64, u32, vp, vp]
+            lib.pmh_check_exp1.restype = i32
+            lib.pmh_check_exp1.argtypes = [vp, i64, vp, vp]
             lib.pmh_merge.restype = i32
             lib.pmh_merge.argtypes = [vp, vp, vp, i64, u32, vp, vp, vp]
             _lib = lib
@@ -336,6 +338,16 @@ def estimate_pairs(sig_a, sig_b, pairs_a, pairs_b, **kw):
 
 def merge(q, z, **kw):
     return handle(q.device.index).merge(q, z, **kw)
+
+
+def check_exp1(words, stream=None):
+    """FP32 Exp(1) of each uint64 word as the candidate path computes it (CUDA int64 tensor in,
+    float32 tensor out)."""
+    out = torch.empty(words.numel(), dtype=torch.float32, device=words.device)
+    rc = load().pmh_check_exp1(_ptr(words), words.numel(), _ptr(out), _stream(stream))
+    if rc:
+        raise PmhError(rc, "pmh_check_exp1 failed")
+    return out
 
 
 def to_u64(t) -> "numpy.ndarray":

@@ -1,0 +1,38 @@
+"""The FP32 Exp(1) variate of the candidate path against FP64 -log1p(-U) (Sec. "ProbMinHash1":
+exponential spacings by inversion).  The precision scheme relies on every FP32 point value being
+within eta = 2^-18 of its FP64 value, with 6 ulp (2^-24) allotted to this variate; the measured
+worst case must stay within that allotment."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+ULP = 2.0 ** -24
+
+
+def _ref(words):
+    k = (words >> np.uint64(11)).astype(np.float64)
+    u = k * 2.0 ** -53
+    return -np.log1p(-u)
+
+
+def test_exp1_fp32_error_bound():
+    from paper_1911_00675_gb300 import build, pmh
+    build.build()
+    rng = np.random.default_rng(0)
+    w = rng.integers(0, 2**64, size=4_000_000, dtype=np.uint64)
+    # edges: U = 0, the smallest U, around the 1 - sqrt(1/2) switch, U -> 1, powers of two
+    k_edges = [0, 1, 2, 3, 2638147582215219 - 2, 2638147582215219 - 1, 2638147582215219, 2638147582215220,
+               2**52 - 1, 2**52, 2**52 + 1, 2**53 - 3, 2**53 - 2, 2**53 - 1]
+    k_edges += [2**j for j in range(53)] + [2**53 - 2**j for j in range(1, 53)]
+    k_edges += list(rng.integers(2638147582215219 - 10**6, 2638147582215219 + 10**6, size=1000))
+    edges = (np.array(k_edges, dtype=np.uint64) << np.uint64(11)) | np.uint64(0x5A5)
+    w = np.concatenate([w, edges])
+    got = pmh.check_exp1(torch.from_numpy(w.view(np.int64)).cuda()).cpu().numpy().astype(np.float64)
+    ref = _ref(w)
+    zero = ref == 0
+    assert np.all(got[zero] == 0)
+    rel = np.abs(got[~zero] - ref[~zero]) / ref[~zero]
+    assert rel.max() <= 6 * ULP, rel.max() / ULP
+    # and it is a real approximation of the inversion, not a looser one
+    assert np.mean(rel) < 1.5 * ULP
