@@ -387,16 +387,29 @@ def main():
         barrier()
         ksteps = max(3, args.steps // 2)
         t0 = time.perf_counter()
+        spans = []
         for _ in range(ksteps):
             e2e_step()
+            spans.append(h.last_host_span_ms()[0])
         barrier()
         te = max_over_ranks((time.perf_counter() - t0) * 1e3 / ksteps)
         identical_e2e = bool(torch.equal(out_h, out32.cpu()))
+        # the copies alone, for reference: inputs in, signatures out (pinned, one stream)
+        barrier()
+        c0 = time.perf_counter()
+        ids.copy_(ids_h, non_blocking=True)
+        w.copy_(w_h, non_blocking=True)
+        torch.cuda.synchronize()
+        c1 = time.perf_counter()
+        out_h.copy_(out32, non_blocking=True)
+        torch.cuda.synchronize()
+        c2 = time.perf_counter()
         h2d = ids_h.numel() * 8 + w_h.numel() * 8 + off_h.numel() * 8
         d2h = out_h.numel() * 8
         e2e = {"value": work * world / (te * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": te, "timing": "host wall clock around the blocking call", "identical_output": identical_e2e,
-               "host_cpus": local_cpus}
+               "host_cpus": local_cpus, "copy_in_ms": (c1 - c0) * 1e3, "copy_out_ms": (c2 - c1) * 1e3,
+               "device_span_ms": statistics.mean(spans), "chunks": h.last_host_span_ms()[1]}
 
     # ---------------- comparator: plain FP64
     h.set_profiling(True)

@@ -171,6 +171,15 @@ pmh_status pmh_sketch_batch_host(pmh_handle h, const uint64_t *ids, const double
                                  int32_t *set_status, int32_t chunks);
 
 /*
+ * pmh_last_host_span_ms -- device-side time of the most recent completed
+ * pmh_sketch_batch_host call on `h`, from its first input copy to its last
+ * output copy (CUDA events), and the number of ranges it used (chunks may be
+ * NULL).  The host wall time of the call minus this span is time the device
+ * waited for the host.  Errors: PMH_ERR_INVALID_ARG without such a call.
+ */
+pmh_status pmh_last_host_span_ms(pmh_handle h, float *ms, int32_t *chunks);
+
+/*
  * pmh_sketch_batch_noalloc -- pmh_sketch_batch for callers that cannot
  * allocate GPU memory: code that runs under another runtime's fixed memory
  * budget, inside a framework that forbids cudaMalloc on its hot path, or

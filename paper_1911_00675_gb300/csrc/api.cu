@@ -66,6 +66,8 @@ struct HostPipe {
     size_t z_cap[2] = {0, 0}, q_cap[2] = {0, 0}, st_cap[2] = {0, 0};
     cudaStream_t s[4] = {nullptr, nullptr, nullptr, nullptr};   // copy in, compute (two), copy out
     std::vector<cudaEvent_t> ev;
+    cudaEvent_t span[2] = {nullptr, nullptr};   // device-side span of the last call (timing events)
+    bool span_valid = false;
 };
 
 struct pmh_handle_s {
@@ -235,6 +237,7 @@ extern "C" void pmh_destroy(pmh_handle h) {
         if (ptr) cudaFree(ptr);
     for (int i = 0; i < 4; i++) if (h->hp.s[i]) cudaStreamDestroy(h->hp.s[i]);
     for (cudaEvent_t e : h->hp.ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->hp.span) if (e) cudaEventDestroy(e);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
@@ -393,11 +396,15 @@ static pmh_status check_sketch_args(pmh_handle h, int64_t num_sets, uint32_t m, 
 
 // The sketch of a CSR batch already in device memory, enqueued on `st`
 // (replayed from a cached CUDA graph when allow_graph and the arguments repeat).
+static TuneKey tune_key(uint32_t m, int32_t precision, int family, int64_t items) {
+    return TuneKey{m, precision, family, items > 0 ? 63 - __builtin_clzll((unsigned long long)items) : -1};
+}
+
 static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, const double *weights,
                                 const int64_t *offsets, int64_t num_sets, uint32_t m, const int32_t *variants,
                                 int32_t num_variants, int32_t precision, uint64_t seed, uint64_t *out_ids,
                                 double *out_q, int32_t *set_status, uint64_t *counters, cudaStream_t st,
-                                bool allow_graph, cudaEvent_t *fam_ev) {
+                                bool allow_graph, cudaEvent_t *fam_ev, const int *kinds_in = nullptr) {
     CUDA_TRY(h, cudaSetDevice(h->device));
     Workspace &w = h->ws[wsi];
     Tables tab;
@@ -413,15 +420,18 @@ static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, cons
     if (h->th.grid_min > 0) bind_grid_scratch(&p, w.grid);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (st) CUDA_TRY(h, cudaStreamIsCapturing(st, &cs));
-    // team shape per family: forced, else tuned, else (tuning off or impossible) the default rule
+    // team shape per family: given by the caller (host pipeline), else forced, else tuned, else
+    // (tuning off or impossible) the default rule
     int kinds[4];
     TuneKey tkey[4];
     bool need_tune = false;
-    {
+    if (kinds_in) {
+        for (int f = 0; f < 4; f++) kinds[f] = kinds_in[f];
+    } else {
         int64_t per_fam[4] = {0, 0, 0, 0};
         for (int v = 0; v < num_variants; v++) per_fam[family_of(variants[v]) - 1] += num_sets;
         for (int f = 0; f < 4; f++) {
-            tkey[f] = TuneKey{m, precision, f + 1, per_fam[f] > 0 ? 63 - __builtin_clzll((unsigned long long)per_fam[f]) : -1};
+            tkey[f] = tune_key(m, precision, f + 1, per_fam[f]);
             kinds[f] = h->force_shape[f];
             if (kinds[f] < 0 && per_fam[f] > 0) {
                 auto it = h->tuned.find(tkey[f]);
@@ -591,6 +601,10 @@ extern "C" pmh_status pmh_sketch_batch_host(pmh_handle h, const uint64_t *ids, c
     auto ev_in = [&](int c) { return hp.ev[kEvPerChunk * c]; };
     auto ev_fam = [&](int c) { return hp.ev.data() + kEvPerChunk * c + 1; };
     auto ev_out = [&](int c) { return hp.ev[kEvPerChunk * c + 5]; };
+    if (!hp.span[0])
+        for (int i = 0; i < 2; i++) CUDA_TRY(h, cudaEventCreate(&hp.span[i]));
+    hp.span_valid = false;
+    CUDA_TRY(h, cudaEventRecord(hp.span[0], s_in));
     // inputs: offsets, then each chunk's elements in place
     CUDA_TRY(h, cudaMemcpyAsync(doff, offsets, (size_t)(num_sets + 1) * 8, cudaMemcpyHostToDevice, s_in));
     for (int c = 0; c < k; c++) {
@@ -600,6 +614,20 @@ extern "C" pmh_status pmh_sketch_batch_host(pmh_handle h, const uint64_t *ids, c
             CUDA_TRY(h, cudaMemcpyAsync(dw + e0 * 8, weights + e0, (size_t)(e1 - e0) * 8, cudaMemcpyHostToDevice, s_in));
         }
         CUDA_TRY(h, cudaEventRecord(ev_in(c), s_in));
+    }
+    // team shapes: the ones tuned for the whole batch's size (or forced), else the default rule; the
+    // ranges are not tuned on their own (their timings would overlap each other)
+    int kinds[4];
+    {
+        int64_t per_fam[4] = {0, 0, 0, 0};
+        for (int v = 0; v < num_variants; v++) per_fam[family_of(variants[v]) - 1] += num_sets;
+        for (int f = 0; f < 4; f++) {
+            kinds[f] = h->force_shape[f];
+            if (kinds[f] < 0 && per_fam[f] > 0) {
+                auto it = h->tuned.find(tune_key(m, precision, f + 1, per_fam[f]));
+                if (it != h->tuned.end()) kinds[f] = it->second;
+            }
+        }
     }
     // chunks alternate between two compute streams (each with its own workspace), so that one
     // chunk's kernels fill the SMs the other's tail leaves idle; each family's rows go back as
@@ -612,7 +640,7 @@ extern "C" pmh_status pmh_sketch_batch_host(pmh_handle h, const uint64_t *ids, c
         if (c >= 2) CUDA_TRY(h, cudaStreamWaitEvent(s_run, ev_out(c - 2), 0));   // chunk outputs are double-buffered
         rc = sketch_device(h, r, (const uint64_t *)dids, (const double *)dw, doff + s0, sc, m, variants, num_variants,
                            precision, seed, (uint64_t *)hp.z[r], out_q ? (double *)hp.q[r] : nullptr,
-                           set_status ? (int32_t *)hp.st[r] : nullptr, nullptr, s_run, false, ev_fam(c));
+                           set_status ? (int32_t *)hp.st[r] : nullptr, nullptr, s_run, false, ev_fam(c), kinds);
         if (rc) {
             for (int i = 0; i < 4; i++) cudaStreamSynchronize(hp.s[i]);
             return rc;
@@ -634,8 +662,23 @@ extern "C" pmh_status pmh_sketch_batch_host(pmh_handle h, const uint64_t *ids, c
         }
         CUDA_TRY(h, cudaEventRecord(ev_out(c), s_out));
     }
+    for (int i = 1; i < 3; i++) {   // the copy-out stream ends after both compute streams
+        CUDA_TRY(h, cudaEventRecord(hp.ev[kEvPerChunk * (k - 1) + 5], hp.s[i]));
+        CUDA_TRY(h, cudaStreamWaitEvent(s_out, hp.ev[kEvPerChunk * (k - 1) + 5], 0));
+    }
+    CUDA_TRY(h, cudaEventRecord(hp.span[1], s_out));
     for (int i = 0; i < 4; i++) CUDA_TRY(h, cudaStreamSynchronize(hp.s[i]));
+    hp.span_valid = true;
     h->last_chunks = k;
+    return PMH_OK;
+}
+
+extern "C" pmh_status pmh_last_host_span_ms(pmh_handle h, float *ms, int32_t *chunks) {
+    if (!h || !ms) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    if (!h->hp.span_valid) return fail(h, PMH_ERR_INVALID_ARG, "no completed pmh_sketch_batch_host call");
+    CUDA_TRY(h, cudaEventElapsedTime(ms, h->hp.span[0], h->hp.span[1]));
+    if (chunks) *chunks = h->last_chunks;
     return PMH_OK;
 }
 

@@ -25,7 +25,7 @@ COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "round
             "cyc_pass0", "cyc_first", "cyc_deep", "cyc_refresh", "cyc_finish", "items", "cyc_surv", "cyc_item",
             "cyc_warp", "reserved17", "reserved18", "reserved19")
 EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_sketch_batch_host",
-           "pmh_sketch_batch_noalloc",
+           "pmh_last_host_span_ms", "pmh_sketch_batch_noalloc",
            "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_kernel_ms_history", "pmh_last_launches",
            "pmh_set_thresholds",
            "pmh_set_team_shape", "pmh_set_autotune", "pmh_last_team_shapes",
@@ -62,6 +62,8 @@ def load(path: str = LIB_PATH):
             lib.pmh_sketch_batch_host.restype = i32
             lib.pmh_sketch_batch_host.argtypes = [vp, vp, vp, vp, i64, u32, ctypes.POINTER(i32), i32, i32, u64, vp, vp,
                                                   vp, i32]
+            lib.pmh_last_host_span_ms.restype = i32
+            lib.pmh_last_host_span_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32)]
             lib.pmh_sketch_batch_noalloc.restype = i32
             lib.pmh_sketch_batch_noalloc.argtypes = [vp, vp, vp, i64, u32, ctypes.POINTER(i32), i32, i32, u64, vp, vp,
                                                      vp, vp, vp]
@@ -201,6 +203,12 @@ class Handle:
                                           _ptr(status), int(chunks))
         self._raise(rc)
         return out_ids, out_q, status
+
+    def last_host_span_ms(self):
+        """(device-side ms from first copy-in to last copy-out, ranges) of the last sketch_batch_host call."""
+        ms, k = ctypes.c_float(), ctypes.c_int32()
+        self._raise(load().pmh_last_host_span_ms(self._h, ctypes.byref(ms), ctypes.byref(k)))
+        return ms.value, k.value
 
     def set_profiling(self, enable: bool = True):
         self._raise(load().pmh_set_profiling(self._h, 1 if enable else 0))
