@@ -409,7 +409,8 @@ def main():
         e2e = {"value": work * world / (te * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": te, "timing": "host wall clock around the blocking call", "identical_output": identical_e2e,
                "host_cpus": local_cpus, "copy_in_ms": (c1 - c0) * 1e3, "copy_out_ms": (c2 - c1) * 1e3,
-               "device_span_ms": statistics.mean(spans), "chunks": h.last_host_span_ms()[1]}
+               "device_span_ms": statistics.mean(spans), "device_span_ms_min": min(spans),
+               "device_span_ms_median": statistics.median(spans), "chunks": h.last_host_span_ms()[1]}
 
     # ---------------- comparator: plain FP64
     h.set_profiling(True)

@@ -304,6 +304,15 @@ pmh_status pmh_set_thresholds(pmh_handle h, double t_c, double t_c_grid, int32_t
 pmh_status pmh_check_exp1(const uint64_t *words, int64_t n, float *out, void *stream);
 
 /*
+ * pmh_check_texp -- the FP32 truncated-exponential variate of the candidate
+ * path, TE(word) = -log1p(U c) * inv with U = (word >> 11) 2^-53, for the FP32
+ * constants c = expm1(-lambda) and inv = 1/lambda (Sec. "ProbMinHash3",
+ * Exp(lambda;0,1) by inversion); same conventions and errors as
+ * pmh_check_exp1.
+ */
+pmh_status pmh_check_texp(const uint64_t *words, int64_t n, float c, float inv, float *out, void *stream);
+
+/*
  * pmh_estimate_allpairs -- numerators of the J_P estimator (Eq. jaccard_estimator)
  * for every pair of signatures: counts[a*num_sigs + b] = #{k : sigs[a][k] == sigs[b][k]}.
  *

@@ -688,6 +688,20 @@ static __global__ void check_exp1_kernel(const uint64_t *__restrict__ w, int64_t
         out[i] = exp1_32(w[i]);
 }
 
+static __global__ void check_texp_kernel(const uint64_t *__restrict__ w, int64_t n, float c, float inv,
+                                         float *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = texp_32(w[i], c, inv);
+}
+
+extern "C" pmh_status pmh_check_texp(const uint64_t *words, int64_t n, float c, float inv, float *out, void *stream) {
+    if (n < 0 || (n > 0 && (!words || !out))) return PMH_ERR_INVALID_ARG;
+    if (n == 0) return PMH_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    check_texp_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(words, n, c, inv, out);
+    return cudaGetLastError() == cudaSuccess ? PMH_OK : PMH_ERR_CUDA;
+}
+
 extern "C" pmh_status pmh_check_exp1(const uint64_t *words, int64_t n, float *out, void *stream) {
     if (n < 0 || (n > 0 && (!words || !out))) return PMH_ERR_INVALID_ARG;
     if (n == 0) return PMH_OK;

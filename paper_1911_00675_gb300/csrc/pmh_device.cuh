@@ -162,8 +162,14 @@ __device__ __forceinline__ float exp1_32(uint64_t w) {
     const float lp = log1p_reduced(f);
     return -__fmaf_rn(ef, 0x1.62e4p-1f, __fmaf_rn(ef, 0x1.7f7d1cp-20f, lp));
 }
+// Exp(lambda;0,1) = -log1p(U c) / lambda, c = expm1(-lambda) in [-1/2, 0).  The
+// argument U c lies in (c, 0].  When it is at least sqrt(1/2) - 1 (always when
+// lambda <= ln sqrt(2): ProbMinHash3 with m >= 4, and every point of ProbMinHash4
+// but the two before the last) the reduced-range log1p applies directly, so the
+// lanes of a warp do not split; otherwise log1pf.
 __device__ __forceinline__ float texp_32(uint64_t w, float c, float inv) {
-    float l = log1pf(__fmul_rn(u53_to_float(w >> 11), c));
+    const float x = __fmul_rn(u53_to_float(w >> 11), c);
+    const float l = x >= -0.29289321f ? log1p_reduced(x) : log1pf(x);
     return __fmul_rn(-l, inv);
 }
 // A positive, finite weight (the item's weights are validated before use):

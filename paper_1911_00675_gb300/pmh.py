@@ -29,7 +29,7 @@ EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "p
            "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_kernel_ms_history", "pmh_last_launches",
            "pmh_set_thresholds",
            "pmh_set_team_shape", "pmh_set_autotune", "pmh_last_team_shapes",
-           "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge", "pmh_check_exp1")
+           "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge", "pmh_check_exp1", "pmh_check_texp")
 
 _lib = None
 _lock = threading.Lock()
@@ -90,6 +90,8 @@ def load(path: str = LIB_PATH):
             lib.pmh_estimate_pairs.argtypes = [vp, vp, vp, vp, vp, i64, u32, vp, vp]
             lib.pmh_check_exp1.restype = i32
             lib.pmh_check_exp1.argtypes = [vp, i64, vp, vp]
+            lib.pmh_check_texp.restype = i32
+            lib.pmh_check_texp.argtypes = [vp, i64, ctypes.c_float, ctypes.c_float, vp, vp]
             lib.pmh_merge.restype = i32
             lib.pmh_merge.argtypes = [vp, vp, vp, i64, u32, vp, vp, vp]
             _lib = lib
@@ -355,6 +357,15 @@ def check_exp1(words, stream=None):
     rc = load().pmh_check_exp1(_ptr(words), words.numel(), _ptr(out), _stream(stream))
     if rc:
         raise PmhError(rc, "pmh_check_exp1 failed")
+    return out
+
+
+def check_texp(words, c: float, inv: float, stream=None):
+    """FP32 truncated-exponential variate of each uint64 word as the candidate path computes it."""
+    out = torch.empty(words.numel(), dtype=torch.float32, device=words.device)
+    rc = load().pmh_check_texp(_ptr(words), words.numel(), float(c), float(inv), _ptr(out), _stream(stream))
+    if rc:
+        raise PmhError(rc, "pmh_check_texp failed")
     return out
 
 
