@@ -84,6 +84,7 @@ enum {
     PMH_CNT_CYC_SURV = 14,    /* survivor expansion, lane-sequential and deep (part of CYC_FIRST) */
     PMH_CNT_CYC_ITEM = 15,    /* whole items, from the queue fetch to the barrier after write-out */
     PMH_CNT_CYC_WARP = 16,    /* warp lifetime in the sketch kernels (start to exit) */
+    PMH_CNT_CYC_BARRIER = 17, /* waiting for the team's other warps at the end of a round (part of CYC_FIRST) */
     PMH_NUM_COUNTERS = 20
 };
 

@@ -938,7 +938,9 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
         if (round > 0) count(c, PMH_CNT_ROUNDS, leader);
         team_sync<TW>();
         run_range<FAM, F32, TW>(c, 0, c.n);
+        const long long t_bar = clock64();
         team_sync<TW>();
+        count(c, PMH_CNT_CYC_BARRIER, (unsigned long long)(clock64() - t_bar));
         count(c, PMH_CNT_CYC_FIRST, (unsigned long long)(clock64() - t_ph));
         t_ph = clock64();
         if (ld_volatile(&ts->unfilled) == 0 || ld_volatile(&ts->status) != PMH_OK) break;
