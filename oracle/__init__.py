@@ -70,6 +70,9 @@ def _load():
             lib.or_jp.restype = dbl; lib.or_jp.argtypes = [vp, vp, i64, vp, vp, i64]
             lib.or_count_equal.restype = u32; lib.or_count_equal.argtypes = [vp, vp, u32]
             lib.or_count_allpairs.restype = i32; lib.or_count_allpairs.argtypes = [vp, i64, u32, vp]
+            lib.or_bbit_code.restype = u64; lib.or_bbit_code.argtypes = [u64, u32, u32, u64]
+            lib.or_bbit_reduce.restype = i32; lib.or_bbit_reduce.argtypes = [vp, i64, u32, u32, u64, vp]
+            lib.or_bbit_estimate.restype = dbl; lib.or_bbit_estimate.argtypes = [u32, u32, u32]
             _lib = lib
     return _lib
 
@@ -240,6 +243,27 @@ def count_allpairs(sigs) -> np.ndarray:
     out = np.zeros((n, n), dtype=np.uint32)
     _load().or_count_allpairs(_p(s), n, m, _p(out))
     return out
+
+
+def bbit_code(z: int, k: int, b: int, seed: int = 0) -> int:
+    """b-bit code of component k with winning id z (Algorithm "Reduction to a b-bit signature")."""
+    return _load().or_bbit_code(z & (2**64 - 1), k, b, seed & (2**64 - 1))
+
+
+def bbit_reduce(sigs, b: int, seed: int = 0) -> np.ndarray:
+    """b-bit codes of every component of a (num x m) signature array, unpacked (uint64)."""
+    s = _u64(sigs)
+    n, m = s.shape
+    out = np.zeros((n, m), dtype=np.uint64)
+    rc = _load().or_bbit_reduce(_p(s), n, m, b, seed & (2**64 - 1), _p(out))
+    if rc:
+        raise OracleError(rc)
+    return out
+
+
+def bbit_estimate(count: int, m: int, b: int) -> float:
+    """Collision-corrected J estimate from the number of equal b-bit codes."""
+    return _load().or_bbit_estimate(int(count), m, b)
 
 
 class OracleError(RuntimeError):

@@ -23,6 +23,8 @@
  *     Weights), the estimator of Eq. jaccard_estimator
  *   - a near-tie scan used to exempt components whose two best candidates are
  *     closer than a relative gap (GPU and host log1p may differ in the last ulp)
+ *   - Algorithm "Reduction to a b-bit signature" (Sec. Introduction / related
+ *     work on b-bit minwise hashing) and the collision-corrected estimate
  *
  * Readings of the paper taken here (also listed in the design doc):
  *   - Ties: components keep the lexicographic minimum of (value, element id);
@@ -875,4 +877,37 @@ int or_count_allpairs(const uint64_t *sig, int64_t num, uint32_t m, uint32_t *ou
         for (int64_t b = 0; b < num; b++)
             out[a * num + b] = or_count_equal(sig + (size_t)a * m, sig + (size_t)b * m, m);
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reduction to a b-bit signature (Algorithm "Reduction to a b-bit
+ * signature"): component k (0-based here) becomes the least significant b
+ * bits of a hash of the pair (z_k, k).  The hash: SplitMix64's finalizer of
+ * z_k XOR a per-index key, the key being output k+1 of SplitMix64 seeded with
+ * mix(seed) -- so the index enters every component's hash (the paper stresses
+ * that it must, to keep collisions of different elements uncorrelated across
+ * components).  b in {1, 2, 4, ..., 64}. */
+uint64_t or_bbit_code(uint64_t z, uint32_t k, uint32_t b, uint64_t seed)
+{
+    const uint64_t key = or_mix64(or_mix64(seed) + ((uint64_t)k + 1) * PHI64);
+    const uint64_t h = or_mix64(z ^ key);
+    return b >= 64 ? h : (h & ((1ull << b) - 1));
+}
+
+int or_bbit_reduce(const uint64_t *sig, int64_t num, uint32_t m, uint32_t b, uint64_t seed, uint64_t *codes)
+{
+    if (b == 0 || b > 64 || (b & (b - 1))) return OR_ERR_INVALID_ARG;
+    for (int64_t a = 0; a < num; a++)
+        for (uint32_t k = 0; k < m; k++) codes[a * m + k] = or_bbit_code(sig[a * m + k], k, b, seed);
+    return OR_OK;
+}
+
+/* Estimate from b-bit codes: equal codes come from equal components
+ * (probability J) or from a collision of two different elements' codes
+ * (probability 2^-b otherwise), so E[count/m] = J + (1 - J) 2^-b and
+ * (count/m - 2^-b) / (1 - 2^-b) is unbiased for J. */
+double or_bbit_estimate(uint32_t count, uint32_t m, uint32_t b)
+{
+    const double r = b >= 64 ? 0.0 : ldexp(1.0, -(int)b);
+    return ((double)count / (double)m - r) / (1.0 - r);
 }

@@ -430,3 +430,75 @@ def test_near_tie_scan_consistency():
         # a huge relative gap flags every component with a runner-up
         flags, ru = oracle.near_ties(v, ids, w, 64, 1, q, z, 1e6)
         assert flags.sum() == np.isfinite(ru).sum()
+
+
+# --------------------------------------------------------------- b-bit signatures
+# Algorithm "Reduction to a b-bit signature": each component becomes b bits of a hash of
+# (component, index); the estimator must account for collisions of different elements.
+
+def test_bbit_64_preserves_equality_exactly():
+    # b = 64 keeps the whole hash: a bijection of the id for each index, so equal-component
+    # counts of the codes are those of the ids
+    rng = np.random.default_rng(70)
+    m, n = 48, 30
+    base = rng.integers(0, 2**63, size=(6, m), dtype=np.uint64)
+    sigs = base[rng.integers(0, 6, size=n)].copy()
+    noise = rng.random((n, m)) < 0.4
+    sigs[noise] = rng.integers(0, 2**63, size=int(noise.sum()), dtype=np.uint64)
+    codes = oracle.bbit_reduce(sigs, 64, seed=3)
+    assert np.array_equal(oracle.count_allpairs(codes), oracle.count_allpairs(sigs))
+    assert np.array_equal(codes[0, :5], [oracle.bbit_code(int(sigs[0, k]), k, 64, 3) for k in range(5)])
+
+
+@pytest.mark.parametrize("b", [1, 2, 4, 8])
+def test_bbit_codes_uniform_and_collision_rate(b):
+    # different ids collide with probability 2^-b; codes are uniform on {0..2^b-1}
+    rng = np.random.default_rng(71 + b)
+    m, n = 512, 400
+    sigs = rng.integers(0, 2**64, size=(n, m), dtype=np.uint64)
+    codes = oracle.bbit_reduce(sigs, b, seed=9)
+    assert codes.max() < 2**b
+    counts = np.bincount(codes.ravel().astype(np.int64), minlength=2**b)
+    expected = codes.size / 2**b
+    chi2 = ((counts - expected) ** 2 / expected).sum()
+    assert chi2 < 2**b + 6 * np.sqrt(2 * 2**b)          # chi-square with 2^b - 1 dof, far tail
+    a, c = codes[0::2], codes[1::2]
+    p = 2.0 ** -b
+    matches = (a == c).sum()
+    trials = a.size
+    assert abs(matches - trials * p) < 5 * np.sqrt(trials * p * (1 - p))
+
+
+def test_bbit_index_enters_the_hash():
+    # two signatures made of one id each, repeated over all components: with the index in the
+    # hash their codes match at rate 2^-b per component, not all-or-nothing
+    m, b = 4096, 1
+    za = np.full((1, m), 0x1234567890ABCDEF, dtype=np.uint64)
+    zb = np.full((1, m), 0x0FEDCBA098765432, dtype=np.uint64)
+    ca = oracle.bbit_reduce(za, b, seed=1)
+    cb = oracle.bbit_reduce(zb, b, seed=1)
+    matches = int((ca == cb).sum())
+    assert abs(matches - m / 2) < 5 * np.sqrt(m / 4)
+    assert len(np.unique(ca)) == 2                        # one id, both code values over the components
+
+
+@pytest.mark.parametrize("b", [1, 4, 8])
+def test_bbit_estimator_is_unbiased(b):
+    # pairs with exactly j*m equal components and the rest distinct: the corrected estimate
+    # averages to j (E[count/m] = J + (1 - J) 2^-b)
+    rng = np.random.default_rng(80 + b)
+    m = 256
+    for j in (0.0, 0.3, 0.8, 1.0):
+        est = []
+        for t in range(200):
+            a = rng.integers(0, 2**64, size=(1, m), dtype=np.uint64)
+            c = rng.integers(0, 2**64, size=(1, m), dtype=np.uint64)
+            eq = rng.permutation(m)[: int(round(j * m))]
+            c[0, eq] = a[0, eq]
+            ca, cc = oracle.bbit_reduce(a, b, 5), oracle.bbit_reduce(c, b, 5)
+            est.append(oracle.bbit_estimate(int((ca == cc).sum()), m, b))
+        p = 2.0 ** -b
+        jj = round(j * m) / m                              # the exact fraction planted
+        sd = np.sqrt((1 - jj) * p * (1 - p) / m) / (1 - p) / np.sqrt(len(est))
+        assert abs(np.mean(est) - jj) < 5 * sd + 1e-12, (jj, np.mean(est))
+    assert oracle.bbit_estimate(m, m, b) == 1.0
