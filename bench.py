@@ -42,6 +42,9 @@ OPS_FIRST_REJECT = 26   # value word (20) + log-free lower bound and compare (6)
 OPS_POINT = 60          # value word (20) + label word (20) + logarithm (~10) + scale/compare (5) + offer (5)
 LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes issue one instruction per clock
 OPS_PAIR_COMPONENT = 3  # equal-component count: two 32-bit compares and one add per component pair
+# 8-bit codes, per pair of 64-bit words (8 fields): xor (2), per 32-bit half three fold steps of
+# shift + or (6) and and-not + popcount (2), two adds (2)
+OPS_BBIT_WORD = 2 + 2 * (6 + 2) + 2
 # DRAM bytes (read + write) of the four family sketch kernels per element-variant, from the ncu
 # capture summarised in profiles/sketch_kernel_pair_c2_2000sets_full.md (same kernel source); the
 # traffic grows in proportion to the elements (one pass over ids and weights per family).
@@ -212,6 +215,23 @@ def secondary(h, dev, n_sms, sm_mhz, peaks, steps=3):
                        "ms": ms, "pairs_per_s": pairs / (ms * 1e-3),
                        "roofline": {"bound": "alu", "achieved": a, "peak": pk, "unit": "Tops/s (32-bit lane ops)",
                                     "frac": a / pk, "ops_per_launch": ops}}
+
+    # the same signatures reduced to 8-bit codes, and their all-pairs equal-field counts
+    bb = 8
+    packed = h.bbit_reduce(z4, bb, seed=1)
+    ms_red = timed(lambda: h.bbit_reduce(z4, bb, seed=1, packed=packed), steps)
+    ms_bb = timed(lambda: h.bbit_allpairs(packed, 1024, bb, upper_only=True, counts=counts), steps)
+    words = packed.shape[1]
+    ops_bb = pairs * words * OPS_BBIT_WORD
+    a_bb = ops_bb / (ms_bb * 1e-3) / 1e12
+    red_bytes = S4 * 1024 * 8 + packed.numel() * 8
+    out["bbit8"] = {"workload": "the same 16,384 signatures reduced to 8-bit codes (Algorithm b-bit), all pairs",
+                    "reduce_ms": ms_red, "allpairs_ms": ms_bb, "pairs_per_s": pairs / (ms_bb * 1e-3),
+                    "reduce_roofline": {"bound": "hbm", "achieved": red_bytes / (ms_red * 1e-3) / 1e9,
+                                        "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                        "frac": red_bytes / (ms_red * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+                    "roofline": {"bound": "alu", "achieved": a_bb, "peak": pk, "unit": "Tops/s (32-bit lane ops)",
+                                 "frac": a_bb / pk, "ops_per_launch": ops_bb}}
     return out
 
 

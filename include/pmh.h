@@ -295,6 +295,31 @@ pmh_status pmh_last_launches(pmh_handle h, int32_t *launches);
 pmh_status pmh_set_thresholds(pmh_handle h, double t_c, double t_c_grid, int32_t rounds, int64_t grid_min);
 
 /*
+ * pmh_bbit_reduce -- Algorithm "Reduction to a b-bit signature": component k
+ * (0-based) of every signature keeps the least significant b bits of a hash
+ * of the pair (z_k, k): mix(z_k ^ mix(mix(seed) + (k+1) phi)), mix the
+ * SplitMix64 finalizer and phi = 0x9E3779B97F4A7C15.
+ *   sigs    device uint64[num_sigs * m] (row-major winning ids)
+ *   b       1, 2, 4, 8, 16, 32 or 64
+ *   packed  device uint64[num_sigs * W], W = ceil(m b / 64): field k occupies
+ *           bits (k b) mod 64 .. +b-1 of word (k b) / 64 of its row; unused high
+ *           bits of a row's last word are zero.
+ * pmh_bbit_allpairs -- for every pair of packed rows, the number of equal
+ * b-bit fields into device uint16[num_sigs * num_sigs] (row-major; with
+ * upper_only only b >= a is written).  Different elements collide with
+ * probability 2^-b, so (count/m - 2^-b) / (1 - 2^-b) estimates J_P without
+ * that bias (the paper notes that the plain estimator Eq. jaccard_estimator
+ * is biased for b-bit signatures).
+ * Both run asynchronously on `stream`.  Errors: PMH_ERR_INVALID_ARG (NULL
+ * pointers, bad b, m < 1), PMH_ERR_UNSUPPORTED (m > 65535 or too many rows
+ * for one all-pairs launch), PMH_ERR_CUDA.
+ */
+pmh_status pmh_bbit_reduce(pmh_handle h, const uint64_t *sigs, int64_t num_sigs, uint32_t m, uint32_t b, uint64_t seed,
+                           uint64_t *packed, void *stream);
+pmh_status pmh_bbit_allpairs(pmh_handle h, const uint64_t *packed, int64_t num_sigs, uint32_t m, uint32_t b,
+                             int32_t upper_only, uint16_t *counts, void *stream);
+
+/*
  * pmh_check_exp1 -- the FP32 Exp(1) variate of the candidate path, E(word) =
  * -ln(1 - U), U = (word >> 11) 2^-53 (the inversion of Sec. "ProbMinHash1",
  * exponential spacings), for each of n device words into device float out[n],

@@ -816,6 +816,159 @@ extern "C" pmh_status pmh_estimate_allpairs(pmh_handle h, const uint64_t *sigs, 
     return PMH_OK;
 }
 
+// ------------------------------------------------------------------ b-bit signatures
+// Algorithm "Reduction to a b-bit signature": component k keeps the low b bits
+// of mix(z_k ^ key_k), key_k = mix(mix(seed) + (k+1) phi) (output k+1 of
+// SplitMix64 seeded with mix(seed)), packed little-endian: field k occupies
+// bits (k b) mod 64 .. +b of word (k b) / 64 of its signature's
+// ceil(m b / 64) words; unused high bits of the last word are zero.
+__device__ __forceinline__ uint64_t bbit_code(uint64_t z, uint32_t k, uint64_t mseed, uint32_t b) {
+    const uint64_t h = mix64(z ^ mix64(mseed + ((uint64_t)k + 1) * kPhi));
+    return b >= 64 ? h : (h & ((1ull << b) - 1));
+}
+
+static __global__ void bbit_reduce_kernel(const uint64_t *__restrict__ sig, int64_t n, uint32_t m, uint32_t b,
+                                          uint64_t mseed, uint32_t words, uint64_t *__restrict__ out) {
+    const uint32_t per = 64 / b;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * words; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = t / words;
+        const uint32_t wd = (uint32_t)(t - a * words);
+        uint64_t acc = 0;
+        for (uint32_t j = 0; j < per; j++) {
+            const uint32_t k = wd * per + j;
+            if (k >= m) break;
+            acc |= bbit_code(sig[a * m + k], k, mseed, b) << (j * b);
+        }
+        out[t] = acc;
+    }
+}
+
+// Number of all-zero b-bit fields of a 32-bit word (b <= 32): fold each field's
+// bits into its lowest bit, then count the lowest bits left clear.
+template <int B>
+__device__ __forceinline__ uint32_t zero_fields32(uint32_t x) {
+    if constexpr (B == 1) {
+        return 32u - __popc(x);
+    } else {
+        constexpr uint32_t low = B == 2 ? 0x55555555u : B == 4 ? 0x11111111u : B == 8 ? 0x01010101u
+                               : B == 16 ? 0x00010001u : 0x00000001u;
+#pragma unroll
+        for (int s = 1; s < B; s <<= 1) x |= x >> s;
+        return __popc(~x & low);
+    }
+}
+
+template <int B>
+__device__ __forceinline__ uint32_t zero_fields64(uint64_t x) {
+    if constexpr (B == 64) return x == 0 ? 1u : 0u;
+    else return zero_fields32<B>((uint32_t)x) + zero_fields32<B>((uint32_t)(x >> 32));
+}
+
+// Equal-field counts of all pairs of packed b-bit signatures: the tiling of
+// allpairs_kernel, over words instead of components; the zero padding of the
+// last word is counted as equal in every pair and subtracted at the end.
+template <int B>
+__global__ void __launch_bounds__(256) bbit_allpairs_kernel(const uint64_t *__restrict__ sig, int64_t n, uint32_t words,
+                                                            uint32_t pad, int upper_only, uint16_t *__restrict__ out) {
+    __shared__ uint64_t As[kKc][kTile + 1];
+    __shared__ uint64_t Bs[kKc][kTile + 1];
+    const int64_t ta = blockIdx.y, tb = blockIdx.x;
+    if (upper_only && ta > tb) return;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t a0 = ta * kTile, b0 = tb * kTile;
+    uint32_t cnt[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) cnt[i][j] = 0;
+    for (uint32_t kc = 0; kc < words; kc += kKc) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int idx = threadIdx.x + 256 * q;
+            const int r = idx >> 4, kk = idx & 15;
+            const uint32_t k = kc + kk;
+            const int64_t ra = a0 + r, rb = b0 + r;
+            // outside the arrays: all ones against all zeros, no field equal
+            As[kk][r] = (ra < n && k < words) ? sig[ra * words + k] : 0xFFFFFFFFFFFFFFFFull;
+            Bs[kk][r] = (rb < n && k < words) ? sig[rb * words + k] : 0ull;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kKc; kk++) {
+            uint64_t a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) cnt[i][j] += zero_fields64<B>(a[i] ^ b[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int64_t a = a0 + ty + 16 * i;
+        if (a >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int64_t b = b0 + tx + 16 * j;
+            if (b >= n || (upper_only && a > b)) continue;
+            out[a * n + b] = (uint16_t)(cnt[i][j] - pad);
+        }
+    }
+}
+
+static bool bbit_width_ok(uint32_t b) { return b >= 1 && b <= 64 && (b & (b - 1)) == 0; }
+
+extern "C" pmh_status pmh_bbit_reduce(pmh_handle h, const uint64_t *sigs, int64_t num_sigs, uint32_t m, uint32_t b,
+                                      uint64_t seed, uint64_t *packed, void *stream) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    if (num_sigs < 0 || m < 1) return fail(h, PMH_ERR_INVALID_ARG, "num_sigs < 0 or m < 1");
+    if (!bbit_width_ok(b)) return fail(h, PMH_ERR_INVALID_ARG, "b = %u is not a power of two in [1, 64]", b);
+    if (num_sigs == 0) return PMH_OK;
+    if (!sigs || !packed) return fail(h, PMH_ERR_INVALID_ARG, "NULL sigs/packed");
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    const uint32_t words = (uint32_t)(((uint64_t)m * b + 63) / 64);
+    const int64_t total = num_sigs * words;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)h->sm_count * 16);
+    bbit_reduce_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(sigs, num_sigs, m, b, host_mix64(seed), words, packed);
+    CUDA_TRY(h, cudaGetLastError());
+    return PMH_OK;
+}
+
+extern "C" pmh_status pmh_bbit_allpairs(pmh_handle h, const uint64_t *packed, int64_t num_sigs, uint32_t m, uint32_t b,
+                                        int32_t upper_only, uint16_t *counts, void *stream) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    if (num_sigs < 0) return fail(h, PMH_ERR_INVALID_ARG, "num_sigs < 0");
+    if (m < 1 || m > 65535) return fail(h, PMH_ERR_UNSUPPORTED, "m = %u outside [1, 65535]", m);
+    if (!bbit_width_ok(b)) return fail(h, PMH_ERR_INVALID_ARG, "b = %u is not a power of two in [1, 64]", b);
+    if (num_sigs == 0) return PMH_OK;
+    if (!packed || !counts) return fail(h, PMH_ERR_INVALID_ARG, "NULL packed/counts");
+    const int64_t tiles = (num_sigs + kTile - 1) / kTile;
+    if (tiles > 65535) return fail(h, PMH_ERR_UNSUPPORTED, "num_sigs too large for one launch");
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    const uint32_t words = (uint32_t)(((uint64_t)m * b + 63) / 64);
+    const uint32_t pad = b == 64 ? 0u : words * (64 / b) - m;
+    dim3 grid((unsigned)tiles, (unsigned)tiles);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int up = upper_only ? 1 : 0;
+    switch (b) {
+        case 1: bbit_allpairs_kernel<1><<<grid, 256, 0, st>>>(packed, num_sigs, words, pad, up, counts); break;
+        case 2: bbit_allpairs_kernel<2><<<grid, 256, 0, st>>>(packed, num_sigs, words, pad, up, counts); break;
+        case 4: bbit_allpairs_kernel<4><<<grid, 256, 0, st>>>(packed, num_sigs, words, pad, up, counts); break;
+        case 8: bbit_allpairs_kernel<8><<<grid, 256, 0, st>>>(packed, num_sigs, words, pad, up, counts); break;
+        case 16: bbit_allpairs_kernel<16><<<grid, 256, 0, st>>>(packed, num_sigs, words, pad, up, counts); break;
+        case 32: bbit_allpairs_kernel<32><<<grid, 256, 0, st>>>(packed, num_sigs, words, pad, up, counts); break;
+        default: bbit_allpairs_kernel<64><<<grid, 256, 0, st>>>(packed, num_sigs, words, pad, up, counts); break;
+    }
+    CUDA_TRY(h, cudaGetLastError());
+    return PMH_OK;
+}
+
 extern "C" pmh_status pmh_estimate_pairs(pmh_handle h, const uint64_t *sig_a, const uint64_t *sig_b,
                                          const int64_t *pairs_a, const int64_t *pairs_b, int64_t num_pairs, uint32_t m,
                                          uint32_t *counts, void *stream) {

@@ -29,7 +29,8 @@ EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "p
            "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_kernel_ms_history", "pmh_last_launches",
            "pmh_set_thresholds",
            "pmh_set_team_shape", "pmh_set_autotune", "pmh_last_team_shapes",
-           "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge", "pmh_check_exp1", "pmh_check_texp")
+           "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge", "pmh_check_exp1", "pmh_check_texp",
+           "pmh_bbit_reduce", "pmh_bbit_allpairs")
 
 _lib = None
 _lock = threading.Lock()
@@ -92,6 +93,10 @@ def load(path: str = LIB_PATH):
             lib.pmh_check_exp1.argtypes = [vp, i64, vp, vp]
             lib.pmh_check_texp.restype = i32
             lib.pmh_check_texp.argtypes = [vp, i64, ctypes.c_float, ctypes.c_float, vp, vp]
+            lib.pmh_bbit_reduce.restype = i32
+            lib.pmh_bbit_reduce.argtypes = [vp, vp, i64, u32, u32, u64, vp, vp]
+            lib.pmh_bbit_allpairs.restype = i32
+            lib.pmh_bbit_allpairs.argtypes = [vp, vp, i64, u32, u32, i32, vp, vp]
             lib.pmh_merge.restype = i32
             lib.pmh_merge.argtypes = [vp, vp, vp, i64, u32, vp, vp, vp]
             _lib = lib
@@ -250,6 +255,28 @@ class Handle:
         a, b = ctypes.c_float(), ctypes.c_float()
         self._raise(load().pmh_last_kernel_ms(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    # -- b-bit signatures ---------------------------------------------------
+    def bbit_reduce(self, sigs, b: int, seed: int = 0, packed=None, stream=None):
+        """Packed b-bit signatures [num_sigs, ceil(m b / 64)] (int64 view of uint64 words)."""
+        _check(sigs, "sigs", _I64, self.device)
+        n, m = sigs.shape
+        words = (m * b + 63) // 64
+        if packed is None:
+            packed = torch.empty((n, words), dtype=torch.int64, device=self.device)
+        self._raise(load().pmh_bbit_reduce(self._h, _ptr(sigs), n, m, int(b), int(seed) & (2**64 - 1), _ptr(packed),
+                                           _stream(stream)))
+        return packed
+
+    def bbit_allpairs(self, packed, m: int, b: int, upper_only: bool = False, counts=None, stream=None):
+        """Equal-field counts of all pairs of packed rows (int16 view of uint16)."""
+        _check(packed, "packed", _I64, self.device)
+        n = packed.shape[0]
+        if counts is None:
+            counts = torch.empty((n, n), dtype=torch.int16, device=self.device)
+        self._raise(load().pmh_bbit_allpairs(self._h, _ptr(packed), n, int(m), int(b), 1 if upper_only else 0,
+                                             _ptr(counts), _stream(stream)))
+        return counts
 
     # -- pmh_estimate_allpairs ---------------------------------------------
     def estimate_allpairs(self, sigs, upper_only: bool = False, counts=None, stream=None):
