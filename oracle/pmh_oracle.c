@@ -33,8 +33,9 @@
  *     ties order dependent; ties have probability ~0.
  *   - Labels are 0-based internally (paper: 1..m).
  *   - Uniform integers use a multiply-high without rejection.
- *   - Truncated exponentials use inverse-transform sampling (the paper's
- *     "straightforward approach", Sec. Truncated Exponential Sampling).
+ *   - Truncated exponentials use inverse-transform sampling, the direct method
+ *     the paper gives before its rejection sampler (Sec. Truncated Exponential
+ *     Sampling).
  *   - Fixed FP64 evaluation order t = b*c, s = a + t, x = w_inv * s; compile
  *     with -ffp-contract=off so no FMA contraction changes the rounding.
  */
