@@ -26,8 +26,8 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-V1, V1A, V2, V3, V3A, V4 = range(6)
-VARIANTS = {"1": V1, "1a": V1A, "2": V2, "3": V3, "3a": V3A, "4": V4}
+V1, V1A, V2, V3, V3A, V4, V3U, V3AU, V4U = range(9)
+VARIANTS = {"1": V1, "1a": V1A, "2": V2, "3": V3, "3a": V3A, "4": V4, "3u": V3U, "3au": V3AU, "4u": V4U}
 OK, ERR_INVALID_ARG, ERR_BAD_WEIGHT, ERR_ITER_LIMIT = 0, 1, 2, 3
 
 

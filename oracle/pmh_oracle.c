@@ -25,6 +25,8 @@
  *     closer than a relative gap (GPU and host log1p may differ in the last ulp)
  *   - Algorithm "Reduction to a b-bit signature" (Sec. Introduction / related
  *     work on b-bit minwise hashing) and the collision-corrected estimate
+ *   - the binary-weight specialisations of ProbMinHash3, 3a and 4 (Sec.
+ *     Conventional Jaccard Similarity): uniform variates, gamma_i = i
  *
  * Readings of the paper taken here (also listed in the design doc):
  *   - Ties: components keep the lexicographic minimum of (value, element id);
@@ -45,7 +47,10 @@
 #include <string.h>
 
 enum { OR_OK = 0, OR_ERR_INVALID_ARG = 1, OR_ERR_BAD_WEIGHT = 2, OR_ERR_ITER_LIMIT = 3, OR_ERR_NO_MEMORY = 5 };
-enum { OR_V1 = 0, OR_V1A = 1, OR_V2 = 2, OR_V3 = 3, OR_V3A = 4, OR_V4 = 5 };
+enum { OR_V1 = 0, OR_V1A = 1, OR_V2 = 2, OR_V3 = 3, OR_V3A = 4, OR_V4 = 5,
+       /* binary-weight specialisations (Sec. Conventional Jaccard Similarity) */
+       OR_V3U = 6, OR_V3AU = 7, OR_V4U = 8 };
+static int is_unweighted(int variant) { return variant == OR_V3U || variant == OR_V3AU || variant == OR_V4U; }
 
 /* ------------------------------------------------------------------------ */
 /* Random stream.  SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output j of
@@ -96,6 +101,7 @@ typedef struct {
     double *dgamma;            /* gamma_i - gamma_{i-1}, i = 1..m-1 */
     double *c4, *inv4;         /* expm1(-lambda_i), 1/lambda_i, i = 1..m-1 */
     double delta;              /* 1/lambda_1 */
+    int unweighted;            /* binary weights: uniform variates, gamma_i = i */
 } or_consts;
 
 static void consts_free(or_consts *c)
@@ -154,10 +160,13 @@ int or_tables(uint32_t m, double *beta, double *gamma, double *dgamma, double *l
  * the i-th point is a direct function of i; for the uncorrelated ones it is
  * the running sum of the paper's recursion. */
 
-/* ProbMinHash3: x_i = w_inv * ((i-1) + Exp(lambda;0,1)). */
+/* ProbMinHash3: x_i = w_inv * ((i-1) + Exp(lambda;0,1)).  With binary weights
+ * (Sec. Conventional Jaccard Similarity) every element has the same interval
+ * boundaries, only the order of points matters, and Exp(lambda;0,1) is
+ * replaced by Uniform([0,1)). */
 static double pmh3_point(const or_consts *c, uint64_t key, double w_inv, uint64_t i)
 {
-    double te = or_texp(or_word(key, 2 * i - 2), c->c3, c->inv3);
+    double te = c->unweighted ? or_unif(or_word(key, 2 * i - 2)) : or_texp(or_word(key, 2 * i - 2), c->c3, c->inv3);
     double s = (double)(i - 1) + te;
     return w_inv * s;
 }
@@ -168,7 +177,11 @@ static double pmh4_point(const or_consts *c, uint64_t key, double w_inv, uint64_
 {
     uint64_t vw = or_word(key, 2 * i - 2);
     double s;
-    if (i < c->m) {
+    if (c->unweighted) {
+        /* binary weights: gamma_i = i, and both truncated exponentials and the last
+         * point's delta * Exp(1) become Uniform([0,1)) (Sec. Conventional Jaccard Similarity) */
+        s = (double)(i - 1) + or_unif(vw);
+    } else if (i < c->m) {
         double t = c->dgamma[i] * or_texp(vw, c->c4[i], c->inv4[i]);
         s = c->gamma[i - 1] + t;
     } else {
@@ -178,8 +191,11 @@ static double pmh4_point(const or_consts *c, uint64_t key, double w_inv, uint64_
     return w_inv * s;
 }
 
-/* Lower bound of point i of ProbMinHash4: w_inv * gamma_{i-1}. */
-static double pmh4_lower(const or_consts *c, double w_inv, uint64_t i) { return w_inv * c->gamma[i - 1]; }
+/* Lower bound of point i of ProbMinHash4: w_inv * gamma_{i-1} (gamma_{i-1} = i-1 with binary weights). */
+static double pmh4_lower(const or_consts *c, double w_inv, uint64_t i)
+{
+    return c->unweighted ? w_inv * (double)(i - 1) : w_inv * c->gamma[i - 1];
+}
 
 /* ------------------------------------------------------------------------ */
 /* Algorithm "Maintenance of stop limit" (Sec. Stop Limit Update): the array
@@ -600,7 +616,7 @@ static int64_t element_hashes(int variant, const or_consts *c, or_perm *p, uint6
     int64_t pts = 0;
     es->ntouched = 0;
     int fam = (variant == OR_V1 || variant == OR_V1A) ? 1 : (variant == OR_V2) ? 2
-            : (variant == OR_V3 || variant == OR_V3A) ? 3 : 4;
+            : (variant == OR_V3 || variant == OR_V3A || variant == OR_V3U || variant == OR_V3AU) ? 3 : 4;
     if (fam == 2 || fam == 4) perm_reset(p);
     double h = 0.0;
     for (uint64_t i = 1;; i++) {
@@ -687,7 +703,7 @@ static int run_brute(int variant, or_sig *s, const or_consts *c, const uint64_t 
 int or_sketch(int variant, int mode, const uint64_t *ids, const double *w, int64_t n, uint32_t m, uint64_t seed,
               double *q_out, uint64_t *z_out, uint64_t *stats_out)
 {
-    if (m < 1 || n < 0 || variant < 0 || variant > 5 || mode < 0 || mode > 1) return OR_ERR_INVALID_ARG;
+    if (m < 1 || n < 0 || variant < 0 || variant > 8 || mode < 0 || mode > 1) return OR_ERR_INVALID_ARG;
     if ((variant == OR_V3 || variant == OR_V3A || variant == OR_V4) && m < 2) return OR_ERR_INVALID_ARG;
     for (int64_t e = 0; e < n; e++) if (check_weight(w[e])) return OR_ERR_BAD_WEIGHT;
     or_consts c;
@@ -696,16 +712,27 @@ int or_sketch(int variant, int mode, const uint64_t *ids, const double *w, int64
     memset(&st, 0, sizeof(st));
     if (consts_init(&c, m)) return OR_ERR_NO_MEMORY;
     if (sig_init(&s, m)) { consts_free(&c); return OR_ERR_NO_MEMORY; }
+    /* binary weights: every element with w > 0 counts with weight 1 */
+    const double *wu = w;
+    double *ones = NULL;
+    if (is_unweighted(variant)) {
+        c.unweighted = 1;
+        ones = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        if (!ones) { sig_free(&s); consts_free(&c); return OR_ERR_NO_MEMORY; }
+        for (int64_t e = 0; e < n; e++) ones[e] = w[e] > 0.0 ? 1.0 : 0.0;
+        wu = ones;
+    }
     int rc;
-    if (mode == 1) rc = run_brute(variant, &s, &c, ids, w, n, seed, &st);
+    if (mode == 1) rc = run_brute(variant, &s, &c, ids, wu, n, seed, &st);
     else switch (variant) {
         case OR_V1: rc = run_pmh1(&s, ids, w, n, seed, &st); break;
         case OR_V1A: rc = run_pmh1a(&s, ids, w, n, seed, &st); break;
         case OR_V2: rc = run_pmh2(&s, &c, ids, w, n, seed, &st); break;
-        case OR_V3: rc = run_pmh3(&s, &c, ids, w, n, seed, &st); break;
-        case OR_V3A: rc = run_pmh3a(&s, &c, ids, w, n, seed, &st); break;
-        default: rc = run_pmh4(&s, &c, ids, w, n, seed, &st); break;
+        case OR_V3: case OR_V3U: rc = run_pmh3(&s, &c, ids, wu, n, seed, &st); break;
+        case OR_V3A: case OR_V3AU: rc = run_pmh3a(&s, &c, ids, wu, n, seed, &st); break;
+        default: rc = run_pmh4(&s, &c, ids, wu, n, seed, &st); break;
     }
+    free(ones);
     if (rc == OR_OK) {
         for (uint32_t k = 0; k < m; k++) {
             q_out[k] = s.q[k + 1];
@@ -752,6 +779,7 @@ int64_t or_near_ties(int variant, const uint64_t *ids, const double *w, int64_t 
                      const double *q, const uint64_t *z, double rel, uint8_t *flags, double *runner_up)
 {
     if ((variant == OR_V3 || variant == OR_V3A || variant == OR_V4) && m < 2) return -OR_ERR_INVALID_ARG;
+    const int unw = is_unweighted(variant);
     double qmax = 0.0;
     for (uint32_t k = 0; k < m; k++) if (q[k] > qmax) qmax = q[k];
     double bound = qmax * (1.0 + rel);
@@ -759,6 +787,7 @@ int64_t or_near_ties(int variant, const uint64_t *ids, const double *w, int64_t 
     or_perm p;
     elem_scratch es;
     if (consts_init(&c, m)) return -OR_ERR_NO_MEMORY;
+    c.unweighted = unw;
     if (perm_init(&p, m)) { consts_free(&c); return -OR_ERR_NO_MEMORY; }
     if (scratch_init(&es, m)) { perm_free(&p); consts_free(&c); return -OR_ERR_NO_MEMORY; }
     double *b1 = (double *)malloc(sizeof(double) * m), *b2 = (double *)malloc(sizeof(double) * m);
@@ -768,7 +797,7 @@ int64_t or_near_ties(int variant, const uint64_t *ids, const double *w, int64_t 
     for (uint32_t k = 0; rc == 0 && k < m; k++) { b1[k] = INFINITY; b2[k] = INFINITY; id1[k] = 0; }
     for (int64_t e = 0; rc == 0 && e < n; e++) {
         if (!(w[e] > 0.0)) continue;
-        const double w_inv = 1.0 / w[e];
+        const double w_inv = unw ? 1.0 : 1.0 / w[e];
         int64_t pts = element_hashes(variant, &c, &p, or_key(ids[e], seed), w_inv, bound, &es);
         if (pts < 0) { rc = -OR_ERR_ITER_LIMIT; break; }
         for (uint32_t t = 0; t < es.ntouched; t++) {

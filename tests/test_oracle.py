@@ -502,3 +502,99 @@ def test_bbit_estimator_is_unbiased(b):
         sd = np.sqrt((1 - jj) * p * (1 - p) / m) / (1 - p) / np.sqrt(len(est))
         assert abs(np.mean(est) - jj) < 5 * sd + 1e-12, (jj, np.mean(est))
     assert oracle.bbit_estimate(m, m, b) == 1.0
+
+
+# --------------------------------------------------- binary-weight specialisations
+# Sec. Conventional Jaccard Similarity: with weights in {0, 1} all elements share the interval
+# boundaries of ProbMinHash3/4, so the truncated exponentials become Uniform([0,1)) and
+# gamma_i = i; ProbMinHash4 then is SuperMinHash.
+UVARS = ["3u", "3au", "4u"]
+
+
+@pytest.mark.parametrize("variant", UVARS)
+def test_unweighted_early_stop_equals_brute_force(variant):
+    rng = np.random.default_rng(300 + UVARS.index(variant))
+    for trial in range(40):
+        n = int(rng.integers(1, 80))
+        m = int(rng.integers(1, 70))
+        ids, _ = _rand_set(rng, n, "unit")
+        w = np.ones(n)
+        q, z, _ = oracle.sketch(variant, ids, w, m, seed=trial)
+        qb, zb, _ = oracle.sketch(variant, ids, w, m, seed=trial, brute=True)
+        assert np.array_equal(z, zb) and np.array_equal(q, qb)
+
+
+def test_unweighted_interleaved_equals_sequential_and_ignores_weight_values():
+    rng = np.random.default_rng(310)
+    for trial in range(20):
+        n = int(rng.integers(1, 2000))
+        m = int(rng.choice([1, 2, 16, 256]))
+        ids, w = _rand_set(rng, n, "pareto")
+        q, z, _ = oracle.sketch("3u", ids, w, m, seed=trial)
+        qa, za, _ = oracle.sketch("3au", ids, w, m, seed=trial)
+        assert np.array_equal(z, za) and np.array_equal(q, qa)
+        # only w > 0 matters: the same set with unit weights has the same signature
+        q1, z1, _ = oracle.sketch("3u", ids, np.ones(n), m, seed=trial)
+        assert np.array_equal(z, z1) and np.array_equal(q, q1)
+        q4, z4, _ = oracle.sketch("4u", ids, w, m, seed=trial)
+        q41, z41, _ = oracle.sketch("4u", ids, np.ones(n), m, seed=trial)
+        assert np.array_equal(z4, z41) and np.array_equal(q4, q41)
+
+
+@pytest.mark.parametrize("variant", UVARS)
+def test_unweighted_marginals_are_uniform(variant):
+    # binary weights: every element wins a component with probability 1/n
+    ids = np.array([11, 22, 33, 44, 55], dtype=np.uint64)
+    m = 32
+    counts = np.zeros(len(ids))
+    for seed in range(400):
+        _, z, _ = oracle.sketch(variant, ids, np.ones(len(ids)), m, seed=seed)
+        for j, d in enumerate(ids):
+            counts[j] += np.count_nonzero(z == d)
+    assert counts.sum() == 400 * m
+    assert stats.chisquare(counts).pvalue > 1e-6
+
+
+def test_unweighted_points_are_uniform_plus_index():
+    # x_i = (i-1) + U_i: the fractional parts of the first points are Uniform([0,1))
+    rng = np.random.default_rng(320)
+    ids = W.distinct_ids(5, 2000, 5)
+    for variant in ("3u", "4u"):
+        q, _, _ = oracle.sketch(variant, ids[:1], np.ones(1), 4096, seed=9)   # one element: all its points
+        frac = q[np.isfinite(q)] % 1.0
+        assert stats.kstest(frac, "uniform").pvalue > 1e-4
+    # 4u draws labels without replacement: point i lands in its own component, so the integer
+    # parts of a single element's signature are a permutation of 0..m-1
+    q, _, _ = oracle.sketch("4u", ids[:1], np.ones(1), 4096, seed=9)
+    assert np.array_equal(np.sort(np.floor(q)), np.arange(4096))
+
+
+def test_pmh4u_is_superminhash():
+    # the binary-weight ProbMinHash4 has SuperMinHash's estimator variance alpha(m,u) J(1-J)/m
+    m, c = 16, 4000
+    rng = np.random.default_rng(330)
+    a_idx, b_idx = [0, 1, 2], [1, 2, 3]
+    jp = 0.5
+    alpha = float(_alpha(m, 4))
+    est = []
+    for t in range(c):
+        ids = W.distinct_ids(int(rng.integers(0, 2**40)), 4, t)
+        _, za, _ = oracle.sketch("4u", ids[a_idx], np.ones(3), m, seed=t)
+        _, zb, _ = oracle.sketch("4u", ids[b_idx], np.ones(3), m, seed=t)
+        est.append(oracle.count_equal(za, zb) / m)
+    mse = float(np.mean((np.array(est) - jp) ** 2))
+    assert mse / (alpha * jp * (1 - jp) / m) == pytest.approx(1.0, abs=0.12)
+
+
+def test_pmh3u_estimator_unbiased_for_jaccard():
+    # E[count/m] = J for binary weights (J_P = J, Sec. Probability Jaccard Similarity)
+    rng = np.random.default_rng(340)
+    m = 64
+    est = []
+    for t in range(600):
+        ids = W.distinct_ids(int(rng.integers(0, 2**40)), 30, t)
+        a, b = ids[:20], ids[10:]          # |A & B| = 10, |A | B| = 30: J = 1/3
+        _, za, _ = oracle.sketch("3u", a, np.ones(20), m, seed=t)
+        _, zb, _ = oracle.sketch("3u", b, np.ones(20), m, seed=t)
+        est.append(oracle.count_equal(za, zb) / m)
+    assert abs(np.mean(est) - 1 / 3) < 5 * np.std(est) / np.sqrt(len(est))
