@@ -41,14 +41,21 @@ typedef enum {
 
 /* The six algorithms of the paper.  1 and 1a (resp. 3 and 3a) are logically
  * equivalent and produce identical signatures (Sec. Interleaved Element
- * Processing); each is still computed as its own item. */
+ * Processing); each is still computed as its own item.  The last three are
+ * the binary-weight specialisations of Sec. Conventional Jaccard Similarity
+ * (for J rather than J_P): every element with w > 0 counts with weight 1,
+ * ProbMinHash3/3a/4 draw Uniform([0,1)) instead of their truncated
+ * exponentials, and gamma_i = i; PMH_V4U is SuperMinHash with a q_max stop. */
 typedef enum {
     PMH_V1 = 0,   /* Algorithm ProbMinHash1: with replacement, uncorrelated */
     PMH_V1A = 1,  /* Algorithm ProbMinHash1a: interleaved ProbMinHash1 */
     PMH_V2 = 2,   /* Algorithm ProbMinHash2: without replacement, uncorrelated */
     PMH_V3 = 3,   /* Algorithm ProbMinHash3: with replacement, correlated (m >= 2) */
     PMH_V3A = 4,  /* Algorithm ProbMinHash3a: interleaved ProbMinHash3 (m >= 2) */
-    PMH_V4 = 5    /* Algorithm ProbMinHash4: without replacement, correlated (m >= 2) */
+    PMH_V4 = 5,   /* Algorithm ProbMinHash4: without replacement, correlated (m >= 2) */
+    PMH_V3U = 6,  /* ProbMinHash3 with binary weights */
+    PMH_V3AU = 7, /* ProbMinHash3a with binary weights (identical to PMH_V3U) */
+    PMH_V4U = 8   /* ProbMinHash4 with binary weights */
 } pmh_variant;
 
 typedef enum {

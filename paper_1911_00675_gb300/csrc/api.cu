@@ -385,7 +385,7 @@ static pmh_status check_sketch_args(pmh_handle h, int64_t num_sets, uint32_t m, 
     if (precision != PMH_FP64 && precision != PMH_FP32_RECHECK) return fail(h, PMH_ERR_INVALID_ARG, "bad precision %d", precision);
     bool has_perm = false;
     for (int v = 0; v < num_variants; v++) {
-        if (variants[v] < PMH_V1 || variants[v] > PMH_V4) return fail(h, PMH_ERR_INVALID_ARG, "bad variant %d", variants[v]);
+        if (variants[v] < PMH_V1 || variants[v] > PMH_V4U) return fail(h, PMH_ERR_INVALID_ARG, "bad variant %d", variants[v]);
         if ((variants[v] == PMH_V3 || variants[v] == PMH_V3A || variants[v] == PMH_V4) && m < 2)
             return fail(h, PMH_ERR_INVALID_ARG, "variant %d requires m >= 2", variants[v]);
         has_perm |= (variants[v] == PMH_V2 || variants[v] == PMH_V4);

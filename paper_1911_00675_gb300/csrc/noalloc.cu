@@ -64,7 +64,7 @@ extern "C" pmh_status pmh_sketch_batch_noalloc(const uint64_t *ids, const double
     if (!variants || num_variants < 1 || num_variants > 8) return fail_na(PMH_ERR_INVALID_ARG, "need 1..8 variants");
     if (precision != PMH_FP64 && precision != PMH_FP32_RECHECK) return fail_na(PMH_ERR_INVALID_ARG, "bad precision %d", precision);
     for (int v = 0; v < num_variants; v++) {
-        if (variants[v] < PMH_V1 || variants[v] > PMH_V4) return fail_na(PMH_ERR_INVALID_ARG, "bad variant %d", variants[v]);
+        if (variants[v] < PMH_V1 || variants[v] > PMH_V4U) return fail_na(PMH_ERR_INVALID_ARG, "bad variant %d", variants[v]);
         if ((variants[v] == PMH_V3 || variants[v] == PMH_V3A || variants[v] == PMH_V4) && m < 2)
             return fail_na(PMH_ERR_INVALID_ARG, "variant %d requires m >= 2", variants[v]);
     }

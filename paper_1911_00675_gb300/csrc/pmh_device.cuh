@@ -30,9 +30,19 @@ constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr float kEta = 0x1p-18f;
 
 __host__ __device__ inline int family_of(int variant) {
-    // PMH_V1 = 0, V1A = 1 -> F1; V2 = 2 -> F2; V3 = 3, V3A = 4 -> F3; V4 = 5 -> F4
-    return variant <= 1 ? 1 : (variant == 2 ? 2 : (variant <= 4 ? 3 : 4));
+    // PMH_V1 = 0, V1A = 1 -> F1; V2 = 2 -> F2; V3 = 3, V3A = 4 -> F3; V4 = 5 -> F4;
+    // binary-weight V3U = 6, V3AU = 7 -> F3; V4U = 8 -> F4
+    switch (variant) {
+        case 0: case 1: return 1;
+        case 2: return 2;
+        case 3: case 4: case 6: case 7: return 3;
+        default: return 4;
+    }
 }
+// Binary-weight specialisations (Sec. Conventional Jaccard Similarity): every
+// element with w > 0 counts with weight 1, ProbMinHash3/3a/4 draw Uniform([0,1))
+// instead of their truncated exponentials, and gamma_i = i.
+__host__ __device__ inline bool variant_unweighted(int variant) { return variant >= 6 && variant <= 8; }
 
 // Per-m constants of Sec. ProbMinHash2/3/4, computed on the host in FP64
 // (arrays indexed as in the paper, length m+1).
@@ -101,6 +111,10 @@ __device__ __forceinline__ double point4_64(const Tables &T, uint64_t vw, uint32
         s = __dadd_rn(T.gamma[T.m - 1], t);
     }
     return __dmul_rn(w_inv, s);
+}
+// Binary-weight F3/F4 point: w_inv * ((i-1) + U), for every i (gamma_i = i)
+__device__ __forceinline__ double point_unw_64(uint64_t vw, uint64_t i, double w_inv) {
+    return __dmul_rn(w_inv, __dadd_rn((double)(i - 1), unif53(vw)));
 }
 __device__ __forceinline__ double lower3_64(uint64_t i, double w_inv) { return __dmul_rn(w_inv, (double)(i - 1)); }
 __device__ __forceinline__ double lower4_64(const Tables &T, uint32_t i, double w_inv) {

@@ -182,6 +182,7 @@ struct Ctx {
     int sigma;
     unsigned int *gbound32;        // grid mode: the item's bound shared by all CTAs (float bits), else null
     unsigned long long *gbound64;  //   and its FP64 bound (double bits)
+    bool unw;                      // binary-weight variant: w_inv = 1, uniform variates, gamma_i = i
 };
 
 __device__ __forceinline__ float ld_volatile(const float *p) { return *(volatile const float *)p; }
@@ -382,8 +383,8 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
     const uint64_t id = P.ids[c.beg + e];
     const double w = P.weights[c.beg + e];
     const uint64_t key = mix64(id ^ P.mixed_seed);
-    const double w_inv = (EXACT || !F32) ? __drcp_rn(w) : 0.0;
-    const float winv32 = winv_scaled(w, c.sigma);
+    const double w_inv = (EXACT || !F32) ? (c.unw ? 1.0 : __drcp_rn(w)) : 0.0;
+    const float winv32 = winv_scaled(c.unw ? 1.0 : w, c.sigma);
     if (FAM == 2 || FAM == 4) {
         for (uint32_t p = lane; p < m; p += 32) c.perm[p] = (uint16_t)p;
         __syncwarp();
@@ -403,10 +404,10 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
         if (!EXACT && FAM >= 3) {
             bool stop;
             if constexpr (F32) {
-                float lb = (FAM == 3) ? winv32 * (float)(base - 1) : winv32 * T.gamma32[base - 1];
+                float lb = (FAM == 3 || c.unw) ? winv32 * (float)(base - 1) : winv32 * T.gamma32[base - 1];
                 stop = lb * (1.0f - kEta) > ld_volatile(&c.ts->bound32);
             } else {
-                double lb = (FAM == 3) ? lower3_64(base, w_inv) : lower4_64(T, base, w_inv);
+                double lb = (FAM == 3 || c.unw) ? lower3_64(base, w_inv) : lower4_64(T, base, w_inv);
                 stop = lb > ld_volatile(&c.ts->bound64);
             }
             if (__shfl_sync(kFull, (int)stop, 0)) return 0.0;
@@ -433,7 +434,8 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
                 carry64 = run;
             } else if (hit) {
                 int src = __ffs(hit) - 1;
-                if (lane == src) x = (FAM == 3) ? point3_64(T, vw, i, w_inv) : point4_64(T, vw, i, w_inv);
+                if (lane == src) x = c.unw ? point_unw_64(vw, i, w_inv)
+                                           : (FAM == 3) ? point3_64(T, vw, i, w_inv) : point4_64(T, vw, i, w_inv);
             }
             if (hit) return __shfl_sync(kFull, x, __ffs(hit) - 1);
             continue;
@@ -456,6 +458,8 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
                 float err = __fadd_rn(__fsub_rn(c_hi, __fsub_rn(sh, bb)), __fsub_rn(tot, bb));
                 c_hi = sh;
                 c_lo = __fadd_rn(c_lo, err);
+            } else if (c.unw) {
+                x32 = act ? __fmul_rn(winv32, __fadd_rn((float)(i - 1), u53_to_float(vw >> 11))) : 0.0f;
             } else if (FAM == 3) {
                 x32 = act ? __fmul_rn(winv32, __fadd_rn((float)(i - 1), texp_32(vw, T.c3_32, T.inv3_32))) : 0.0f;
             } else {
@@ -484,6 +488,8 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
                     if (lane == s) x = run;
                 }
                 carry64 = run;
+            } else if (c.unw) {
+                x = act ? point_unw_64(vw, i, w_inv) : 0.0;
             } else if (FAM == 3) {
                 x = act ? point3_64(T, vw, i, w_inv) : 0.0;
             } else {
@@ -614,8 +620,7 @@ __device__ bool process_survivors(Ctx<F32> &c, int n) {
                 key = ws->sb_key[j];
                 winv32 = ws->sb_winv[j];
                 if constexpr (!F32) {
-                    const double w = P.weights[c.beg + e];
-                    w_inv = __drcp_rn(w);
+                    w_inv = c.unw ? 1.0 : __drcp_rn(P.weights[c.beg + e]);
                     id = P.ids[c.beg + e];
                 }
                 i = 1;
@@ -634,10 +639,10 @@ __device__ bool process_survivors(Ctx<F32> &c, int n) {
             // correlated families: point i lies above its lower bound
             if (FAM >= 3 && i >= 2) {
                 if constexpr (F32) {
-                    const float lb = (FAM == 3) ? winv32 * (float)(i - 1) : winv32 * T.gamma32[i - 1];
+                    const float lb = (FAM == 3 || c.unw) ? winv32 * (float)(i - 1) : winv32 * T.gamma32[i - 1];
                     done = lb * (1.0f - kEta) > ld_volatile(&c.ts->bound32);
                 } else {
-                    const double lb = (FAM == 3) ? lower3_64(i, w_inv) : lower4_64(T, i, w_inv);
+                    const double lb = (FAM == 3 || c.unw) ? lower3_64(i, w_inv) : lower4_64(T, i, w_inv);
                     done = lb > ld_volatile(&c.ts->bound64);
                 }
             }
@@ -671,6 +676,7 @@ __device__ bool process_survivors(Ctx<F32> &c, int n) {
                     float x32;
                     if (FAM == 1) { s32 = __fadd_rn(s32, exp1_32(vw)); x32 = __fmul_rn(winv32, s32); }
                     else if (FAM == 2) { s32 = __fadd_rn(s32, __fmul_rn(T.beta32[i], exp1_32(vw))); x32 = __fmul_rn(winv32, s32); }
+                    else if (c.unw) x32 = __fmul_rn(winv32, __fadd_rn((float)(i - 1), u53_to_float(vw >> 11)));
                     else if (FAM == 3) x32 = __fmul_rn(winv32, __fadd_rn((float)(i - 1), texp_32(vw, T.c3_32, T.inv3_32)));
                     else {
                         float sv;
@@ -688,6 +694,7 @@ __device__ bool process_survivors(Ctx<F32> &c, int n) {
                 } else {
                     if (FAM == 1) x64 = __dadd_rn(x64, term1_64(vw, w_inv));
                     else if (FAM == 2) x64 = __dadd_rn(x64, term2_64(T, vw, i, w_inv));
+                    else if (c.unw) x64 = point_unw_64(vw, i, w_inv);
                     else if (FAM == 3) x64 = point3_64(T, vw, i, w_inv);
                     else x64 = point4_64(T, vw, i, w_inv);
                     const double b64 = ld_volatile(&c.ts->bound64);
@@ -706,7 +713,7 @@ __device__ bool process_survivors(Ctx<F32> &c, int n) {
                     int est;
                     if (!(y < 1e9f)) est = 1 << 30;
                     else if (FAM == 1 || FAM == 2) { const float mu = fmaxf(y, 0.0f); est = (int)(mu + 3.0f * sqrtf(mu) + 2.0f); }
-                    else if (FAM == 3) est = (int)y;
+                    else if (FAM == 3 || c.unw) est = (int)y;
                     else est = (int)((float)m * (1.0f - __expf(-T.lambda1_32 * y)) * 1.001f) + 1;
                     if (est >= kCap) to_deep = true;
                 }
@@ -759,7 +766,7 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
     constexpr int team_warps = TW;
     TeamShared *ts = c.ts;
     WarpShared *ws = c.ws;
-    const float te_lo = (FAM >= 3) ? P.tab.te_lo : 1.0f;
+    const float te_lo = (FAM >= 3 && !c.unw) ? P.tab.te_lo : 1.0f;
     if (lane == 0) ws->sb_n = 0;
     __syncwarp();
     bool refreshed = false;
@@ -817,7 +824,7 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
                 if (weight_positive(w)) {
                     valid[h] = true;
                     key[h] = mix64(P.ids[c.beg + e] ^ P.mixed_seed);
-                    winv[h] = winv_scaled(w, c.sigma);
+                    winv[h] = winv_scaled(c.unw ? 1.0 : w, c.sigma);
                     const float xlo = winv[h] * unif_lo(value_word(key[h], 1)) * te_lo;
                     surv[h] = !(xlo * (1.0f - 8.0f * 0x1p-24f) > ld_volatile(&ts->bound32));
                 }
@@ -892,7 +899,9 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
         if constexpr (F32) ((uint64_t *)c.sig)[k] = kEmptyKey;
         else { ((Rec64 *)c.sig)[k].q = __longlong_as_double(0x7FF0000000000000ll); ((Rec64 *)c.sig)[k].id = 0; }
     }
-    const SetStat st0 = P.stats[set];
+    c.unw = variant_unweighted(P.variants[item_v]);
+    SetStat st0 = P.stats[set];
+    if (c.unw) st0.wsum = (double)st0.npos;   // binary weights: each element counts 1
     if (leader) {
         ts->status = st0.bad ? PMH_ERR_BAD_WEIGHT : PMH_OK;
         ts->unfilled = (int)m;
@@ -1100,7 +1109,9 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
     const uint32_t m = P.m;
     TeamShared *ts = c.ts;
     const bool leader = threadIdx.x == 0;
-    const SetStat st0 = P.stats[set];
+    c.unw = variant_unweighted(P.variants[item_v]);
+    SetStat st0 = P.stats[set];
+    if (c.unw) st0.wsum = (double)st0.npos;   // binary weights: each element counts 1
     const bool live = !st0.bad && st0.npos > 0;
     for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
         if constexpr (F32) ((uint64_t *)c.sig)[k] = kEmptyKey;

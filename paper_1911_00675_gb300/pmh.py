@@ -17,8 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libpmh.so")
 
 OK, ERR_INVALID_ARG, ERR_BAD_WEIGHT, ERR_ITER_LIMIT, ERR_CUDA, ERR_NO_MEMORY, ERR_UNSUPPORTED = range(7)
-V1, V1A, V2, V3, V3A, V4 = range(6)
-VARIANTS = {"1": V1, "1a": V1A, "2": V2, "3": V3, "3a": V3A, "4": V4}
+V1, V1A, V2, V3, V3A, V4, V3U, V3AU, V4U = range(9)
+VARIANTS = {"1": V1, "1a": V1A, "2": V2, "3": V3, "3a": V3A, "4": V4, "3u": V3U, "3au": V3AU, "4u": V4U}
 FP64, FP32_RECHECK = 0, 1
 SHAPE_WARP, SHAPE_CTA8, SHAPE_QUAD, SHAPE_PAIR, SHAPE_QUAD8, SHAPE_QUAD8L = range(6)
 COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "rounds", "deep", "prefiltered",
