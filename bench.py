@@ -37,9 +37,15 @@ VARIANTS = ["1", "1a", "2", "3", "3a", "4"]
 # Algorithmic integer/FP32 operations per unit of work (counted from the
 # method's arithmetic): one SplitMix64 word is 2 64-bit
 # xor-shift-multiply rounds + 1 xor-shift + the counter add = 20 32-bit ops.
-OPS_KEY = 20            # element key: mix(id ^ mix(seed))
-OPS_FIRST_REJECT = 26   # value word (20) + log-free lower bound and compare (6)
-OPS_POINT = 60          # value word (20) + label word (20) + logarithm (~10) + scale/compare (5) + offer (5)
+# SplitMix64 word: three 64-bit xor-shifts (4 each), two 64-bit multiplies by a constant (3 each) and the
+# 64-bit counter add (2) = 20.
+OPS_ELEMENT = 60        # every element-variant: key = mix(id ^ mix(seed)) (22), weight check (2), scaled 1/w
+                        # from the exponent and mantissa with one reciprocal (10), value word of point 1 (20),
+                        # 23-bit uniform lower bound (3), bound product and compare (3)
+OPS_POINT = 70          # every generated point: value word (20), label word (20), label from the word (3;
+                        # the lazy permutation's bookkeeping is not counted), logarithm (20), point value and
+                        # stop compare (4), offer to the component (3)
+OPS_POINT1_SHARED = 20  # the value word of a survivor's point 1 was counted with its element
 LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes issue one instruction per clock
 OPS_PAIR_COMPONENT = 3  # equal-component count: two 32-bit compares and one add per component pair
 # 8-bit codes, per pair of 64-bit words (8 fields): xor (2), per 32-bit half three fold steps of
@@ -460,7 +466,8 @@ def main():
     k_avg = statistics.mean(kernel_ms)
     sm_mhz = clk["sm_mhz"] if clk else 2070.0
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    per_launch_ops = (c["elements"] * OPS_KEY + c["prefiltered"] * OPS_FIRST_REJECT + c["points32"] * OPS_POINT)
+    survivors = c["elements"] - c["prefiltered"]
+    per_launch_ops = c["elements"] * OPS_ELEMENT + c["points32"] * OPS_POINT - survivors * OPS_POINT1_SHARED
     achieved = per_launch_ops / (k_avg * 1e-3) / 1e12
     peak = n_sms * LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (32-bit lane ops)",
