@@ -47,7 +47,11 @@ namespace pmh {
 constexpr int kMaxCont = 64;       // contender records per team (overflow -> PMH_ERR_ITER_LIMIT)
 constexpr int kCasLimit = 1 << 16; // CAS retries per offer (each failure means another offer succeeded)
 constexpr int kSurvCap = 128;      // survivor buffer per warp: < 64 left over + <= 64 new per filter step
-constexpr int kSurvBatch = 64;     // survivors expanded together (keeps the lanes of the expansion busy)
+#ifndef PMH_SURV_BATCH
+#define PMH_SURV_BATCH 64
+#endif
+constexpr int kSurvBatch = PMH_SURV_BATCH;   // survivors expanded together (keeps the lanes of the expansion busy)
+static_assert(kSurvBatch >= 1 && kSurvBatch <= 64, "the buffer holds < kSurvBatch left over + 64 new");
 
 struct __align__(16) Rec64 {
     double q;
@@ -583,9 +587,20 @@ __device__ __forceinline__ uint32_t resolve_contenders(Ctx<true> &c) {
 // Long sequences go to warp-cooperative deep mode instead; so does a
 // sequence that outgrows the lane-sequential cap (the FP32 running sum's error
 // bound holds for at most kSeqCap terms, the write list has kFyCap entries).
-constexpr int kPrefSteps = 4;  // filter: L2 prefetch distance in 64-element steps of a warp
-constexpr int kSeqCap = 32;   // lane-sequential points (ProbMinHash1/2/4)
-constexpr int kSeqCap3 = 64;  // lane-sequential points (ProbMinHash3)
+// Tuning constants (compile-time; the defaults are the measured best on c2).
+#ifndef PMH_PREF_STEPS
+#define PMH_PREF_STEPS 4
+#endif
+#ifndef PMH_SEQ_CAP
+#define PMH_SEQ_CAP 32
+#endif
+#ifndef PMH_SEQ_CAP3
+#define PMH_SEQ_CAP3 64
+#endif
+constexpr int kPrefSteps = PMH_PREF_STEPS;  // filter: L2 prefetch distance in 64-element steps of a warp
+constexpr int kSeqCap = PMH_SEQ_CAP;        // lane-sequential points (ProbMinHash1)
+constexpr int kSeqCap3 = PMH_SEQ_CAP3;      // lane-sequential points (ProbMinHash3)
+static_assert(kSeqCap <= 32, "the FP32 running-sum error bound holds for at most 32 terms");
 
 template <int FAM, bool F32>
 __device__ bool process_survivors(Ctx<F32> &c, int n) {
