@@ -361,9 +361,18 @@ inline cudaError_t plan_batch(int sm_count, int precision, uint32_t m, const int
 // on `st`.  `ev` (optional) receives records before the queue build, before
 // the sketch kernels and after them; `fam_ev` (optional) one record after
 // each family's kernels, in plan order.
+// Streams and events that let the family kernels of one call run side by side
+// (forked from and joined back into the caller's stream), so that the SMs one
+// family's kernel leaves idle in its tail start the next family's items.
+struct FamilyFork {
+    cudaStream_t s[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
 inline cudaError_t enqueue_batch(SketchParams p, const Plan &plan, int precision, int sm_count, uint64_t *queue,
                                  unsigned int *qmeta, SetStat *stats, cudaStream_t st, cudaEvent_t *ev,
-                                 cudaEvent_t *fam_ev = nullptr) {
+                                 cudaEvent_t *fam_ev = nullptr, const FamilyFork *ff = nullptr) {
     const int64_t items = p.num_sets * p.num_variants;
     FamOfVariant fv{};
     for (int v = 0; v < p.num_variants; v++) fv.f[v] = family_of(p.variants[v]);
@@ -384,17 +393,30 @@ inline cudaError_t enqueue_batch(SketchParams p, const Plan &plan, int precision
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     p.stats = stats;
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
+    const bool forked = ff && plan.nfam > 1;
+    if (forked) {
+        if ((e = cudaEventRecord(ff->fork, st)) != cudaSuccess) return e;
+        for (int j = 0; j < plan.nfam; j++)
+            if ((e = cudaStreamWaitEvent(ff->s[j], ff->fork, 0)) != cudaSuccess) return e;
+    }
     for (int j = 0; j < plan.nfam; j++) {
+        cudaStream_t sj = forked ? ff->s[j] : st;
         p.queue = queue + plan.qbase[j];
         p.queue_len = plan.qlen[j];
         p.head = qmeta + kQHead + (plan.fam[j] - 1);
-        e = sketch_launch_any(precision == PMH_FP32_RECHECK, plan.fam[j], plan.shape[j], plan.grid[j], p, st);
+        e = sketch_launch_any(precision == PMH_FP32_RECHECK, plan.fam[j], plan.shape[j], plan.grid[j], p, sj);
         if (e != cudaSuccess) return e;
         if (p.gctl && plan.ggrid[j] > 0) {
-            e = grid_launch_any(precision == PMH_FP32_RECHECK, plan.fam[j], plan.gshape[j], plan.ggrid[j], p, st);
+            e = grid_launch_any(precision == PMH_FP32_RECHECK, plan.fam[j], plan.gshape[j], plan.ggrid[j], p, sj);
             if (e != cudaSuccess) return e;
         }
-        if (fam_ev && (e = cudaEventRecord(fam_ev[j], st)) != cudaSuccess) return e;
+        if (fam_ev && (e = cudaEventRecord(fam_ev[j], sj)) != cudaSuccess) return e;
+    }
+    if (forked) {
+        for (int j = 0; j < plan.nfam; j++) {
+            if ((e = cudaEventRecord(ff->join[j], ff->s[j])) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(st, ff->join[j], 0)) != cudaSuccess) return e;
+        }
     }
     if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
     return cudaSuccess;
