@@ -68,6 +68,7 @@ typedef struct pmh_handle_s *pmh_handle;
 
 /* Limits. */
 #define PMH_MAX_M 8192u                 /* signature size m <= 8192 */
+#define PMH_MAX_VARIANTS 16             /* variants per pmh_sketch_batch call (repeats allowed) */
 #define PMH_MAX_SET_ELEMENTS 0xFFFFFFFFll /* elements per set < 2^32 */
 
 /* Device counters written by pmh_sketch_batch when `counters` is non-NULL
@@ -125,7 +126,8 @@ const char *pmh_last_error(pmh_handle h);
  *             whose offsets are decreasing gets PMH_ERR_INVALID_ARG in set_status.
  *   num_sets  >= 0.
  *   m         signature size, 1 <= m <= PMH_MAX_M (m >= 2 for V3/V3A/V4).
- *   variants  host int32[num_variants] of pmh_variant values (repeats allowed);
+ *   variants  host int32[num_variants] of pmh_variant values (repeats allowed),
+ *             1 <= num_variants <= PMH_MAX_VARIANTS;
  *             item (v, s) is set s sketched with variants[v].
  *   precision pmh_precision.
  *   seed      stream seed; signatures are comparable only for equal (m, seed)

@@ -27,7 +27,7 @@ struct GraphKey {
     const void *ids, *weights, *offsets, *out_ids, *out_q, *status, *counters;
     int64_t num_sets;
     uint32_t m;
-    int32_t variants[8];
+    int32_t variants[PMH_MAX_VARIANTS];
     int32_t num_variants, precision, profiling;
     uint64_t seed;
     int32_t kinds[4];
@@ -402,10 +402,11 @@ static pmh_status check_sketch_args(pmh_handle h, int64_t num_sets, uint32_t m, 
                                     int32_t num_variants, int32_t precision) {
     if (num_sets < 0) return fail(h, PMH_ERR_INVALID_ARG, "num_sets < 0");
     if (num_sets >= (1ll << 40)) return fail(h, PMH_ERR_UNSUPPORTED, "num_sets >= 2^40");
-    if (num_variants >= 1 && num_variants <= 8 && num_sets * num_variants > 0x7FFFFFFFll - (1ll << 24))
+    if (num_variants >= 1 && num_variants <= PMH_MAX_VARIANTS && num_sets * num_variants > 0x7FFFFFFFll - (1ll << 24))
         return fail(h, PMH_ERR_UNSUPPORTED, "num_sets * num_variants too large for one call");
     if (m < 1 || m > PMH_MAX_M) return fail(h, PMH_ERR_UNSUPPORTED, "m = %u outside [1, %u]", m, PMH_MAX_M);
-    if (!variants || num_variants < 1 || num_variants > 8) return fail(h, PMH_ERR_INVALID_ARG, "need 1..8 variants");
+    if (!variants || num_variants < 1 || num_variants > PMH_MAX_VARIANTS)
+        return fail(h, PMH_ERR_INVALID_ARG, "need 1..%d variants", PMH_MAX_VARIANTS);
     if (precision != PMH_FP64 && precision != PMH_FP32_RECHECK) return fail(h, PMH_ERR_INVALID_ARG, "bad precision %d", precision);
     bool has_perm = false;
     for (int v = 0; v < num_variants; v++) {

@@ -90,7 +90,7 @@ constexpr int64_t kStatChunk = 65536;           // elements per statistics chunk
 constexpr int64_t kStatBig = 4 * kStatChunk;    // sets longer than this are split over all blocks
 
 struct FamOfVariant {
-    int f[8];
+    int f[PMH_MAX_VARIANTS];
 };
 
 __device__ __forceinline__ int queue_bucket(const int64_t *off, int64_t s) {

@@ -61,7 +61,8 @@ extern "C" pmh_status pmh_sketch_batch_noalloc(const uint64_t *ids, const double
     set_thread_error("");
     if (num_sets < 0) return fail_na(PMH_ERR_INVALID_ARG, "num_sets < 0");
     if (m < 1 || m > PMH_MAX_M) return fail_na(PMH_ERR_UNSUPPORTED, "m = %u outside [1, %u]", m, PMH_MAX_M);
-    if (!variants || num_variants < 1 || num_variants > 8) return fail_na(PMH_ERR_INVALID_ARG, "need 1..8 variants");
+    if (!variants || num_variants < 1 || num_variants > PMH_MAX_VARIANTS)
+        return fail_na(PMH_ERR_INVALID_ARG, "need 1..%d variants", PMH_MAX_VARIANTS);
     if (precision != PMH_FP64 && precision != PMH_FP32_RECHECK) return fail_na(PMH_ERR_INVALID_ARG, "bad precision %d", precision);
     for (int v = 0; v < num_variants; v++) {
         if (variants[v] < PMH_V1 || variants[v] > PMH_V4U) return fail_na(PMH_ERR_INVALID_ARG, "bad variant %d", variants[v]);

@@ -101,7 +101,7 @@ struct SketchParams {
     int64_t num_sets;
     uint32_t m;
     uint64_t mixed_seed;          // mix64(seed)
-    int32_t variants[8];
+    int32_t variants[PMH_MAX_VARIANTS];
     int32_t num_variants;
     Tables tab;
     uint64_t *out_ids;

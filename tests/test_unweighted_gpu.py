@@ -52,3 +52,18 @@ def test_unweighted_grid_mode(H):
             check_sets(b, v, z[vi], q[vi], range(b.num_sets), seed=6)
     finally:
         H.set_thresholds()
+
+
+def test_all_nine_variants_and_repeats_in_one_call(H):
+    from paper_1911_00675_gb300 import pmh
+    b = W.random_batch(750, [3, 90, 1200], 128, "unit")
+    allv = ["1", "1a", "2", "3", "3a", "4", "3u", "3au", "4u"]
+    vs = allv + ["4u", "1", "3", "2", "3au", "4", "1a"]          # 16: the most one call takes
+    z, q, st = run(H, b, vs, 1, with_q=True, seed=21)
+    assert (st == 0).all()
+    for vi, v in enumerate(vs):
+        zi, qi, _ = run(H, b, [v], 1, with_q=True, seed=21)
+        assert np.array_equal(z[vi], zi[0]) and np.array_equal(q[vi], qi[0]), v
+    with pytest.raises(pmh.PmhError) as ei:
+        run(H, b, vs + ["1"], 1)
+    assert ei.value.code == pmh.ERR_INVALID_ARG
