@@ -93,6 +93,8 @@ enum {
     PMH_CNT_CYC_ITEM = 15,    /* whole items, from the queue fetch to the barrier after write-out */
     PMH_CNT_CYC_WARP = 16,    /* warp lifetime in the sketch kernels (start to exit) */
     PMH_CNT_CYC_BARRIER = 17, /* waiting for the team's other warps at the end of a round (part of CYC_FIRST) */
+    PMH_CNT_SEQ_STEPS = 18,   /* warp steps of lane-sequential survivor expansion (32 lane slots each) */
+    PMH_CNT_SEQ_POINTS = 19,  /* points evaluated lane-sequentially (part of POINTS32/POINTS64) */
     PMH_NUM_COUNTERS = 20
 };
 

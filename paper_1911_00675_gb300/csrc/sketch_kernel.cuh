@@ -140,7 +140,7 @@ struct WarpShared {
     unsigned long long cnt[PMH_NUM_COUNTERS];   // work counters of this warp (lane 0 adds)
     int dq_n;                  // deep-mode queue length (the queue reuses sb_e, see process_survivors)
     int slot[32];              // Fisher-Yates scratch (deep mode)
-    uint32_t sb_e[kSurvCap];   // prefilter survivors: element index
+    uint32_t sb_e[32 + kSurvCap];   // prefilter survivors: element index, from sb_e[32] (deep queue from sb_e[0])
     uint64_t sb_key[kSurvCap]; //   stream key
     float sb_winv[kSurvCap];   //   and scaled FP32 reciprocal weight
     int sb_n;
@@ -597,13 +597,43 @@ __device__ __forceinline__ uint32_t resolve_contenders(Ctx<true> &c) {
 #ifndef PMH_SEQ_CAP3
 #define PMH_SEQ_CAP3 64
 #endif
+#ifndef PMH_SEQ_KEEP
+#define PMH_SEQ_KEEP 8
+#endif
+#ifndef PMH_SEQ_KEEP_FAMS
+#define PMH_SEQ_KEEP_FAMS 3     // families whose busy lanes carry over (bit f-1: ProbMinHash f); the measured best on c2
+#endif
 constexpr int kPrefSteps = PMH_PREF_STEPS;  // filter: L2 prefetch distance in 64-element steps of a warp
+constexpr int kSeqKeep = PMH_SEQ_KEEP;      // idle lanes at which a dry buffer hands the rest to the next call (0: never)
+static_assert(kSeqKeep >= 0 && kSeqKeep <= 32, "a count of lanes");
 constexpr int kSeqCap = PMH_SEQ_CAP;        // lane-sequential points (ProbMinHash1)
 constexpr int kSeqCap3 = PMH_SEQ_CAP3;      // lane-sequential points (ProbMinHash3)
 static_assert(kSeqCap <= 32, "the FP32 running-sum error bound holds for at most 32 terms");
 
+// Lane-sequential state of one lane: the survivor it is expanding.  For
+// ProbMinHash1/3 it outlives a call of process_survivors: when the buffer runs
+// dry while a few lanes are still busy, those lanes keep their elements and
+// resume them in the next call, together with the survivors that the filter
+// buffered meanwhile (the bound only falls in between, so a resumed sequence
+// stops no later than it would have).  ProbMinHash2/4 lanes keep their
+// Fisher-Yates write lists in place meanwhile; since those share bytes with
+// the deep-mode permutation, their deep queue waits for a call that ends with
+// every lane idle.  Which families carry lanes over is a tuning constant
+// (PMH_SEQ_KEEP_FAMS).
+template <bool F32>
+struct SeqLane {
+    bool has;
+    uint32_t e, i;
+    uint64_t key, id;
+    float winv32, s32;
+    double w_inv, x64;
+    int fyn;
+};
+
+// Expands the n buffered survivors (ws->sb_e[32 + j], sb_key[j], sb_winv[j]).
+// fin: the last call of the pass (every sequence ends in it).
 template <int FAM, bool F32>
-__device__ bool process_survivors(Ctx<F32> &c, int n) {
+__device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, int n, bool fin) {
     const long long t_sv = clock64();
     const SketchParams &P = *c.p;
     const Tables &T = P.tab;
@@ -612,75 +642,76 @@ __device__ bool process_survivors(Ctx<F32> &c, int n) {
     WarpShared *ws = c.ws;
     constexpr bool kPerm = (FAM == 2 || FAM == 4);
     constexpr int kCap = (FAM == 3) ? kSeqCap3 : (kPerm ? kFyCap : kSeqCap);   // the write list bounds ProbMinHash2/4
-    bool has = false, won = false;
-    uint32_t e = 0, i = 0;
-    uint64_t key = 0, id = 0;
-    float winv32 = 0.0f, s32 = 0.0f;
-    double w_inv = 0.0, x64 = 0.0;
-    int fyn = 0;
+    constexpr bool kKeep = kSeqKeep > 0 && ((PMH_SEQ_KEEP_FAMS >> (FAM - 1)) & 1);
+    bool won = false;
     int next = 0;
     uint32_t npts = 0;
-    if (lane == 0) ws->dq_n = 0;
-    __syncwarp();
+    int nsteps = 0;
 #pragma unroll 1
-    for (int step = 0;; ++step) {
+    for (;; ++nsteps) {
         // idle lanes take the next survivors
-        const unsigned idle = __ballot_sync(kFull, !has);
+        const unsigned idle = __ballot_sync(kFull, !L.has);
         const int avail = n - next;
         if (avail > 0 && idle) {
             const int rank = __popc(idle & ((1u << lane) - 1u));
-            if (!has && rank < avail) {
+            if (!L.has && rank < avail) {
                 const int j = next + rank;
-                e = ws->sb_e[j];
-                key = ws->sb_key[j];
-                winv32 = ws->sb_winv[j];
+                L.e = ws->sb_e[32 + j];
+                L.key = ws->sb_key[j];
+                L.winv32 = ws->sb_winv[j];
                 if constexpr (!F32) {
-                    w_inv = c.unw ? 1.0 : __drcp_rn(P.weights[c.beg + e]);
-                    id = P.ids[c.beg + e];
+                    L.w_inv = c.unw ? 1.0 : __drcp_rn(P.weights[c.beg + L.e]);
+                    L.id = P.ids[c.beg + L.e];
                 }
-                i = 1;
-                s32 = 0.0f;
-                x64 = 0.0;
-                fyn = 0;
-                has = true;
+                L.i = 1;
+                L.s32 = 0.0f;
+                L.x64 = 0.0;
+                L.fyn = 0;
+                L.has = true;
             }
             next += min(__popc(idle), avail);
+        } else if (kKeep && !fin && avail <= 0 && __popc(idle) >= kSeqKeep) {
+            if (!kPerm) break;   // the buffer is dry: the busy lanes carry on in the next call
+            __syncwarp();
+            if (ld_volatile(&ws->dq_n) + 32 - __popc(idle) <= 32) break;
         }
-        // every taken slot has been read: the deep queue may now reuse sb_e[0, next)
+        // every taken slot has been read.  The deep queue fills sb_e[0, 32 + next):
+        // it holds at most one entry per survivor taken here or carried in (< 32),
+        // plus, for ProbMinHash2/4, the entries left waiting (with the carried lanes <= 32)
         __syncwarp();
-        if (!__any_sync(kFull, has)) break;
-        if (has) {
+        if (!__any_sync(kFull, L.has)) break;
+        if (L.has) {
             bool done = false, to_deep = false;
             // correlated families: point i lies above its lower bound
-            if (FAM >= 3 && i >= 2) {
+            if (FAM >= 3 && L.i >= 2) {
                 if constexpr (F32) {
-                    const float lb = (FAM == 3 || c.unw) ? winv32 * (float)(i - 1) : winv32 * T.gamma32[i - 1];
+                    const float lb = (FAM == 3 || c.unw) ? L.winv32 * (float)(L.i - 1) : L.winv32 * T.gamma32[L.i - 1];
                     done = lb * (1.0f - kEta) > ld_volatile(&c.ts->bound32);
                 } else {
-                    const double lb = (FAM == 3 || c.unw) ? lower3_64(i, w_inv) : lower4_64(T, i, w_inv);
+                    const double lb = (FAM == 3 || c.unw) ? lower3_64(L.i, L.w_inv) : lower4_64(T, L.i, L.w_inv);
                     done = lb > ld_volatile(&c.ts->bound64);
                 }
             }
             if (!done) {
-                const uint64_t vw = value_word(key, i);
-                const uint64_t lw = label_word(key, i);
+                const uint64_t vw = value_word(L.key, L.i);
+                const uint64_t lw = label_word(L.key, L.i);
                 uint32_t k;
                 if constexpr (kPerm) {
                     // step t = i-1 of the lazy Fisher-Yates permutation; list entry = (position << 16) | value
-                    const uint32_t t = i - 1;
+                    const uint32_t t = L.i - 1;
                     const uint32_t r = t + uniform_int(lw, m - t);
                     uint32_t moved = t, lab = r;   // untouched positions hold their own index
                     // the latest write wins: scanning backwards, keep the first match
-                    for (int j = fyn - 1; j >= 0; --j) {
+                    for (int j = L.fyn - 1; j >= 0; --j) {
                         const uint32_t ent = c.fy[j * 32 + lane];
                         if ((ent >> 16) == t) { moved = ent & 0xFFFFu; break; }
                     }
-                    for (int j = fyn - 1; j >= 0; --j) {
+                    for (int j = L.fyn - 1; j >= 0; --j) {
                         const uint32_t ent = c.fy[j * 32 + lane];
                         if ((ent >> 16) == r) { lab = ent & 0xFFFFu; break; }
                     }
-                    if (fyn < kFyCap) c.fy[fyn * 32 + lane] = (r << 16) | moved;
-                    fyn++;
+                    if (L.fyn < kFyCap) c.fy[L.fyn * 32 + lane] = (r << 16) | moved;
+                    L.fyn++;
                     k = lab;
                 } else {
                     k = uniform_int(lw, m);
@@ -689,41 +720,41 @@ __device__ bool process_survivors(Ctx<F32> &c, int n) {
                 float y = 0.0f;
                 if constexpr (F32) {
                     float x32;
-                    if (FAM == 1) { s32 = __fadd_rn(s32, exp1_32(vw)); x32 = __fmul_rn(winv32, s32); }
-                    else if (FAM == 2) { s32 = __fadd_rn(s32, __fmul_rn(T.beta32[i], exp1_32(vw))); x32 = __fmul_rn(winv32, s32); }
-                    else if (c.unw) x32 = __fmul_rn(winv32, __fadd_rn((float)(i - 1), u53_to_float(vw >> 11)));
-                    else if (FAM == 3) x32 = __fmul_rn(winv32, __fadd_rn((float)(i - 1), texp_32(vw, T.c3_32, T.inv3_32)));
+                    if (FAM == 1) { L.s32 = __fadd_rn(L.s32, exp1_32(vw)); x32 = __fmul_rn(L.winv32, L.s32); }
+                    else if (FAM == 2) { L.s32 = __fadd_rn(L.s32, __fmul_rn(T.beta32[L.i], exp1_32(vw))); x32 = __fmul_rn(L.winv32, L.s32); }
+                    else if (c.unw) x32 = __fmul_rn(L.winv32, __fadd_rn((float)(L.i - 1), u53_to_float(vw >> 11)));
+                    else if (FAM == 3) x32 = __fmul_rn(L.winv32, __fadd_rn((float)(L.i - 1), texp_32(vw, T.c3_32, T.inv3_32)));
                     else {
                         float sv;
-                        if (i < m) sv = __fadd_rn(T.gamma32[i - 1], __fmul_rn(T.dgamma32[i], texp_32(vw, T.c4_32[i], T.inv4_32[i])));
+                        if (L.i < m) sv = __fadd_rn(T.gamma32[L.i - 1], __fmul_rn(T.dgamma32[L.i], texp_32(vw, T.c4_32[L.i], T.inv4_32[L.i])));
                         else sv = __fadd_rn(T.gamma32[m - 1], __fmul_rn(T.delta32, exp1_32(vw)));
-                        x32 = __fmul_rn(winv32, sv);
+                        x32 = __fmul_rn(L.winv32, sv);
                     }
                     const float b32 = ld_volatile(&c.ts->bound32);
                     beyond = x32 * (1.0f - kEta) > b32;
-                    if (!beyond) won |= Offer<true>::run(c, k, x32, e);
-                    if (i == 1) {
-                        y = __fdiv_rn(b32, winv32) * (1.0f + 4.0f * kEta);
-                        if (FAM == 1 || FAM == 2) y -= s32 * (1.0f - kEta);
+                    if (!beyond) won |= Offer<true>::run(c, k, x32, L.e);
+                    if (L.i == 1) {
+                        y = __fdiv_rn(b32, L.winv32) * (1.0f + 4.0f * kEta);
+                        if (FAM == 1 || FAM == 2) y -= L.s32 * (1.0f - kEta);
                     }
                 } else {
-                    if (FAM == 1) x64 = __dadd_rn(x64, term1_64(vw, w_inv));
-                    else if (FAM == 2) x64 = __dadd_rn(x64, term2_64(T, vw, i, w_inv));
-                    else if (c.unw) x64 = point_unw_64(vw, i, w_inv);
-                    else if (FAM == 3) x64 = point3_64(T, vw, i, w_inv);
-                    else x64 = point4_64(T, vw, i, w_inv);
+                    if (FAM == 1) L.x64 = __dadd_rn(L.x64, term1_64(vw, L.w_inv));
+                    else if (FAM == 2) L.x64 = __dadd_rn(L.x64, term2_64(T, vw, L.i, L.w_inv));
+                    else if (c.unw) L.x64 = point_unw_64(vw, L.i, L.w_inv);
+                    else if (FAM == 3) L.x64 = point3_64(T, vw, L.i, L.w_inv);
+                    else L.x64 = point4_64(T, vw, L.i, L.w_inv);
                     const double b64 = ld_volatile(&c.ts->bound64);
-                    beyond = x64 > b64;
-                    if (!beyond) won |= Offer<false>::run(c, k, x64, id);
-                    if (i == 1)
-                        y = (FAM == 1 || FAM == 2) ? (float)((b64 - x64) * (1.0 / w_inv))
-                                                   : __fdiv_rn(ld_volatile(&c.ts->bound32), winv32);
-                    if (i == 1) y *= (1.0f + 4.0f * kEta);
+                    beyond = L.x64 > b64;
+                    if (!beyond) won |= Offer<false>::run(c, k, L.x64, L.id);
+                    if (L.i == 1)
+                        y = (FAM == 1 || FAM == 2) ? (float)((b64 - L.x64) * (1.0 / L.w_inv))
+                                                   : __fdiv_rn(ld_volatile(&c.ts->bound32), L.winv32);
+                    if (L.i == 1) y *= (1.0f + 4.0f * kEta);
                 }
                 npts++;
                 if ((FAM == 1 || FAM == 2) && beyond) done = true;                 // uncorrelated: points increase
-                if (kPerm && i >= m) done = true;                                  // the sequence has m points
-                if (!done && i == 1) {
+                if (kPerm && L.i >= m) done = true;                                // the sequence has m points
+                if (!done && L.i == 1) {
                     // estimated number of further points below the bound
                     int est;
                     if (!(y < 1e9f)) est = 1 << 30;
@@ -732,26 +763,37 @@ __device__ bool process_survivors(Ctx<F32> &c, int n) {
                     else est = (int)((float)m * (1.0f - __expf(-T.lambda1_32 * y)) * 1.001f) + 1;
                     if (est >= kCap) to_deep = true;
                 }
-                if (!done && !to_deep && (int)i >= kCap) to_deep = true;            // outgrew the lane-sequential cap
-                i++;
+                if (!done && !to_deep && (int)L.i >= kCap) to_deep = true;            // outgrew the lane-sequential cap
+                L.i++;
             }
             if (to_deep) {
-                // at most one entry per taken survivor, so at < next: the slot was read already
+                // queued for deep mode; at < 32 + next: the slot is slack or was read already
                 const int at = atomicAdd(&ws->dq_n, 1);
-                if (at < kSurvCap) ws->sb_e[at] = e;
+                if (at < 32 + kSurvCap) ws->sb_e[at] = L.e;
                 done = true;
             }
-            if (done) has = false;
+            if (done) L.has = false;
         }
     }
-    if (npts) atomicAdd(&ws->cnt[F32 ? PMH_CNT_POINTS32 : PMH_CNT_POINTS64], (unsigned long long)npts);
+    {
+        uint32_t tot = npts;
+        for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(kFull, tot, o);
+        if (lane == 0 && tot) {
+            ws->cnt[F32 ? PMH_CNT_POINTS32 : PMH_CNT_POINTS64] += tot;
+            ws->cnt[PMH_CNT_SEQ_POINTS] += tot;
+            ws->cnt[PMH_CNT_SEQ_STEPS] += (unsigned long long)nsteps;
+        }
+    }
     __syncwarp();
-    // ---- deep mode for the long sequences
-    const int total_deep = min(ws->dq_n, kSurvCap);
-    if (total_deep) {
+    // ---- deep mode for the long sequences (ProbMinHash2/4: once no lane holds a write list)
+    const int total_deep = min(ws->dq_n, 32 + kSurvCap);
+    if (total_deep && (!kPerm || !__any_sync(kFull, L.has))) {
         const long long td = clock64();
         for (int j = 0; j < total_deep; ++j) deep<FAM, F32, false>(c, ws->sb_e[j], 0);
         count(c, PMH_CNT_CYC_DEEP, (unsigned long long)(clock64() - td));
+        __syncwarp();
+        if (lane == 0) ws->dq_n = 0;
+        __syncwarp();
     }
     count(c, PMH_CNT_CYC_SURV, (unsigned long long)(clock64() - t_sv));
     return __any_sync(kFull, won);
@@ -777,16 +819,16 @@ template <int FAM, bool F32, int TW>
 __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
     const SketchParams &P = *c.p;
     const int lane = threadIdx.x & 31;
-    const int tw = (int)(threadIdx.x >> 5) % TW;
     constexpr int team_warps = TW;
     TeamShared *ts = c.ts;
     WarpShared *ws = c.ws;
     const float te_lo = (FAM >= 3 && !c.unw) ? P.tab.te_lo : 1.0f;
-    if (lane == 0) ws->sb_n = 0;
+    if (lane == 0) { ws->sb_n = 0; ws->dq_n = 0; }
     __syncwarp();
     bool refreshed = false;
     int steps = 0;
-    (void)tw;
+    SeqLane<F32> L;
+    L.has = false;
     // claim size: 64 elements, or less for short ranges so that every warp of the
     // team gets a share of the survivors (about four claims per warp)
     const unsigned long long csz = TW == 1 ? 64ull
@@ -797,83 +839,97 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
         if (lane == 0) claim = TW == 1 ? ts->next : atomicAdd(&ts->next, csz);
         if (TW == 1 && lane == 0) ts->next = claim + csz;
         claim = __shfl_sync(kFull, claim, 0);
-        if (claim >= (unsigned long long)hi) break;
-        const uint32_t base = (uint32_t)claim;
-        const uint32_t end = (uint32_t)min((unsigned long long)hi, claim + csz);
-        if (c.gbound32 && (steps++ & 15) == 0) {
-            // grid mode: adopt the bound published by the other CTAs of this item
-            if (lane == 0) {
-                atomic_min_pos_float(&ts->bound32, __uint_as_float(ld_volatile((const int *)c.gbound32)));
-                if constexpr (!F32)
-                    atomic_min_pos_double(&ts->bound64, __longlong_as_double((long long)ld_volatile((const uint64_t *)c.gbound64)));
+        const bool fin = claim >= (unsigned long long)hi;   // the pass is over for this warp
+        int n = ws->sb_n;
+        if (!fin) {
+            const uint32_t base = (uint32_t)claim;
+            const uint32_t end = (uint32_t)min((unsigned long long)hi, claim + csz);
+            if (c.gbound32 && (steps++ & 15) == 0) {
+                // grid mode: adopt the bound published by the other CTAs of this item
+                if (lane == 0) {
+                    atomic_min_pos_float(&ts->bound32, __uint_as_float(ld_volatile((const int *)c.gbound32)));
+                    if constexpr (!F32)
+                        atomic_min_pos_double(&ts->bound64, __longlong_as_double((long long)ld_volatile((const uint64_t *)c.gbound64)));
+                }
+                __syncwarp();
             }
-            __syncwarp();
-        }
-        // L2 prefetch of this warp's step kPrefSteps ahead (ids and weights: up to
-        // five 128-byte lines each), so that its loads find L2 instead of HBM
-        {
-            const uint32_t pb = base + (uint32_t)(kPrefSteps * team_warps * 64);
-            const int pl = lane < 5 ? lane : lane - 5;
-            const uint32_t pe = pb + (uint32_t)min(pl * 16, 63);
-            if (lane < 10 && pe < hi) {
-                const void *a = lane < 5 ? (const void *)(P.ids + c.beg + pe) : (const void *)(P.weights + c.beg + pe);
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+            // L2 prefetch of this warp's step kPrefSteps ahead (ids and weights: up to
+            // five 128-byte lines each), so that its loads find L2 instead of HBM
+            {
+                const uint32_t pb = base + (uint32_t)(kPrefSteps * team_warps * 64);
+                const int pl = lane < 5 ? lane : lane - 5;
+                const uint32_t pe = pb + (uint32_t)min(pl * 16, 63);
+                if (lane < 10 && pe < hi) {
+                    const void *a = lane < 5 ? (const void *)(P.ids + c.beg + pe) : (const void *)(P.weights + c.beg + pe);
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+                }
             }
-        }
-        // filter two elements per lane: the log-free lower bound of the first point
-        bool surv[2];
-        uint64_t key[2];
-        uint32_t ev[2];
-        float winv[2];
-        bool valid[2];
+            // filter two elements per lane: the log-free lower bound of the first point.
+            // Weights and ids are loaded together (the id does not wait for the weight).
+            bool surv[2];
+            uint64_t key[2];
+            uint32_t ev[2];
+            float winv[2];
+            bool valid[2];
+            double wv[2];
+            uint64_t idv[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint32_t e = base + 32 * h + lane;
-            ev[h] = e;
-            surv[h] = false;
-            key[h] = 0;
-            winv[h] = 0.0f;
-            valid[h] = false;
-            if (e < end) {
-                const double w = P.weights[c.beg + e];
-                if (weight_positive(w)) {
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t e = base + 32 * h + lane;
+                wv[h] = 0.0;
+                idv[h] = 0;
+                if (e < end) {
+                    wv[h] = P.weights[c.beg + e];
+                    idv[h] = P.ids[c.beg + e];
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t e = base + 32 * h + lane;
+                ev[h] = e;
+                surv[h] = false;
+                key[h] = 0;
+                winv[h] = 0.0f;
+                valid[h] = false;
+                if (e < end && weight_positive(wv[h])) {
                     valid[h] = true;
-                    key[h] = mix64(P.ids[c.beg + e] ^ P.mixed_seed);
-                    winv[h] = winv_scaled(c.unw ? 1.0 : w, c.sigma);
+                    key[h] = mix64(idv[h] ^ P.mixed_seed);
+                    winv[h] = winv_scaled(c.unw ? 1.0 : wv[h], c.sigma);
                     const float xlo = winv[h] * unif_lo(value_word(key[h], 1)) * te_lo;
                     surv[h] = !(xlo * (1.0f - 8.0f * 0x1p-24f) > ld_volatile(&ts->bound32));
                 }
             }
-        }
-        int n = ws->sb_n;
-        unsigned nvalid = 0, nsurv = 0;
+            unsigned nvalid = 0, nsurv = 0;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const unsigned msk = __ballot_sync(kFull, surv[h]);
-            if (surv[h]) {
-                const int pos = n + __popc(msk & ((1u << lane) - 1u));
-                if (pos < kSurvCap) {   // always true: n <= kSurvBatch - 1 before the two appends of <= 32
-                    ws->sb_e[pos] = ev[h];
-                    ws->sb_key[pos] = key[h];
-                    ws->sb_winv[pos] = winv[h];
-                } else {
-                    ts->status = PMH_ERR_ITER_LIMIT;
+            for (int h = 0; h < 2; ++h) {
+                const unsigned msk = __ballot_sync(kFull, surv[h]);
+                if (surv[h]) {
+                    const int pos = n + __popc(msk & ((1u << lane) - 1u));
+                    if (pos < kSurvCap) {   // always true: n <= kSurvBatch - 1 before the two appends of <= 32
+                        ws->sb_e[32 + pos] = ev[h];
+                        ws->sb_key[pos] = key[h];
+                        ws->sb_winv[pos] = winv[h];
+                    } else {
+                        ts->status = PMH_ERR_ITER_LIMIT;
+                    }
                 }
+                n = min(n + __popc(msk), kSurvCap);
+                nsurv += __popc(msk);
+                nvalid += popc_ballot(valid[h]);
             }
-            n = min(n + __popc(msk), kSurvCap);
-            nsurv += __popc(msk);
-            nvalid += popc_ballot(valid[h]);
+            count(c, PMH_CNT_ELEMENTS, nvalid);
+            count(c, PMH_CNT_PREFILTERED, nvalid - nsurv);
+            __syncwarp();
         }
-        count(c, PMH_CNT_ELEMENTS, nvalid);
-        count(c, PMH_CNT_PREFILTERED, nvalid - nsurv);
-        __syncwarp();
+        // expand a full batch of survivors; at the end of the pass, whatever is left
         bool any_win = false;
-        if (n >= kSurvBatch) {
-            any_win = process_survivors<FAM, F32>(c, n);
+        if (fin ? (n > 0 || __any_sync(kFull, L.has)) : n >= kSurvBatch) {
+            any_win = process_survivors<FAM, F32>(c, L, n, fin);
             n = 0;
         }
         if (lane == 0) ws->sb_n = n;
         __syncwarp();
+        if (fin) break;
         // refresh q_max once everything is filled
         const int uf = __shfl_sync(kFull, lane == 0 ? ld_volatile(&ts->unfilled) : 1, 0);
         if (uf == 0 && (!refreshed || any_win)) {
@@ -884,11 +940,6 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
                 if constexpr (!F32) atomicMin(c.gbound64, (unsigned long long)__double_as_longlong(ld_volatile(&ts->bound64)));
             }
         }
-    }
-    {
-        const int rest = ws->sb_n;
-        __syncwarp();
-        if (rest > 0) process_survivors<FAM, F32>(c, rest);
     }
 }
 

@@ -23,7 +23,7 @@ FP64, FP32_RECHECK = 0, 1
 SHAPE_WARP, SHAPE_CTA8, SHAPE_QUAD, SHAPE_PAIR, SHAPE_QUAD8, SHAPE_QUAD8L = range(6)
 COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "rounds", "deep", "prefiltered",
             "cyc_pass0", "cyc_first", "cyc_deep", "cyc_refresh", "cyc_finish", "items", "cyc_surv", "cyc_item",
-            "cyc_warp", "cyc_barrier", "reserved18", "reserved19")
+            "cyc_warp", "cyc_barrier", "seq_steps", "seq_points")
 EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_sketch_batch_host",
            "pmh_last_host_span_ms", "pmh_sketch_batch_noalloc",
            "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_kernel_ms_history", "pmh_last_launches",
