@@ -89,7 +89,10 @@ struct pmh_handle_s {
     int last_chunks = 0;
     HostPipe hp;
     FamilyFork ff;               // family kernels side by side (pmh_sketch_batch)
-    bool concurrent_families = true;
+#ifndef PMH_FAMILY_FORK
+#define PMH_FAMILY_FORK 1
+#endif
+    bool concurrent_families = PMH_FAMILY_FORK;
     int force_shape[4] = {-1, -1, -1, -1};   // per family: TeamShape, or -1
     int last_shape[4] = {-1, -1, -1, -1};    // shapes of the most recent call (-1: family absent)
     bool autotune = true;

@@ -200,10 +200,10 @@ __device__ __forceinline__ void atomic_min_pos_float(float *addr, float v) {
 __device__ __forceinline__ void atomic_min_pos_double(double *addr, double v) {
     atomicMin((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
 }
-// Warp-uniform counter update (lane 0 adds).
+// Warp-uniform counter update (lane 0 adds; nothing when the call has no counters).
 template <bool F32>
 __device__ __forceinline__ void count(Ctx<F32> &c, int idx, unsigned long long v) {
-    if ((threadIdx.x & 31) == 0) c.ws->cnt[idx] += v;
+    if (c.p->counters && (threadIdx.x & 31) == 0) c.ws->cnt[idx] += v;
 }
 __device__ __forceinline__ unsigned popc_ballot(bool b) { return __popc(__ballot_sync(kFull, b)); }
 
@@ -390,7 +390,13 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
     const double w_inv = (EXACT || !F32) ? (c.unw ? 1.0 : __drcp_rn(w)) : 0.0;
     const float winv32 = winv_scaled(c.unw ? 1.0 : w, c.sigma);
     if (FAM == 2 || FAM == 4) {
-        for (uint32_t p = lane; p < m; p += 32) c.perm[p] = (uint16_t)p;
+        // identity permutation, eight 16-bit entries per 16-byte store (the region
+        // holds align16(2m) bytes, so the last store stays inside it)
+        uint4 *p4 = (uint4 *)c.perm;
+        for (uint32_t q = lane; q * 8 < m; q += 32) {
+            const uint32_t a = q * 8;
+            p4[q] = make_uint4(a | (a + 1) << 16, (a + 2) | (a + 3) << 16, (a + 4) | (a + 5) << 16, (a + 6) | (a + 7) << 16);
+        }
         __syncwarp();
     }
     if (!EXACT) count(c, PMH_CNT_DEEP, 1);
@@ -474,7 +480,7 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
                 }
                 x32 = __fmul_rn(winv32, sv);
             }
-            count(c, PMH_CNT_POINTS32, popc_ballot(act));
+            if (P.counters) count(c, PMH_CNT_POINTS32, popc_ballot(act));
             const bool beyond = x32 * (1.0f - kEta) > ld_volatile(&c.ts->bound32);
             bool wi = false;
             if (act && !beyond) wi = Offer<true>::run(c, k, x32, e);
@@ -499,7 +505,7 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
             } else {
                 x = act ? point4_64(T, vw, i, w_inv) : 0.0;
             }
-            count(c, PMH_CNT_POINTS64, popc_ballot(act));
+            if (P.counters) count(c, PMH_CNT_POINTS64, popc_ballot(act));
             const bool beyond = x > ld_volatile(&c.ts->bound64);
             bool wi = false;
             if (act && !beyond) wi = Offer<false>::run(c, k, x, id);
@@ -734,8 +740,9 @@ __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, 
                     beyond = x32 * (1.0f - kEta) > b32;
                     if (!beyond) won |= Offer<true>::run(c, k, x32, L.e);
                     if (L.i == 1) {
-                        y = __fdiv_rn(b32, L.winv32) * (1.0f + 4.0f * kEta);
-                        if (FAM == 1 || FAM == 2) y -= L.s32 * (1.0f - kEta);
+                        // bound * w (minus x_1 * w): only chooses the expansion mode, so approximate
+                        y = __fdividef(b32, L.winv32);
+                        if (FAM == 1 || FAM == 2) y -= L.s32;
                     }
                 } else {
                     if (FAM == 1) L.x64 = __dadd_rn(L.x64, term1_64(vw, L.w_inv));
@@ -758,7 +765,10 @@ __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, 
                     // estimated number of further points below the bound
                     int est;
                     if (!(y < 1e9f)) est = 1 << 30;
-                    else if (FAM == 1 || FAM == 2) { const float mu = fmaxf(y, 0.0f); est = (int)(mu + 3.0f * sqrtf(mu) + 2.0f); }
+                    else if (FAM == 1 || FAM == 2) {
+                        const float mu = fmaxf(y, 0.0f);
+                        est = (int)(mu + 3.0f * (mu > 0.0f ? mu * rsqrtf(mu) : 0.0f) + 2.0f);
+                    }
                     else if (FAM == 3 || c.unw) est = (int)y;
                     else est = (int)((float)m * (1.0f - __expf(-T.lambda1_32 * y)) * 1.001f) + 1;
                     if (est >= kCap) to_deep = true;
@@ -866,6 +876,7 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
             }
             // filter two elements per lane: the log-free lower bound of the first point.
             // Weights and ids are loaded together (the id does not wait for the weight).
+            const float b32 = ld_volatile(&ts->bound32);
             bool surv[2];
             uint64_t key[2];
             uint32_t ev[2];
@@ -896,7 +907,7 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
                     key[h] = mix64(idv[h] ^ P.mixed_seed);
                     winv[h] = winv_scaled(c.unw ? 1.0 : wv[h], c.sigma);
                     const float xlo = winv[h] * unif_lo(value_word(key[h], 1)) * te_lo;
-                    surv[h] = !(xlo * (1.0f - 8.0f * 0x1p-24f) > ld_volatile(&ts->bound32));
+                    surv[h] = !(xlo * (1.0f - 8.0f * 0x1p-24f) > b32);
                 }
             }
             unsigned nvalid = 0, nsurv = 0;
@@ -915,10 +926,12 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
                 }
                 n = min(n + __popc(msk), kSurvCap);
                 nsurv += __popc(msk);
-                nvalid += popc_ballot(valid[h]);
+                if (P.counters) nvalid += popc_ballot(valid[h]);
             }
-            count(c, PMH_CNT_ELEMENTS, nvalid);
-            count(c, PMH_CNT_PREFILTERED, nvalid - nsurv);
+            if (P.counters) {
+                count(c, PMH_CNT_ELEMENTS, nvalid);
+                count(c, PMH_CNT_PREFILTERED, nvalid - nsurv);
+            }
             __syncwarp();
         }
         // expand a full batch of survivors; at the end of the pass, whatever is left
