@@ -20,14 +20,15 @@
 //     kernel that runs once per set for all variants.
 //   * Filter: each lane takes two elements per step and rejects the first
 //     point without a logarithm (Exp(1) >= U, Exp(lambda;0,1) >=
-//     U(1-e^-lambda)/lambda).  Survivors are compacted and processed 32 at a
-//     time (first point, label, offer, continuation count); continuations are
-//     packed as segments of consecutive points into 32-lane rounds (segmented
-//     scan of the uncorrelated spacings, Eq. uncorrelated_recursion; the lazy
-//     Fisher-Yates permutation of Algorithm "Lazy generation of random
-//     permutation elements" resolved inside the round with match/shuffle).
-//     Sequences longer than one round are expanded 32 points at a time in
-//     deep mode.
+//     U(1-e^-lambda)/lambda).  Survivors are compacted into a per-warp buffer
+//     and expanded lane-sequentially with work stealing: each lane owns one
+//     element and computes one point of it per step (the uncorrelated running
+//     sum of Eq. uncorrelated_recursion term by term; the lazy Fisher-Yates
+//     permutation of Algorithm "Lazy generation of random permutation
+//     elements" through a per-lane write list).  Elements with long sequences
+//     are expanded warp-cooperatively instead (deep mode): 32 points per step,
+//     a warp scan of the spacings, and 32 Fisher-Yates steps resolved at once
+//     with match/shuffle.
 //   * q_max (Sec. Stop Limit Update) is a warp max-reduction over the shared
 //     signature, refreshed after updates, instead of the binary tree.
 //   * FP64 path: each component holds (q, id), updated with a 128-bit CAS
@@ -300,18 +301,27 @@ __device__ void refresh_bound(Ctx<F32> &c) {
 // (Algorithm "Lazy generation of random permutation elements", 0-based).
 // In-group dependencies: the value at position p before step t is the value
 // moved there by the latest earlier step u with r_u = p, else perm[p]; chains
-// of such moves are resolved by pointer jumping over lanes.
+// of such moves are resolved by pointer jumping over lanes.  A step never
+// targets the position of an earlier step (r_u >= u), so the latest earlier
+// writer of position t0 + j is the highest lane below j among the lanes that
+// target it.
 __device__ __forceinline__ uint32_t fy_group(uint16_t *perm, int *slot, uint32_t m, uint32_t t0, uint64_t lw, bool act) {
     const int lane = threadIdx.x & 31;
     const uint32_t t = t0 + lane;
     const uint32_t r = act ? t + uniform_int(lw, m - t) : 0xFFFFFFFFu;
+    const uint32_t same = __match_any_sync(kFull, r);   // lanes with the same target
     slot[lane] = -1;
     __syncwarp();
-    if (act && r != t && r - t0 < 32u) atomicMax(&slot[r - t0], lane);
+    const uint32_t j = r - t0;                           // target inside the group: j in (lane, 32)
+    if (act && j < 32u && j != (uint32_t)lane) {
+        const uint32_t below = same & ((1u << j) - 1u);
+        if (lane == 31 - __clz(below)) slot[j] = lane;
+    }
     __syncwarp();
-    int ptr = slot[lane];
+    int ptr = act ? slot[lane] : -1;
     uint32_t val = (act && ptr < 0) ? (uint32_t)perm[t] : 0u;
-    for (int it = 0; it < 5; ++it) {
+    // chains are short: most groups need no jump at all
+    for (int it = 0; it < 5 && __any_sync(kFull, ptr >= 0); ++it) {
         int src = ptr >= 0 ? ptr : lane;
         uint32_t v2 = __shfl_sync(kFull, val, src);
         int p2 = __shfl_sync(kFull, ptr, src);
@@ -320,7 +330,6 @@ __device__ __forceinline__ uint32_t fy_group(uint16_t *perm, int *slot, uint32_t
         }
     }
     const uint32_t moved = val;   // value at position t just before step t
-    const uint32_t same = __match_any_sync(kFull, r);
     const uint32_t earlier = same & ((1u << lane) - 1u);
     const int w2 = earlier ? 31 - __clz(earlier) : -1;
     const uint32_t from_lane = __shfl_sync(kFull, moved, w2 >= 0 ? w2 : lane);
@@ -331,38 +340,6 @@ __device__ __forceinline__ uint32_t fy_group(uint16_t *perm, int *slot, uint32_t
     if (act && later == 0 && r >= t0 + 32) perm[r] = (uint16_t)moved;
     __syncwarp();
     return label;
-}
-
-// Segmented Fisher-Yates inside one round: lanes [a, a+len) hold steps
-// 0..len-1 of one element whose permutation is still the identity (the
-// segment starts at step 0).  Returns each lane's label; the dependency rules
-// are those of fy_group.
-__device__ __forceinline__ uint32_t fy_segment(int *slot, uint32_t m, int a, int len, int t, uint64_t lw, bool act) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t r = act ? (uint32_t)t + uniform_int(lw, m - (uint32_t)t) : 0xFFFFFFFFu;
-    slot[lane] = -1;
-    __syncwarp();
-    // a write to position p < len of this element lands in lane a + p (the lane of step p);
-    // positions >= len belong to no step of the segment and are read only as labels
-    if (act && r != (uint32_t)t && r < (uint32_t)len) atomicMax(&slot[a + (int)r], lane);
-    __syncwarp();
-    int ptr = act ? slot[lane] : -1;
-    uint32_t val = (act && ptr < 0) ? (uint32_t)t : 0u;     // identity: P[t] = t
-    for (int it = 0; it < 5; ++it) {
-        int src = ptr >= 0 ? ptr : lane;
-        uint32_t v2 = __shfl_sync(kFull, val, src);
-        int p2 = __shfl_sync(kFull, ptr, src);
-        if (ptr >= 0) {
-            if (p2 < 0) { val = v2; ptr = -1; } else ptr = p2;
-        }
-    }
-    const uint32_t key = act ? (((uint32_t)a << 16) | r) : 0xFFFFFFFFu;
-    const uint32_t same = __match_any_sync(kFull, key);
-    const uint32_t earlier = same & ((1u << lane) - 1u);
-    const int w2 = (act && earlier) ? 31 - __clz(earlier) : -1;
-    const uint32_t from_lane = __shfl_sync(kFull, val, w2 >= 0 ? w2 : lane);
-    __syncwarp();
-    return (w2 >= 0) ? from_lane : r;   // identity: P[r] = r
 }
 
 __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
@@ -606,6 +583,9 @@ __device__ __forceinline__ uint32_t resolve_contenders(Ctx<true> &c) {
 #ifndef PMH_SEQ_KEEP
 #define PMH_SEQ_KEEP 8
 #endif
+#ifndef PMH_EST_SIGMAS
+#define PMH_EST_SIGMAS 0.0f     // ProbMinHash1/2: deep mode when mean + this many sd of the point count (+2) reach the cap
+#endif
 #ifndef PMH_SEQ_KEEP_FAMS
 #define PMH_SEQ_KEEP_FAMS 3     // families whose busy lanes carry over (bit f-1: ProbMinHash f); the measured best on c2
 #endif
@@ -707,14 +687,13 @@ __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, 
                     const uint32_t t = L.i - 1;
                     const uint32_t r = t + uniform_int(lw, m - t);
                     uint32_t moved = t, lab = r;   // untouched positions hold their own index
-                    // the latest write wins: scanning backwards, keep the first match
+                    // the latest write wins: one backward scan, keeping the first match of each
+                    bool ft = false, fr = false;
                     for (int j = L.fyn - 1; j >= 0; --j) {
                         const uint32_t ent = c.fy[j * 32 + lane];
-                        if ((ent >> 16) == t) { moved = ent & 0xFFFFu; break; }
-                    }
-                    for (int j = L.fyn - 1; j >= 0; --j) {
-                        const uint32_t ent = c.fy[j * 32 + lane];
-                        if ((ent >> 16) == r) { lab = ent & 0xFFFFu; break; }
+                        const uint32_t pos = ent >> 16;
+                        if (!ft && pos == t) { moved = ent & 0xFFFFu; ft = true; }
+                        if (!fr && pos == r) { lab = ent & 0xFFFFu; fr = true; }
                     }
                     if (L.fyn < kFyCap) c.fy[L.fyn * 32 + lane] = (r << 16) | moved;
                     L.fyn++;
@@ -767,7 +746,7 @@ __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, 
                     if (!(y < 1e9f)) est = 1 << 30;
                     else if (FAM == 1 || FAM == 2) {
                         const float mu = fmaxf(y, 0.0f);
-                        est = (int)(mu + 3.0f * (mu > 0.0f ? mu * rsqrtf(mu) : 0.0f) + 2.0f);
+                        est = (int)(mu + PMH_EST_SIGMAS * (mu > 0.0f ? mu * rsqrtf(mu) : 0.0f) + 2.0f);
                     }
                     else if (FAM == 3 || c.unw) est = (int)y;
                     else est = (int)((float)m * (1.0f - __expf(-T.lambda1_32 * y)) * 1.001f) + 1;
