@@ -572,7 +572,7 @@ __device__ __forceinline__ uint32_t resolve_contenders(Ctx<true> &c) {
 // bound holds for at most kSeqCap terms, the write list has kFyCap entries).
 // Tuning constants (compile-time; the defaults are the measured best on c2).
 #ifndef PMH_PREF_STEPS
-#define PMH_PREF_STEPS 4
+#define PMH_PREF_STEPS 0     // off: measured 1 % faster on c2 once the kernels became issue-bound
 #endif
 #ifndef PMH_SEQ_CAP
 #define PMH_SEQ_CAP 32
@@ -589,7 +589,7 @@ __device__ __forceinline__ uint32_t resolve_contenders(Ctx<true> &c) {
 #ifndef PMH_SEQ_KEEP_FAMS
 #define PMH_SEQ_KEEP_FAMS 3     // families whose busy lanes carry over (bit f-1: ProbMinHash f); the measured best on c2
 #endif
-constexpr int kPrefSteps = PMH_PREF_STEPS;  // filter: L2 prefetch distance in 64-element steps of a warp
+constexpr int kPrefSteps = PMH_PREF_STEPS;  // filter: L2 prefetch distance in 64-element steps of a warp (0: none)
 constexpr int kSeqKeep = PMH_SEQ_KEEP;      // idle lanes at which a dry buffer hands the rest to the next call (0: never)
 static_assert(kSeqKeep >= 0 && kSeqKeep <= 32, "a count of lanes");
 constexpr int kSeqCap = PMH_SEQ_CAP;        // lane-sequential points (ProbMinHash1)
@@ -844,7 +844,7 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
             }
             // L2 prefetch of this warp's step kPrefSteps ahead (ids and weights: up to
             // five 128-byte lines each), so that its loads find L2 instead of HBM
-            {
+            if (kPrefSteps > 0) {
                 const uint32_t pb = base + (uint32_t)(kPrefSteps * team_warps * 64);
                 const int pl = lane < 5 ? lane : lane - 5;
                 const uint32_t pe = pb + (uint32_t)min(pl * 16, 63);
