@@ -52,9 +52,9 @@ OPS_PAIR_COMPONENT = 3  # equal-component count: two 32-bit compares and one add
 # shift + or (6) and and-not + popcount (2), two adds (2)
 OPS_BBIT_WORD = 2 + 2 * (6 + 2) + 2
 # DRAM bytes (read + write) of the four family sketch kernels per element-variant, from the ncu
-# capture summarised in profiles/sketch_kernel_pair_c2_2000sets_full.md (same kernel source); the
+# capture summarised in profiles/sketch_kernel_c2_2000sets_full.md (same kernel source); the
 # traffic grows in proportion to the elements (one pass over ids and weights per family).
-TRAFFIC_BYTES_PER_ELEMENT_VARIANT = 13.60
+TRAFFIC_BYTES_PER_ELEMENT_VARIANT = 13.89
 
 
 def parse():
@@ -68,8 +68,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="wall budget of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--team-shape", type=int, default=-1,
-                    help="pin the sketch kernels' team shape (0 warp, 1 cta8, 2 quad, 3 pair, 4 quad8, 5 quad8l); "
+    ap.add_argument("--team-shape", type=str, default="-1",
+                    help="pin the sketch kernels' team shape (0 warp, 1 cta8, 2 quad, 3 pair, 4 quad8, 5 quad8l), "
+                         "one value for every family or four comma-separated values for ProbMinHash1..4; "
                          "-1 = autotuned")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the per-kernel measurements beside the headline (huge set, all-pairs counts)")
@@ -360,8 +361,12 @@ def main():
     st32 = torch.empty((len(VARIANTS), S), dtype=torch.int32, device=dev)
     st64 = torch.empty_like(st32)
     h = pmh.Handle(local)
-    if args.team_shape >= 0:
-        h.set_team_shape(0, args.team_shape)
+    shapes_pinned = [int(x) for x in args.team_shape.split(",")]
+    if len(shapes_pinned) == 1 and shapes_pinned[0] >= 0:
+        h.set_team_shape(0, shapes_pinned[0])
+    elif len(shapes_pinned) == 4:
+        for f, sh in enumerate(shapes_pinned):
+            h.set_team_shape(f + 1, sh)
     stream = torch.cuda.current_stream()
 
     def step(prec, out, st):
