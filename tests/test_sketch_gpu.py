@@ -184,3 +184,21 @@ def test_autotune_picks_a_shape_and_keeps_results(H):
     z3, q3, _ = run(H, b, ["1", "2", "3a", "4"], 1, seed=1)      # default rule
     assert np.array_equal(z1, z3) and np.array_equal(q1, q3)
     H.set_autotune(1)
+
+
+@pytest.mark.parametrize("shape", [0, 3, 4], ids=["warp", "pair", "quad8"])
+def test_carried_lanes_heavy_tailed_weights(H, shape):
+    # Large sets with Pareto weights: most survivors end after a point or two while a few heavy
+    # elements run long, so ProbMinHash1/2 warps hand busy lanes over to the next survivor batch
+    # (and ProbMinHash2 defers its deep queue until no lane holds a write list).  Nothing of that
+    # may change a signature.
+    b = W.random_batch(920 + shape, [20000, 3, 45000, 700, 12000], 512, "pareto")
+    H.set_team_shape(0, shape)
+    try:
+        for precision in (0, 1):
+            z, q, st = run(H, b, ["1", "2", "1a"], precision, with_q=True, seed=17)
+            assert (st == 0).all()
+            for vi, v in enumerate(["1", "2", "1a"]):
+                check_sets(b, v, z[vi], q[vi], range(b.num_sets), seed=17)
+    finally:
+        H.set_team_shape(0, -1)
