@@ -158,7 +158,7 @@ pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const double *wei
  * weights, offsets and the outputs in host memory.
  *
  * The call splits the sets into `chunks` contiguous ranges by work (the first
- * range gets half the share of the others; chunks <= 0: automatic, 2 for
+ * range gets half the share of the others; chunks <= 0: automatic, 3 for
  * batches of 2^22 elements or more, else 1) and pipelines them on internal
  * streams: host->device copy of a range's elements; the sketch of the range,
  * alternating between two compute streams so that one range's kernels fill
