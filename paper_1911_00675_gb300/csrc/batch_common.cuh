@@ -336,6 +336,15 @@ inline cudaError_t plan_batch(int sm_count, int precision, uint32_t m, const int
                 if (cta_s.blocks_per_sm > 0) shape = cta_s;
             }
         }
+        if (shape.blocks_per_sm <= 0) {
+            // large m: the shape with the most resident warps among those that fit at all
+            for (int k = 0; k < kNumShapes; k++) {
+                LaunchShape t{};
+                e = sketch_shape_any(f32, f, k, m, &t);
+                if (e != cudaSuccess) return e;
+                if (t.blocks_per_sm * (t.block / 32) > shape.blocks_per_sm * (shape.block / 32)) shape = t;
+            }
+        }
         if (shape.blocks_per_sm <= 0) { *fits = false; return cudaSuccess; }
         int grid = sm_count * shape.blocks_per_sm;
         const int teams_per_block = shape.block / 32 / shape.team_warps;

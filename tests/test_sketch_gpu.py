@@ -202,3 +202,21 @@ def test_carried_lanes_heavy_tailed_weights(H, shape):
                 check_sets(b, v, z[vi], q[vi], range(b.num_sets), seed=17)
     finally:
         H.set_team_shape(0, -1)
+
+
+@pytest.mark.parametrize("autotune", [1, 0], ids=["tuned", "default-rule"])
+def test_largest_m(H, autotune):
+    # m = PMH_MAX_M = 8192: one FP64 signature is 128 KiB of shared memory, so only the shapes
+    # with one team per block fit; every variant must still run and match the oracle
+    from paper_1911_00675_gb300 import pmh
+    b = W.random_batch(8192, [1, 40, 900, 3000], 8192, "lognormal")
+    H.set_autotune(autotune)
+    try:
+        z64, q64, st64 = run(H, b, VARS, 0, with_q=True, seed=21)
+        z32, q32, st32 = run(H, b, VARS, 1, with_q=True, seed=21)
+    finally:
+        H.set_autotune(1)
+    assert (st64 == 0).all() and (st32 == 0).all()
+    assert np.array_equal(z64, z32) and np.array_equal(q64, q32)
+    for vi, v in enumerate(VARS):
+        check_sets(b, v, z64[vi], q64[vi], range(b.num_sets), seed=21)
