@@ -200,6 +200,18 @@ __device__ __forceinline__ float unif_lo(uint64_t w) {
 // reciprocal).  Weights too small for the float range give 2^100: every point
 // of such an element is then far beyond any bound (E >= 2^-53 unless E = 0,
 // and E = 0 gives x = 0 exactly in both precisions).
+// The float whose reciprocal winv_scaled takes: w * 2^-sigma with the mantissa
+// truncated to 23 bits (exponent clamped at 254), or 0 when it is below the
+// normal float range.  winv_from_ws(ws_scaled(w, s)) == winv_scaled(w, s).
+__device__ __forceinline__ float ws_scaled(double w, int sigma) {
+    uint64_t b = (uint64_t)__double_as_longlong(w);
+    int e = (int)((b >> 52) & 0x7FF);
+    int ef = e - 1023 - sigma + 127;
+    if (e == 0 || ef <= 0) return 0.0f;
+    if (ef >= 254) ef = 254;
+    return __uint_as_float(((uint32_t)ef << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
+}
+__device__ __forceinline__ float winv_from_ws(float ws) { return ws == 0.0f ? 0x1p100f : __frcp_rn(ws); }
 __device__ __forceinline__ float winv_scaled(double w, int sigma) {
     uint64_t b = (uint64_t)__double_as_longlong(w);
     int e = (int)((b >> 52) & 0x7FF);

@@ -583,6 +583,9 @@ __device__ __forceinline__ uint32_t resolve_contenders(Ctx<true> &c) {
 #ifndef PMH_SEQ_KEEP
 #define PMH_SEQ_KEEP 8
 #endif
+#ifndef PMH_FILTER_WS
+#define PMH_FILTER_WS 1         // filter compares U against bound * w (no reciprocal for rejected elements)
+#endif
 #ifndef PMH_EST_SIGMAS
 #define PMH_EST_SIGMAS 0.0f     // ProbMinHash1/2: deep mode when mean + this many sd of the point count (+2) reach the cap
 #endif
@@ -633,6 +636,11 @@ __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, 
     int next = 0;
     uint32_t npts = 0;
     int nsteps = 0;
+#if PMH_FILTER_WS
+    // the filter buffered w * 2^-sigma: the scaled reciprocal weight of every new survivor
+    for (int j = lane; j < n; j += 32) ws->sb_winv[j] = winv_from_ws(ws->sb_winv[j]);
+    __syncwarp();
+#endif
 #pragma unroll 1
     for (;; ++nsteps) {
         // idle lanes take the next survivors
@@ -884,9 +892,19 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
                 if (e < end && weight_positive(wv[h])) {
                     valid[h] = true;
                     key[h] = mix64(idv[h] ^ P.mixed_seed);
+#if PMH_FILTER_WS
+                    // w * 2^-sigma instead of its reciprocal: U te_lo > bound w rejects, and the
+                    // reciprocal is taken only for the buffered survivors (process_survivors).
+                    // Conservative: the products' roundings and the truncated mantissa are
+                    // within the 16-ulp slack.
+                    winv[h] = ws_scaled(c.unw ? 1.0 : wv[h], c.sigma);
+                    const float ulo = __fmul_rn(unif_lo(value_word(key[h], 1)), te_lo);
+                    surv[h] = !(__fmul_rn(ulo, 1.0f - 16.0f * 0x1p-24f) > __fmul_rn(b32, winv[h]));
+#else
                     winv[h] = winv_scaled(c.unw ? 1.0 : wv[h], c.sigma);
                     const float xlo = winv[h] * unif_lo(value_word(key[h], 1)) * te_lo;
                     surv[h] = !(xlo * (1.0f - 8.0f * 0x1p-24f) > b32);
+#endif
                 }
             }
             unsigned nvalid = 0, nsurv = 0;
