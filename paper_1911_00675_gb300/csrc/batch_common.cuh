@@ -82,7 +82,7 @@ inline uint64_t host_mix64(uint64_t z) {
 // starts, [512, 516) per-family head counters of the persistent kernels.
 // [516] counts the sets whose statistics are split over all blocks; [520, ...)
 // lists them (u64 set indices, kBigCap of them).
-constexpr int kQHist = 0, kQStart = 256, kQHead = 512, kQBigCount = 516, kQBigList = 520;
+constexpr int kQHist = 0, kQStart = 256, kQHead = 512, kQBigCount = 516, kQStatNext = 518, kQBigList = 520;
 constexpr int kBigCap = 1024;
 constexpr int kQMetaWords = kQBigList + 2 * kBigCap;
 constexpr int kQMetaClearWords = kQBigList;     // words cleared per call
@@ -176,36 +176,49 @@ struct StatPart {
     unsigned int np = 0;
     int bad = 0;
 };
+__device__ __forceinline__ void stat_one(StatPart &r, uint64_t x) {
+    const int ex = (int)(x >> 52) & 0x7FF;
+    const bool neg = (x >> 63) != 0;
+    const bool zero = (x << 1) == 0;
+    if (ex == 0x7FF || (neg && !zero)) { r.bad = 1; return; }
+    if (zero) return;
+    if (ex == 0) {   // subnormal: counted, adds nothing to the sum; bad if 1/w overflows
+        if (isinf(__drcp_rn(__longlong_as_double((long long)x)))) r.bad = 1;
+        else r.np++;
+        return;
+    }
+    scaled_add(r.sum, x);
+    r.np++;
+}
 __device__ __forceinline__ StatPart block_stats(const unsigned long long *wb, int64_t b, int64_t e) {
     __shared__ float sacc[8];
     __shared__ int sme[8], sbad[8];
     __shared__ unsigned int snp[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     StatPart r;
-    for (int64_t i0 = b + threadIdx.x; i0 < e; i0 += 4 * (int64_t)blockDim.x) {
-        uint64_t bits[4];
+    // 16-byte loads of two weights each: a first weight off the 16-byte grid and a last odd one
+    // are read alone (a zero pair, used as padding, counts as two skipped weights)
+    int64_t a = b;
+    if (a < e && ((uintptr_t)(wb + a) & 15u) != 0) {
+        if (threadIdx.x == 0) stat_one(r, __ldcs(wb + a));
+        a++;
+    }
+    const int64_t np2 = (e - a) / 2;
+    const ulonglong2 *w2 = (const ulonglong2 *)(wb + a);
+    for (int64_t p0 = threadIdx.x; p0 < np2; p0 += 4 * (int64_t)blockDim.x) {
+        ulonglong2 v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int64_t i = i0 + (int64_t)u * blockDim.x;
-            bits[u] = i < e ? (uint64_t)__ldcs(wb + i) : 0ull;
+            const int64_t p = p0 + (int64_t)u * blockDim.x;
+            v[u] = p < np2 ? __ldcs(w2 + p) : make_ulonglong2(0ull, 0ull);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const uint64_t x = bits[u];
-            const int ex = (int)(x >> 52) & 0x7FF;
-            const bool neg = (x >> 63) != 0;
-            const bool zero = (x << 1) == 0;
-            if (ex == 0x7FF || (neg && !zero)) { r.bad = 1; continue; }
-            if (zero) continue;
-            if (ex == 0) {   // subnormal: counted, adds nothing to the sum; bad if 1/w overflows
-                if (isinf(__drcp_rn(__longlong_as_double((long long)x)))) r.bad = 1;
-                else r.np++;
-                continue;
-            }
-            scaled_add(r.sum, x);
-            r.np++;
+            stat_one(r, v[u].x);
+            stat_one(r, v[u].y);
         }
     }
+    if (a + 2 * np2 < e && threadIdx.x == 0) stat_one(r, __ldcs(wb + e - 1));
     for (int o = 16; o; o >>= 1) {
         const int me2 = __shfl_xor_sync(0xFFFFFFFFu, r.sum.me, o);
         const float acc2 = __shfl_xor_sync(0xFFFFFFFFu, r.sum.acc, o);
@@ -227,14 +240,20 @@ __device__ __forceinline__ double scaled_value(const ScaledSum &s) {
     return s.me < 0 ? 0.0 : ldexp((double)s.acc, s.me - 1023);
 }
 
-// Pass 1: one block per set, grid-stride over sets.  A set longer than
-// kStatBig is listed (up to kBigCap of them) and only its first chunk is
-// summed here; pass 2 adds the rest with all blocks.
+// Pass 1: one block per set, the blocks taking sets from a shared counter (set
+// sizes vary by orders of magnitude, so a fixed deal leaves blocks idle).  A
+// set longer than kStatBig is listed (up to kBigCap of them) and only its
+// first chunk is summed here; pass 2 adds the rest with all blocks.
 static __global__ void __launch_bounds__(256) set_stats_kernel(const int64_t *off, const double *w, int64_t num_sets,
                                                                SetStat *out, unsigned int *meta) {
     __shared__ int s_listed;
+    __shared__ long long s_next;
     const unsigned long long *wb = (const unsigned long long *)w;
-    for (int64_t s = blockIdx.x; s < num_sets; s += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) s_next = (long long)atomicAdd((unsigned long long *)(meta + kQStatNext), 1ull);
+        __syncthreads();
+        const int64_t s = s_next;
+        if (s >= num_sets) break;
         const int64_t b = off[s], e = off[s + 1];
         int64_t end = e;
         if (threadIdx.x == 0) {

@@ -220,3 +220,25 @@ def test_largest_m(H, autotune):
     assert np.array_equal(z64, z32) and np.array_equal(q64, q32)
     for vi, v in enumerate(VARS):
         check_sets(b, v, z64[vi], q64[vi], range(b.num_sets), seed=21)
+
+
+def test_inputs_off_the_16_byte_grid(H):
+    # ids and weights one element into a larger allocation: 8-byte but not 16-byte aligned (the
+    # statistics read weights two at a time on the 16-byte grid and must handle both edges)
+    from paper_1911_00675_gb300 import pmh
+    b = W.random_batch(4242, [1, 2, 3, 600, 70001, 0, 5], 128, "exp")
+    ids, w, off = to_dev(b)
+    ids_u = torch.empty(ids.numel() + 1, dtype=ids.dtype, device=ids.device)[1:]
+    w_u = torch.empty(w.numel() + 1, dtype=w.dtype, device=w.device)[1:]
+    ids_u.copy_(ids)
+    w_u.copy_(w)
+    assert w_u.data_ptr() % 16 == 8
+    for prec in (0, 1):
+        za, qa, sa = H.sketch_batch(ids, w, off, b.m, VARS, prec, 4, with_q=True)
+        zb, qb, sb = H.sketch_batch(ids_u, w_u, off, b.m, VARS, prec, 4, with_q=True)
+        torch.cuda.synchronize()
+        assert torch.equal(za, zb) and torch.equal(qa, qb) and torch.equal(sa, sb)
+        assert int(sa.abs().sum()) == 0
+    z, q, st = run(H, b, VARS, 1, with_q=True, seed=4)
+    for vi, v in enumerate(VARS):
+        check_sets(b, v, z[vi], q[vi], range(b.num_sets), seed=4)
