@@ -251,12 +251,13 @@ pmh_status pmh_kernel_ms_history(pmh_handle h, int32_t max_calls, float *queue_m
  * pmh_set_team_shape(h, family, shape): family 1..4 (ProbMinHash1/1a, 2,
  * 3/3a, 4) or 0 for all; shape one of the above, or -1 to let the handle
  * choose.  A shape whose shared memory does not fit falls back to the default
- * rule (warp teams when 12 warps per SM fit, else CTA8).
+ * rule (teams of 2 warps when 16 warps per SM fit, else warp teams, else CTA8;
+ * else the shape with the most resident warps that fits).
  *
  * pmh_set_autotune(h, enable): with enable = 1 (the default), the first
  * pmh_sketch_batch for a new (m, precision, family, log2 of the item count)
- * runs the batch once per shape on the caller's stream, waits for it, and keeps
- * the fastest shape per family for later calls; not during stream capture
+ * runs the batch twice per shape on the caller's stream, waits for it, and
+ * keeps the shape with the fastest trial per family for later calls; not during stream capture
  * (the default rule applies there).  enable = 0 uses the default rule;
  * enable = -1 also forgets the shapes chosen so far and keeps tuning on.
  *

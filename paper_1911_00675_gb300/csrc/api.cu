@@ -369,7 +369,10 @@ static pmh_status autotune_shapes(pmh_handle h, Workspace &w, SketchParams p, ui
         for (int i = 0; i < 7; i++) CUDA_TRY(h, cudaEventCreate(&h->tev[i]));
     float best[4] = {1e30f, 1e30f, 1e30f, 1e30f};
     int best_kind[4] = {-1, -1, -1, -1};
-    for (int cand = 0; cand < kNumShapes; cand++) {
+    // two passes over the shapes, keeping each one's faster trial: a first launch of a kernel
+    // (module loading, cold caches) would otherwise decide between shapes within a few percent
+    for (int trial = 0; trial < 2 * kNumShapes; trial++) {
+        const int cand = trial % kNumShapes;
         int ck[4];
         for (int f = 0; f < 4; f++) ck[f] = kinds[f] >= 0 ? kinds[f] : cand;
         Plan plan;
