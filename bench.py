@@ -39,13 +39,14 @@ VARIANTS = ["1", "1a", "2", "3", "3a", "4"]
 # xor-shift-multiply rounds + 1 xor-shift + the counter add = 20 32-bit ops.
 # SplitMix64 word: three 64-bit xor-shifts (4 each), two 64-bit multiplies by a constant (3 each) and the
 # 64-bit counter add (2) = 20.
-OPS_ELEMENT = 60        # every element-variant: key = mix(id ^ mix(seed)) (22), weight check (2), scaled 1/w
-                        # from the exponent and mantissa with one reciprocal (10), value word of point 1 (20),
-                        # 23-bit uniform lower bound (3), bound product and compare (3)
+OPS_ELEMENT = 55        # every element-variant: key = mix(id ^ mix(seed)) (22), weight check (2), scaled w
+                        # from the exponent and mantissa (5), value word of point 1 (20), 23-bit uniform
+                        # lower bound (3), the products bound * w and U * (1 - e^-lambda)/lambda and compare (3)
 OPS_POINT = 70          # every generated point: value word (20), label word (20), label from the word (3;
                         # the lazy permutation's bookkeeping is not counted), logarithm (20), point value and
                         # stop compare (4), offer to the component (3)
-OPS_POINT1_SHARED = 20  # the value word of a survivor's point 1 was counted with its element
+OPS_SURVIVOR = -10      # per survivor: its point-1 value word was counted with its element (-20), and its
+                        # scaled 1/w is one reciprocal (+10)
 LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes issue one instruction per clock
 OPS_PAIR_COMPONENT = 3  # equal-component count: two 32-bit compares and one add per component pair
 # 8-bit codes, per pair of 64-bit words (8 fields): xor (2), per 32-bit half three fold steps of
@@ -479,7 +480,7 @@ def main():
     sm_mhz = clk["sm_mhz"] if clk else 2070.0
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     survivors = c["elements"] - c["prefiltered"]
-    per_launch_ops = c["elements"] * OPS_ELEMENT + c["points32"] * OPS_POINT - survivors * OPS_POINT1_SHARED
+    per_launch_ops = c["elements"] * OPS_ELEMENT + c["points32"] * OPS_POINT + survivors * OPS_SURVIVOR
     achieved = per_launch_ops / (k_avg * 1e-3) / 1e12
     peak = n_sms * LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (32-bit lane ops)",
