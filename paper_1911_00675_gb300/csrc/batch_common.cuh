@@ -15,8 +15,11 @@ namespace pmh {
 
 // ------------------------------------------------------------------ tables
 // Per-m constants of Sec. ProbMinHash2/3/4 in FP64 (host libm), plus FP32
-// copies for the filter: five FP64 arrays then five FP32 arrays of m+1 entries.
-inline size_t table_bytes(uint32_t m) { return 5 * ((size_t)m + 1) * (sizeof(double) + sizeof(float)); }
+// copies for the filter: five FP64 arrays then five FP32 arrays of m+1 entries,
+// then (16-byte aligned) the ProbMinHash4 FP32 constants of each point packed
+// in one float4.
+constexpr size_t table_f4_off(uint32_t m) { return ((5 * ((size_t)m + 1) * (sizeof(double) + sizeof(float))) + 15) & ~(size_t)15; }
+constexpr size_t table_bytes(uint32_t m) { return table_f4_off(m) + ((size_t)m + 1) * 16; }
 
 // Fills `host` (table_bytes(m) bytes) and sets `out` to point into the same
 // layout at device address `dev`.
@@ -41,6 +44,19 @@ inline void build_tables(uint32_t m, unsigned char *host, const void *dev, Table
     }
     float *f = (float *)(host + 5 * n * sizeof(double));
     for (size_t i = 0; i < 5 * n; i++) f[i] = (float)beta[i];
+    {
+        const float *g32 = f + n, *dg32 = f + 2 * n, *c432 = f + 3 * n, *i432 = f + 4 * n;
+        float *q = (float *)(host + table_f4_off(m));
+        for (size_t i = 0; i < 4 * n; i++) q[i] = 0.0f;
+        for (uint32_t i = 1; i <= m; i++) {
+            q[4 * i + 0] = g32[i - 1];
+            if (i < m) {
+                q[4 * i + 1] = dg32[i];
+                q[4 * i + 2] = c432[i];
+                q[4 * i + 3] = i432[i];
+            }
+        }
+    }
     const char *d = (const char *)dev;
     Tables &t = *out;
     t.m = m;
@@ -55,6 +71,7 @@ inline void build_tables(uint32_t m, unsigned char *host, const void *dev, Table
     t.dgamma32 = (const float *)(fb + 2 * n * sizeof(float));
     t.c4_32 = (const float *)(fb + 3 * n * sizeof(float));
     t.inv4_32 = (const float *)(fb + 4 * n * sizeof(float));
+    t.p4 = (const float4 *)(d + table_f4_off(m));
     t.c3 = c3;
     t.inv3 = inv3;
     t.delta = delta;

@@ -18,7 +18,8 @@ using namespace pmh;
 namespace {
 
 // Scratch layout: tables for m <= PMH_MAX_M | queue metadata | work queue | per-set statistics.
-constexpr size_t kTableRegion = 512u * 1024u;                                  // >= table_bytes(PMH_MAX_M)
+constexpr size_t kTableRegion = 640u * 1024u;                                  // >= table_bytes(PMH_MAX_M)
+static_assert(kTableRegion >= table_bytes(PMH_MAX_M), "table region too small");
 constexpr size_t kMetaRegion = 16384;                                           // >= kQMetaWords * 4
 constexpr size_t kQueueRegion = (size_t)PMH_NOALLOC_MAX_ITEMS * sizeof(uint64_t);
 constexpr size_t kStatsRegion = (size_t)PMH_NOALLOC_MAX_SETS * 16;

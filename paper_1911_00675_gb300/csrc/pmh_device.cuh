@@ -54,6 +54,7 @@ struct Tables {
     const double *c4;       // expm1(-lambda_i), lambda_i = log1p(1/(m-i))
     const double *inv4;     // 1/lambda_i
     const float *beta32, *gamma32, *dgamma32, *c4_32, *inv4_32;
+    const float4 *p4;       // ProbMinHash4 point i: {gamma_{i-1}, dgamma_i, c4_i, inv4_i} in FP32, one 16-byte load (i = m: {gamma_{m-1}, 0, 0, 0})
     double c3, inv3, delta; // ProbMinHash3: expm1(-lambda), 1/lambda; ProbMinHash4: delta = 1/lambda_1
     float c3_32, inv3_32, delta32;
     float te_lo;            // (1-e^{-lambda_1})/lambda_1 rounded down: Exp(lambda_1;0,1) >= U * te_lo

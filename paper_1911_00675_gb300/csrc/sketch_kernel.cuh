@@ -452,8 +452,9 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
             } else {
                 float sv = 0.0f;
                 if (act) {
-                    if (i < m) sv = __fadd_rn(T.gamma32[i - 1], __fmul_rn(T.dgamma32[i], texp_32(vw, T.c4_32[i], T.inv4_32[i])));
-                    else sv = __fadd_rn(T.gamma32[m - 1], __fmul_rn(T.delta32, exp1_32(vw)));
+                    const float4 q = T.p4[i];
+                    if (i < m) sv = __fadd_rn(q.x, __fmul_rn(q.y, texp_32(vw, q.z, q.w)));
+                    else sv = __fadd_rn(q.x, __fmul_rn(T.delta32, exp1_32(vw)));
                 }
                 x32 = __fmul_rn(winv32, sv);
             }
@@ -679,7 +680,7 @@ __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, 
             // correlated families: point i lies above its lower bound
             if (FAM >= 3 && L.i >= 2) {
                 if constexpr (F32) {
-                    const float lb = (FAM == 3 || c.unw) ? L.winv32 * (float)(L.i - 1) : L.winv32 * T.gamma32[L.i - 1];
+                    const float lb = (FAM == 3 || c.unw) ? L.winv32 * (float)(L.i - 1) : L.winv32 * T.p4[L.i].x;
                     done = lb * (1.0f - kEta) > ld_volatile(&c.ts->bound32);
                 } else {
                     const double lb = (FAM == 3 || c.unw) ? lower3_64(L.i, L.w_inv) : lower4_64(T, L.i, L.w_inv);
@@ -719,8 +720,9 @@ __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, 
                     else if (FAM == 3) x32 = __fmul_rn(L.winv32, __fadd_rn((float)(L.i - 1), texp_32(vw, T.c3_32, T.inv3_32)));
                     else {
                         float sv;
-                        if (L.i < m) sv = __fadd_rn(T.gamma32[L.i - 1], __fmul_rn(T.dgamma32[L.i], texp_32(vw, T.c4_32[L.i], T.inv4_32[L.i])));
-                        else sv = __fadd_rn(T.gamma32[m - 1], __fmul_rn(T.delta32, exp1_32(vw)));
+                        const float4 q = T.p4[L.i];
+                        if (L.i < m) sv = __fadd_rn(q.x, __fmul_rn(q.y, texp_32(vw, q.z, q.w)));
+                        else sv = __fadd_rn(q.x, __fmul_rn(T.delta32, exp1_32(vw)));
                         x32 = __fmul_rn(L.winv32, sv);
                     }
                     const float b32 = ld_volatile(&c.ts->bound32);
