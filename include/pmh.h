@@ -201,7 +201,7 @@ pmh_status pmh_last_host_span_ms(pmh_handle h, float *ms, int32_t *chunks);
  * Same arguments and results as pmh_sketch_batch (without a handle: it runs
  * on the current device), computed by the same kernels.  Its scratch memory
  * (constant tables, work queue, per-set statistics) is one fixed array of
- * about 3.5 MiB that every GPU holds for as long as the library is loaded;
+ * about 3.6 MiB that every GPU holds for as long as the library is loaded;
  * the call itself allocates and frees no device memory and builds no CUDA
  * graph.  Limits: num_sets <= PMH_NOALLOC_MAX_SETS and
  * num_sets * num_variants <= PMH_NOALLOC_MAX_ITEMS; larger batches return
