@@ -55,7 +55,7 @@ OPS_BBIT_WORD = 2 + 2 * (6 + 2) + 2
 # DRAM bytes (read + write) of the four family sketch kernels per element-variant, from the ncu
 # capture summarised in profiles/sketch_kernel_c2_2000sets_full.md (same kernel source); the
 # traffic grows in proportion to the elements (one pass over ids and weights per family).
-TRAFFIC_BYTES_PER_ELEMENT_VARIANT = 13.96
+TRAFFIC_BYTES_PER_ELEMENT_VARIANT = 13.95
 
 
 def parse():
