@@ -143,7 +143,7 @@ struct WarpShared {
     int slot[32];              // Fisher-Yates scratch (deep mode)
     uint32_t sb_e[32 + kSurvCap];   // prefilter survivors: element index, from sb_e[32] (deep queue from sb_e[0])
     uint64_t sb_key[kSurvCap]; //   stream key
-    float sb_winv[kSurvCap];   //   and scaled FP32 reciprocal weight
+    float sb_winv[kSurvCap];   //   and scaled FP32 weight (its reciprocal once the batch is expanded)
     int sb_n;
 };
 
@@ -600,16 +600,16 @@ constexpr int kSeqCap = PMH_SEQ_CAP;        // lane-sequential points (ProbMinHa
 constexpr int kSeqCap3 = PMH_SEQ_CAP3;      // lane-sequential points (ProbMinHash3)
 static_assert(kSeqCap <= 32, "the FP32 running-sum error bound holds for at most 32 terms");
 
-// Lane-sequential state of one lane: the survivor it is expanding.  For
-// ProbMinHash1/3 it outlives a call of process_survivors: when the buffer runs
-// dry while a few lanes are still busy, those lanes keep their elements and
-// resume them in the next call, together with the survivors that the filter
-// buffered meanwhile (the bound only falls in between, so a resumed sequence
-// stops no later than it would have).  ProbMinHash2/4 lanes keep their
-// Fisher-Yates write lists in place meanwhile; since those share bytes with
-// the deep-mode permutation, their deep queue waits for a call that ends with
-// every lane idle.  Which families carry lanes over is a tuning constant
-// (PMH_SEQ_KEEP_FAMS).
+// Lane-sequential state of one lane: the survivor it is expanding.  In the
+// families that carry lanes over (PMH_SEQ_KEEP_FAMS: ProbMinHash1 and 2 by
+// default) it outlives a call of process_survivors: when the buffer runs dry
+// while a few lanes are still busy, those lanes keep their elements and resume
+// them in the next call, together with the survivors that the filter buffered
+// meanwhile (the bound only falls in between, so a resumed sequence stops no
+// later than it would have).  ProbMinHash2/4 lanes keep their Fisher-Yates
+// write lists in place meanwhile; since those share bytes with the deep-mode
+// permutation, their deep queue waits for a call that ends with every lane
+// idle.
 template <bool F32>
 struct SeqLane {
     bool has;
@@ -620,8 +620,9 @@ struct SeqLane {
     int fyn;
 };
 
-// Expands the n buffered survivors (ws->sb_e[32 + j], sb_key[j], sb_winv[j]).
-// fin: the last call of the pass (every sequence ends in it).
+// Expands the n buffered survivors (ws->sb_e[32 + j], sb_key[j], sb_winv[j];
+// the filter leaves w * 2^-sigma in sb_winv, replaced by its scaled reciprocal
+// on entry).  fin: the last call of the pass (every sequence ends in it).
 template <int FAM, bool F32>
 __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, int n, bool fin) {
     const long long t_sv = clock64();
