@@ -25,3 +25,14 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    """Near-tie rates of the sampled full-size parity tests (oracle near ties over components)."""
+    mod = sys.modules.get("parity_util")
+    if mod is None:
+        return
+    for label, near, comps, mism in mod.NEAR_TIE_LOG:
+        rate = near / comps if comps else 0.0
+        terminalreporter.write_line(f"near ties {label}: {near} of {comps} components ({rate:.2e}), "
+                                    f"{mism} exempted id mismatches")

@@ -18,7 +18,11 @@ import oracle
 
 VARS = ["1", "1a", "2", "3", "3a", "4"]
 NEAR_REL = 1e-12
+NEAR_MAX_FRACTION = 1e-6
 Q_RTOL = 1e-10
+# (label, near ties, components scanned) of the tests that scanned every sampled set; printed at
+# the end of the run by the terminal summary in conftest.py
+NEAR_TIE_LOG = []
 
 
 def to_dev(batch):
@@ -37,18 +41,24 @@ def run(H, batch, variants, precision, with_q=True, seed=0, counters=None):
     return (pmh.to_u64(z), q.cpu().numpy() if q is not None else None, st.cpu().numpy())
 
 
-def check_sets(batch, variant, z, q, sets, seed=0, stats=None):
-    """Compares GPU rows z[s], q[s] with the oracle for the listed sets."""
+def check_sets(batch, variant, z, q, sets, seed=0, stats=None, scan=False):
+    """Compares GPU rows z[s], q[s] with the oracle for the listed sets.
+
+    stats (optional dict): "near" counts the oracle's near ties, "components" the components
+    compared, "mismatch" the exempted id mismatches.  Without `scan` near ties are counted only
+    in sets with a mismatch; with `scan` every set is scanned, so "near" / "components" is the
+    near-tie rate of the sample."""
     m = batch.m
     for s in sets:
         ids, w = batch.set(s)
         qo, zo, _ = oracle.sketch(variant, ids, w, m, seed=seed)
         diff = np.nonzero(z[s] != zo)[0]
-        if len(diff):
+        if len(diff) or (scan and stats is not None):
             flags, _ = oracle.near_ties(variant, ids, w, m, seed, qo, zo, NEAR_REL)
             assert flags[diff].all(), f"set {s} variant {variant}: {len(diff)} unflagged id mismatches, e.g. k={diff[:5]}"
             if stats is not None:
                 stats["near"] += int(flags.sum())
+                stats["mismatch"] = stats.get("mismatch", 0) + len(diff)
         if stats is not None:
             stats["components"] += m
         if q is not None:
@@ -57,3 +67,10 @@ def check_sets(batch, variant, z, q, sets, seed=0, stats=None):
             np.testing.assert_allclose(q[s][fin], qo[fin], rtol=Q_RTOL, atol=0)
 
 
+
+
+def assert_near_tie_rate(stats, label=None):
+    """The exemption's limit: near ties at most 1e-6 of the components compared."""
+    if label is not None:
+        NEAR_TIE_LOG.append((label, stats["near"], stats["components"], stats.get("mismatch", 0)))
+    assert stats["near"] <= NEAR_MAX_FRACTION * stats["components"], stats

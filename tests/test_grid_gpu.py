@@ -12,7 +12,7 @@ import pytest
 import torch
 
 from paper_1911_00675_gb300 import workloads as W
-from parity_util import VARS, check_sets, run
+from parity_util import VARS, assert_near_tie_rate, check_sets, run
 
 pytestmark = pytest.mark.gpu
 GRID_MIN = 40_000
@@ -141,8 +141,8 @@ def test_c5_full_size(H, precision):
     z, q, st = run(H, b, ["3a"], precision, seed=0)
     _status_ok(st)
     stats = {"near": 0, "components": 0}
-    check_sets(b, "3a", z[0], q[0], [0], seed=0, stats=stats)
-    assert stats["near"] <= 4
+    check_sets(b, "3a", z[0], q[0], [0], seed=0, stats=stats, scan=True)
+    assert_near_tie_rate(stats, f"c5 ({'fp32' if precision else 'fp64'}, one set of 1e8, m=4096)")
 
 
 def test_profiling_history_records_each_call(H):

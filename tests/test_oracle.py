@@ -432,6 +432,76 @@ def test_near_tie_scan_consistency():
         assert flags.sum() == np.isfinite(ru).sum()
 
 
+def _singleton_hashes(variant, ids, w, m, seed):
+    """h_k(d) for every element d and component k: the signature of the one-element set {d} holds
+    exactly d's first point with each label (Eq. def_new_exp), computed by the pinned algorithm."""
+    return np.array([oracle.sketch(variant, ids[j:j + 1], w[j:j + 1], m, seed=seed)[0] for j in range(len(ids))])
+
+
+@pytest.mark.parametrize("variant", VARS + ["3u", "3au", "4u"])
+def test_near_tie_scan_runner_up_equals_singletons(variant):
+    # The near-tie scan decides which GPU/oracle id mismatches are forgiven, so its runner-up is
+    # pinned to an independent computation: per component the second smallest h_k(d) over the
+    # set's elements (Eq. signature_def ranks (h_k(d), d) lexicographically), taken from the
+    # singleton signatures.  The scan only sees points up to q_max (1 + rel); wide windows
+    # (rel = 0.3, 3) put runner-ups of the maximum component above q_max inside it.
+    rng = np.random.default_rng(810 + (VARS + ["3u", "3au", "4u"]).index(variant))
+    for trial, m in enumerate([7, 16, 33, 64]):
+        n = int(rng.integers(2, 60))
+        ids, w = _rand_set(rng, n, ["uniform", "pareto", "lognormal", "unit"][trial])
+        seed = 40 + trial
+        h = _singleton_hashes(variant, ids, w, m, seed)
+        q, z, _ = oracle.sketch(variant, ids, w, m, seed=seed)
+        for rel in (1e-12, 0.3, 3.0):
+            flags, ru = oracle.near_ties(variant, ids, w, m, seed, q, z, rel)
+            bound = q.max() * (1.0 + rel)
+            for k in range(m):
+                order = np.lexsort((ids, h[:, k]))
+                assert ids[order[0]] == z[k] and h[order[0], k] == q[k]
+                second = h[order[1], k]
+                expect = second if second <= bound else np.inf
+                assert ru[k] == expect, (variant, m, rel, k)
+                assert bool(flags[k]) == bool(np.isfinite(expect) and expect - q[k] < rel * q[k])
+
+
+@pytest.mark.parametrize("variant", VARS)
+@pytest.mark.parametrize("where", ["first", "max"])
+def test_near_tie_scan_flags_a_planted_tie(variant, where):
+    # Two elements A and B.  B's weight is chosen so that its point with label k lies within
+    # 3e-13 relative above A's (all of B's points scale with 1/w_B), so A wins component k by
+    # less than 1e-12 relative: a near tie the scan must flag with B's value as runner-up.
+    # where = "first": k = the label of A's first point.  where = "max": k = A's largest
+    # component, which stays the set's maximum component (every component is at most A's
+    # value), so B's point lies above q_max and is found only through the widened window.
+    m, seed = 16, 9
+    pool = W.distinct_ids(1 << 33, 400, 77)
+    a, wa = pool[:1], np.array([1.0])
+    ha = oracle.sketch(variant, a, wa, m, seed=seed)[0]
+    k = int(np.argmin(ha)) if where == "first" else int(np.argmax(ha))
+    for b in pool[1:]:
+        hb1 = oracle.sketch(variant, np.array([b], dtype=np.uint64), np.array([1.0]), m, seed=seed)[0]
+        wb = hb1[k] / (ha[k] * (1.0 + 3e-13))
+        hb = oracle.sketch(variant, np.array([b], dtype=np.uint64), np.array([wb]), m, seed=seed)[0]
+        gap = (hb[k] - ha[k]) / ha[k]
+        if not 0.0 < gap < 1e-12:
+            continue
+        # A must win every other component comfortably (B's values elsewhere well above A's)
+        others = np.delete(np.arange(m), k)
+        if where == "max" and not (hb[others] > ha[others] * 1.01).all():
+            continue
+        ids = np.array([a[0], b], dtype=np.uint64)
+        w = np.array([wa[0], wb])
+        q, z, _ = oracle.sketch(variant, ids, w, m, seed=seed)
+        assert z[k] == a[0] and q[k] == ha[k]
+        if where == "max":
+            assert q[k] == q.max()
+        flags, ru = oracle.near_ties(variant, ids, w, m, seed, q, z, 1e-12)
+        assert flags[k] == 1 and ru[k] == hb[k]
+        assert flags.sum() == 1
+        return
+    pytest.fail("no element found to plant a near tie")
+
+
 # --------------------------------------------------------------- b-bit signatures
 # Algorithm "Reduction to a b-bit signature": each component becomes b bits of a hash of
 # (component, index); the estimator must account for collisions of different elements.

@@ -19,7 +19,7 @@ import torch
 
 import oracle
 from paper_1911_00675_gb300 import workloads as W
-from parity_util import NEAR_REL, Q_RTOL, VARS, check_sets, run, to_dev  # noqa: F401
+from parity_util import NEAR_REL, Q_RTOL, VARS, assert_near_tie_rate, check_sets, run, to_dev  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -128,7 +128,7 @@ def test_c1_full(H):
             check_sets(b, v, z[vi], q[vi] if q is not None else None, range(b.num_sets))
 
 
-def _sampled_parity(H, b, variants, n_sample, seed=0):
+def _sampled_parity(H, b, variants, n_sample, seed=0, label=None):
     z64, _, st64 = run(H, b, variants, 0, with_q=False)
     z32, _, st32 = run(H, b, variants, 1, with_q=False)
     assert (st64 == 0).all() and (st32 == 0).all()
@@ -141,18 +141,18 @@ def _sampled_parity(H, b, variants, n_sample, seed=0):
                                      rng.choice(len(order), n_sample // 2, replace=False)]))
     stats = {"near": 0, "components": 0}
     for vi, v in enumerate(variants):
-        check_sets(b, v, z32[vi], None, pick, stats=stats)
-    assert stats["near"] <= max(1e-6 * stats["components"], 0)
+        check_sets(b, v, z32[vi], None, pick, stats=stats, scan=True)
+    assert_near_tie_rate(stats, label)
 
 
 @pytest.mark.slow
 def test_c2_full_sampled(H):
-    _sampled_parity(H, W.batch_c2(), VARS, 24)
+    _sampled_parity(H, W.batch_c2(), VARS, 24, label="c2 (20,000 sets, m=1024, six variants; sampled sets)")
 
 
 @pytest.mark.slow
 def test_c3_full_sampled(H):
-    _sampled_parity(H, W.batch_c3(), ["2", "4"], 10)
+    _sampled_parity(H, W.batch_c3(), ["2", "4"], 10, label="c3 (10,000 x 10,000, Pareto(1.5), m=4096; sampled sets)")
 
 
 @pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5], ids=["warp", "cta8", "quad", "pair", "quad8", "quad8l"])
