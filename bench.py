@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -34,9 +35,7 @@ METRIC = "set elements sketched/sec at m=1024 on 1 GB300 (FP32+recheck vs plain 
 UNIT = "elements/s"
 VARIANTS = ["1", "1a", "2", "3", "3a", "4"]
 
-# Algorithmic integer/FP32 operations per unit of work (counted from the
-# method's arithmetic): one SplitMix64 word is 2 64-bit
-# xor-shift-multiply rounds + 1 xor-shift + the counter add = 20 32-bit ops.
+# Algorithmic integer/FP32 operations per unit of work, counted from the method's arithmetic.
 # SplitMix64 word: three 64-bit xor-shifts (4 each), two 64-bit multiplies by a constant (3 each) and the
 # 64-bit counter add (2) = 20.
 OPS_ELEMENT = 55        # every element-variant: key = mix(id ^ mix(seed)) (22), weight check (2), scaled w
@@ -53,9 +52,11 @@ OPS_PAIR_COMPONENT = 3  # equal-component count: two 32-bit compares and one add
 # shift + or (6) and and-not + popcount (2), two adds (2)
 OPS_BBIT_WORD = 2 + 2 * (6 + 2) + 2
 # DRAM bytes (read + write) of the four family sketch kernels per element-variant, from the ncu
-# capture summarised in profiles/sketch_kernel_c2_2000sets_full.md (same kernel source); the
-# traffic grows in proportion to the elements (one pass over ids and weights per family).
+# capture summarised in profiles/sketch_kernel_c2_2000sets_full.md; the traffic grows in
+# proportion to the elements (one pass over ids and weights per family).
 TRAFFIC_BYTES_PER_ELEMENT_VARIANT = 13.95
+TRAFFIC_BASIS = ("ncu dram bytes per element-variant on a 2,000-set c2-shaped batch (kernel source of commit "
+                 "305e05b) x this step's work")
 
 
 def parse():
@@ -80,11 +81,11 @@ def parse():
 
 # ------------------------------------------------------------------ CPU oracle
 def _oracle_task(args):
-    """Worker: oracle signature of one (set, variant); returns the element count."""
-    variant, ids, w, m = args
+    """Worker: oracle signature of one (set, variant); returns (variant, set, elements, points)."""
+    variant, s, ids, w, m = args
     import oracle
-    oracle.sketch(variant, ids, w, m, seed=0)
-    return len(ids)
+    _, _, st = oracle.sketch(variant, ids, w, m, seed=0)
+    return variant, s, len(ids), st["points"]
 
 
 def _oracle_pool(cores):
@@ -95,13 +96,14 @@ def _oracle_pool(cores):
     import numpy as np
     ctx = mp.get_context("spawn")
     pool = ctx.Pool(cores)
-    pool.map(_oracle_task, [("1", np.array([1], dtype=np.uint64), np.ones(1), 8)] * cores)
+    pool.map(_oracle_task, [("1", 0, np.array([1], dtype=np.uint64), np.ones(1), 8)] * cores)
     return pool
 
 
-def oracle_throughput(batch, seconds, cores, rng_seed=1):
+def oracle_throughput(batch, seconds, cores, rng_seed=1, done=None):
     """Elements x variants per second of the oracle on a random sample of (set, variant) tasks,
-    run on `cores` processes for about `seconds` of wall time."""
+    run on `cores` processes for about `seconds` of wall time.  `done` (optional list) receives
+    (variant, set, points) of every finished task."""
     import numpy as np
     import oracle
     oracle.build()
@@ -110,17 +112,57 @@ def oracle_throughput(batch, seconds, cores, rng_seed=1):
     pool = _oracle_pool(cores)
     done_elems, done_tasks = 0, 0
     t0 = time.perf_counter()
-    it = pool.imap_unordered(_oracle_task, ((v, *batch.set(s), batch.m) for v, s in tasks), chunksize=1)
+    it = pool.imap_unordered(_oracle_task, ((v, int(s), *batch.set(s), batch.m) for v, s in tasks), chunksize=1)
     try:
-        for n in it:
+        for v, s, n, pts in it:
             done_elems += n
             done_tasks += 1
+            if done is not None:
+                done.append((v, s, pts))
             if time.perf_counter() - t0 > seconds:
                 break
     finally:
         el = time.perf_counter() - t0
         pool.terminate()
     return done_elems / el, done_elems, done_tasks, el
+
+
+def parallel_overhead(h, batch, done, dev):
+    """GPU point evaluations against the oracle's sequential point count on the same (set, variant)
+    tasks: the oracle generates each element's points in order and stops at the running q_max, the
+    GPU runs threshold rounds over elements in parallel.  The GPU side runs one call per variant
+    over the sets the oracle finished with that variant."""
+    import numpy as np
+    import torch
+    from paper_1911_00675_gb300 import pmh
+    from paper_1911_00675_gb300 import workloads as W
+    by_v = {}
+    for v, s, pts in done:
+        by_v.setdefault(v, []).append((s, pts))
+    gpu = {"points32": 0, "prefiltered": 0, "elements": 0, "deep": 0}
+    oracle_pts = 0
+    for v, lst in by_v.items():
+        sets = np.array(sorted(s for s, _ in lst), dtype=np.int64)
+        oracle_pts += sum(p for _, p in lst)
+        sizes = batch.offsets[sets + 1] - batch.offsets[sets]
+        idx = np.concatenate([np.arange(batch.offsets[s], batch.offsets[s + 1]) for s in sets])
+        off = np.zeros(len(sets) + 1, dtype=np.int64)
+        np.cumsum(sizes, out=off[1:])
+        sub = W.Batch(batch.ids[idx], batch.weights[idx], off, batch.m)
+        cnt = torch.zeros(len(pmh.COUNTERS), dtype=torch.int64, device=dev)
+        h.sketch_batch(torch.from_numpy(sub.ids.view(np.int64)).to(dev), torch.from_numpy(sub.weights).to(dev),
+                       torch.from_numpy(sub.offsets).to(dev), batch.m, [v], pmh.FP32_RECHECK, 0, counters=cnt)
+        c = dict(zip(pmh.COUNTERS, cnt.cpu().tolist()))
+        for k in gpu:
+            gpu[k] += c[k]
+    tasks = sum(len(x) for x in by_v.values())
+    return {"tasks": tasks, "oracle_points": oracle_pts, "gpu_points32": gpu["points32"],
+            "gpu_prefiltered": gpu["prefiltered"], "gpu_elements": gpu["elements"], "gpu_deep_elements": gpu["deep"],
+            "factor_points": gpu["points32"] / max(1, oracle_pts),
+            "factor_points_and_prefiltered": (gpu["points32"] + gpu["prefiltered"]) / max(1, oracle_pts),
+            "note": "factor_points = FP32 point evaluations on the GPU / points the oracle generated on the same "
+                    "(set, variant) tasks; the second factor also counts each element the GPU rejected by its "
+                    "first point's lower bound (no logarithm) as one point"}
 
 
 # ------------------------------------------------------------------ host placement
@@ -148,13 +190,15 @@ def bind_gpu_local_cpus(gpu_index):
 
 # ------------------------------------------------------------------ peaks
 def measured_peaks():
-    """HBM GB/s and SM clock measured on this GPU type (MEASURED_PEAKS.json), else the stated fallback."""
+    """HBM GB/s measured on this GPU type (MEASURED_PEAKS.json, a STREAM-style copy), else the value
+    that file held on the GB300s when it was last present."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "basis": "measured"}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "basis": "measured (MEASURED_PEAKS.json)"}
     except Exception:
-        return {"hbm_gbs": 6800.0, "basis": "fallback"}
+        return {"hbm_gbs": 6780.0, "basis": "measured copy bandwidth of this pool's GB300s (MEASURED_PEAKS.json "
+                                            "absent in this run: its earlier value)"}
 
 
 def alu_peak(n_sms, sm_mhz):
@@ -163,8 +207,9 @@ def alu_peak(n_sms, sm_mhz):
 
 # ------------------------------------------------------------------ secondary kernels
 def secondary(h, dev, n_sms, sm_mhz, peaks, steps=3):
-    """Per-kernel measurements beside the headline: grid mode on one huge set (HBM-bound) and the
-    all-pairs equal-component count (integer-ALU-bound).  Device time by CUDA events on the stream."""
+    """Per-kernel measurements beside the headline: the precision config (FP32 + recheck against FP64
+    at m = 4096), grid mode on one huge set (HBM-bound) and the all-pairs equal-component count
+    (integer-ALU-bound).  Device time by CUDA events on the stream."""
     import numpy as np
     import torch
     from paper_1911_00675_gb300 import pmh
@@ -182,6 +227,39 @@ def secondary(h, dev, n_sms, sm_mhz, peaks, steps=3):
         e1.record(stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / k
+
+    # precision config: 10,000 sets x n = 10,000, Pareto(1.5) weights, m = 4096, ProbMinHash2 and 4,
+    # FP32 candidates + FP64 recheck against the all-FP64 path on identical inputs
+    b3 = W.batch_c3()
+    ids3 = torch.from_numpy(b3.ids.view(np.int64)).to(dev)
+    w3 = torch.from_numpy(b3.weights).to(dev)
+    off3 = torch.from_numpy(b3.offsets).to(dev)
+    n3 = b3.num_elements
+    S3 = b3.num_sets
+    del b3
+    v3 = ["2", "4"]
+    z3 = {p: torch.empty((2, S3, 4096), dtype=torch.int64, device=dev) for p in (0, 1)}
+    st3 = {p: torch.empty((2, S3), dtype=torch.int32, device=dev) for p in (0, 1)}
+    res = {}
+    for prec, name, k in ((pmh.FP32_RECHECK, "fp32", steps), (pmh.FP64, "fp64", 1)):
+        ms = timed(lambda: h.sketch_batch(ids3, w3, off3, 4096, v3, prec, 0, out_ids=z3[prec], status=st3[prec]), k)
+        res[name] = {"ms": ms, "elements_per_s": 2 * n3 / (ms * 1e-3),
+                     "status_ok": bool((st3[prec] == 0).all().item())}
+    cnt3 = torch.zeros(len(pmh.COUNTERS), dtype=torch.int64, device=dev)
+    h.sketch_batch(ids3, w3, off3, 4096, v3, pmh.FP32_RECHECK, 0, out_ids=z3[1], status=st3[1], counters=cnt3)
+    torch.cuda.synchronize()
+    c3 = dict(zip(pmh.COUNTERS, cnt3.cpu().tolist()))
+    out["precision_c3"] = {
+        "workload": "10,000 sets x n=10,000, Pareto(x_m=1, tail 1.5) weights, m=4096, ProbMinHash2 and 4",
+        **res, "speedup_fp32_vs_fp64": res["fp64"]["ms"] / res["fp32"]["ms"],
+        "identical_output": bool(torch.equal(z3[0], z3[1])),
+        "near_margin_events": c3["contenders"], "exact_fp64_evaluations": c3["resolved"],
+        "items_redone_in_fp64": c3["redo"], "components": 2 * S3 * 4096,
+        "points32": c3["points32"], "points64": c3["points64"],
+        "note": "near_margin_events: pairs of FP32 candidates of one component within the FP32 error bound "
+                "(2^-18 relative), each resolved by exact FP64 evaluation; the oracle's own near ties "
+                "(< 1e-12 relative) are counted by the GPU parity tests"}
+    del ids3, w3, off3, z3, st3
 
     # huge set: 1e8 elements, lognormal(0, 2) weights, m = 4096, ProbMinHash3a, every SM on the one set
     b5 = W.batch_c5()
@@ -214,7 +292,7 @@ def secondary(h, dev, n_sms, sm_mhz, peaks, steps=3):
     del ids4, w4, off4
     S4 = z4.shape[0]
     counts = torch.empty((S4, S4), dtype=torch.int16, device=dev)
-    ms = timed(lambda: h.estimate_allpairs(z4, upper_only=True, counts=counts), steps)
+    ms = timed(lambda: h.estimate_jp(z4, upper_only=True, counts=counts), steps)
     pairs = S4 * (S4 + 1) // 2
     ops = pairs * 1024 * OPS_PAIR_COMPONENT
     a = ops / (ms * 1e-3) / 1e12
@@ -252,11 +330,11 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        fd, self.path = tempfile.mkstemp(prefix=f"pmh_clocks_gpu{gpu_index}_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                                           "-lms", "200", "-i", str(self.gpu)], stdout=self.f,
@@ -288,6 +366,10 @@ class ClockSampler:
                 for n, v in zip(names, parts[5:9]):
                     if v.lower() == "active":
                         reasons.add(n)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
@@ -386,8 +468,9 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    # ---------------- headline: FP32 + recheck
-    h.set_profiling(True)
+    # ---------------- headline: FP32 + recheck, as the library runs it: each call replays the cached CUDA
+    # graph of the batch (the first call autotunes the team shapes and captures the graph)
+    h.set_profiling(False)
     for _ in range(args.warmup):
         step(pmh.FP32_RECHECK, out32, st32)
     clocks = ClockSampler(local)
@@ -400,9 +483,20 @@ def main():
     e1.record(stream)
     barrier()
     t32 = max_over_ranks(e0.elapsed_time(e1) / args.steps)
-    queue_ms, kernel_ms = h.kernel_ms_history(args.steps)   # the library's events of those same calls
     launches_per_step = h.last_launches()
     shapes_headline = h.last_team_shapes()
+    # the same steps again with the library's profiling events (direct launches, not graph replay): the
+    # device time of the queue build and of the sketch kernels of each call
+    h.set_profiling(True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(pmh.FP32_RECHECK, out32, st32)
+    e1.record(stream)
+    barrier()
+    t32_profiled = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    queue_ms, kernel_ms = h.kernel_ms_history(args.steps)
+    h.set_profiling(False)
 
     # ---------------- e2e: host buffers in, signatures back, every step, through the host-buffer C-ABI
     # call (pinned host memory; the library pipelines copy-in, sketch and copy-out over chunks of sets)
@@ -426,10 +520,10 @@ def main():
             walls.append((time.perf_counter() - s0) * 1e3)
             spans.append(h.last_host_span_ms()[0])
         barrier()
+        # the mean step (total wall time / steps) is the end-to-end rate; the median is reported beside
+        # it (the host link is shared with the other GPU of the same CPU, which slows some steps)
         te_mean = max_over_ranks((time.perf_counter() - t0) * 1e3 / ksteps)
-        # the host link is shared with the other GPU of the same CPU: a busy neighbour slows some
-        # steps several-fold, so the headline is the median step (the mean is reported beside it)
-        te = max_over_ranks(statistics.median(walls))
+        te_median = max_over_ranks(statistics.median(walls))
         identical_e2e = bool(torch.equal(out_h, out32.cpu()))
         # the copies alone, for reference: inputs in, signatures out (pinned, one stream)
         barrier()
@@ -443,16 +537,17 @@ def main():
         c2 = time.perf_counter()
         h2d = ids_h.numel() * 8 + w_h.numel() * 8 + off_h.numel() * 8
         d2h = out_h.numel() * 8
-        e2e = {"value": work * world / (te * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": te, "ms_per_step_mean": te_mean,
-               "timing": f"median over {ksteps} steps of the host wall clock around each blocking call",
+        e2e = {"value": work * world / (te_mean * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": te_mean, "ms_per_step_median": te_median,
+               "value_median_step": work * world / (te_median * 1e-3),
+               "timing": f"host wall clock over {ksteps} blocking calls / {ksteps} (median step beside it)",
+               "step_ms": walls,
                "identical_output": identical_e2e,
                "host_cpus": local_cpus, "copy_in_ms": (c1 - c0) * 1e3, "copy_out_ms": (c2 - c1) * 1e3,
                "device_span_ms": statistics.mean(spans), "device_span_ms_min": min(spans),
                "device_span_ms_median": statistics.median(spans), "chunks": h.last_host_span_ms()[1]}
 
-    # ---------------- comparator: plain FP64
-    h.set_profiling(True)
+    # ---------------- comparator: plain FP64 (graph replay as well), then its kernel time from profiled calls
     for _ in range(min(args.warmup, 2)):
         step(pmh.FP64, out64, st64)
     barrier()
@@ -462,7 +557,9 @@ def main():
     e1.record(stream)
     barrier()
     t64 = max_over_ranks(e0.elapsed_time(e1) / max(1, args.fp64_steps))
-    k64 = h.kernel_ms_history(args.fp64_steps)[1] or [float("nan")]
+    h.set_profiling(True)
+    step(pmh.FP64, out64, st64)
+    k64 = h.kernel_ms_history(1)[1] or [float("nan")]
     clk = clocks.stop()
     h.set_profiling(False)
 
@@ -485,9 +582,11 @@ def main():
     peak = n_sms * LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (32-bit lane ops)",
                 "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_ELEMENT_VARIANT * work,
-                "traffic_basis": "ncu dram bytes per element-variant on a 2,000-set c2-shaped batch x this step's work",
+                "traffic_basis": TRAFFIC_BASIS,
                 "kernel": "pmh::sketch_kernel<FP32> (four family launches per step)",
-                "kernel_ms": k_avg, "ops_per_launch": per_launch_ops,
+                "kernel_ms": k_avg, "kernel_ms_basis": "library CUDA events around the sketch kernels of each "
+                                                         "profiled call (the second timed pass)",
+                "ops_per_launch": per_launch_ops,
                 "peak_basis": f"{n_sms} SMs x {LANES_PER_SM_CLK} lane-ops/clk x {sm_mhz:.0f} MHz (median under load)"}
 
     # ---------------- queue build + set statistics: one read of offsets (x3) and weights
@@ -502,13 +601,16 @@ def main():
     if not args.no_secondary:
         sec_res = secondary(h, dev, n_sms, sm_mhz, peaks)
 
-    # ---------------- CPU baseline (rank 0, N=1 only)
+    # ---------------- CPU baseline (rank 0, N=1 only), and the GPU's point work on the same tasks
     cpu = None
+    overhead = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = len(os.sched_getaffinity(0)) or 1
-        v, el, tasks, sec = oracle_throughput(batch, args.cpu_seconds, cores)
+        done = []
+        v, el, tasks, sec = oracle_throughput(batch, args.cpu_seconds, cores, done=done)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{tasks} random (set, variant) tasks, {el} elements, {sec:.1f} s wall on {cores} processes"}
+        overhead = parallel_overhead(h, batch, done, dev)
 
     if rank == 0:
         value = work * world / (t32 * 1e-3)
@@ -522,6 +624,9 @@ def main():
                        "precision": "fp32 candidates + fp64 recheck", "parallelism": f"weak x{world}",
                        "team_shapes": shapes_headline,
                        "l2": f"inputs {(16 * n_elem + 8 * S) / 1e9:.2f} GB per step > 129 MB L2"},
+            "timing": "CUDA events around the timed steps on the launching stream; each step replays the "
+                      "library's cached CUDA graph",
+            "ms_per_step_profiled": t32_profiled,
             "fp64": {"value": work * world / (t64 * 1e-3), "ms_per_step": t64, "kernel_ms": statistics.mean(k64),
                      "speedup_fp32_vs_fp64": t64 / t32},
             "identical_output": identical, "status_ok": statuses_ok,
@@ -529,6 +634,7 @@ def main():
             "queue_build_ms": statistics.mean(queue_ms),
             "roofline": roofline,
             "queue_build_roofline": queue_roof,
+            "parallel_overhead": overhead,
             "secondary": sec_res,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -33,7 +33,7 @@ typedef enum {
     PMH_OK = 0,
     PMH_ERR_INVALID_ARG = 1,   /* argument rejected on the host, or bad offsets (per set) */
     PMH_ERR_BAD_WEIGHT = 2,    /* per set: a weight is < 0, NaN, +-inf, or 1/w is not finite */
-    PMH_ERR_ITER_LIMIT = 3,    /* per set: an iteration or resource cap was hit (Sec. Experiments) */
+    PMH_ERR_ITER_LIMIT = 3,    /* per set: an iteration cap was hit (Sec. Experiments), or a redo list was full */
     PMH_ERR_CUDA = 4,          /* a CUDA runtime call failed */
     PMH_ERR_NO_MEMORY = 5,     /* workspace allocation failed */
     PMH_ERR_UNSUPPORTED = 6    /* a size outside the supported limits */
@@ -95,7 +95,8 @@ enum {
     PMH_CNT_CYC_BARRIER = 17, /* waiting for the team's other warps at the end of a round (part of CYC_FIRST) */
     PMH_CNT_SEQ_STEPS = 18,   /* warp steps of lane-sequential survivor expansion (32 lane slots each) */
     PMH_CNT_SEQ_POINTS = 19,  /* points evaluated lane-sequentially (part of POINTS32/POINTS64) */
-    PMH_NUM_COUNTERS = 20
+    PMH_CNT_REDO = 20,        /* FP32 items whose contender log overflowed, sketched again in FP64 */
+    PMH_NUM_COUNTERS = 21
 };
 
 /* Creates a handle bound to CUDA device `device` (the device is made current
@@ -153,6 +154,21 @@ pmh_status pmh_sketch_batch(pmh_handle h, const uint64_t *ids, const double *wei
                             int32_t *set_status, uint64_t *counters, void *stream);
 
 /*
+ * pmh_sync_status -- waits for `stream` to reach this call, then reduces the
+ * per-item statuses a pmh_sketch_batch call wrote (set_status of n items).
+ *   counts     host int64[8] or NULL: counts[c] = items with status c for
+ *              c = 0..6; counts[7] = items with any other value.
+ *   first_bad  host int64 or NULL: index of the first item whose status is not
+ *              PMH_OK, or -1.
+ * Returns PMH_OK when every item is PMH_OK, else the status of the first item
+ * that is not (PMH_ERR_INVALID_ARG for a value outside the enum), or a
+ * host-side error (NULL handle, n < 0, NULL set_status with n > 0;
+ * PMH_ERR_CUDA).  A small device buffer stays with the handle.
+ */
+pmh_status pmh_sync_status(pmh_handle h, const int32_t *set_status, int64_t n, int64_t *counts, int64_t *first_bad,
+                           void *stream);
+
+/*
  * pmh_sketch_batch_host -- pmh_sketch_batch on HOST buffers: the same batch,
  * variants, precision, seed and results (identical values), with ids,
  * weights, offsets and the outputs in host memory.
@@ -199,18 +215,21 @@ pmh_status pmh_last_host_span_ms(pmh_handle h, float *ms, int32_t *chunks);
  * no counterpart; this is an interface of this library only.
  *
  * Same arguments and results as pmh_sketch_batch (without a handle: it runs
- * on the current device), computed by the same kernels.  Its scratch memory
- * (constant tables, work queue, per-set statistics) is one fixed array of
- * about 3.6 MiB that every GPU holds for as long as the library is loaded;
+ * on the current device), computed by the same kernels, except that grid mode
+ * is off: a set of 2^20 elements or more is sketched by one team instead of
+ * the whole GPU (same result, far slower).  Its scratch memory (constant
+ * tables, work queue, FP64 redo list, per-set statistics) is one fixed array
+ * of about 5.6 MiB that every GPU holds for as long as the library is loaded;
  * the call itself allocates and frees no device memory and builds no CUDA
  * graph.  Limits: num_sets <= PMH_NOALLOC_MAX_SETS and
  * num_sets * num_variants <= PMH_NOALLOC_MAX_ITEMS; larger batches return
- * PMH_ERR_UNSUPPORTED (message in pmh_last_error(NULL)).
- * The first call on a device resolves the array's device address; make that
- * first call before any stream capture.  Every call on a device shares the
- * array, which keeps the last call's contents: calls whose work overlaps on
- * the GPU (other streams, other host threads) race and must be ordered by the
- * caller.
+ * PMH_ERR_UNSUPPORTED (message in pmh_last_error(NULL)).  Each call resolves
+ * the array's device address and uploads the tables of its m from a static
+ * host buffer in stream order; because later calls rewrite that buffer, a
+ * call made while `stream` is being captured into a CUDA graph returns
+ * PMH_ERR_UNSUPPORTED.  Every call on a device shares the array: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and must
+ * be ordered by the caller.
  */
 #define PMH_NOALLOC_MAX_SETS 65536
 #define PMH_NOALLOC_MAX_ITEMS 262144
@@ -277,8 +296,10 @@ pmh_status pmh_last_team_shapes(pmh_handle h, int32_t *shapes);
 
 /*
  * pmh_last_launches -- number of kernels the most recent pmh_sketch_batch on
- * `h` launched (queue build, statistics, per-family sketch kernels and, when
- * grid mode is on, its reset kernel and per-family grid kernels).
+ * `h` launched (queue build, statistics, per-family sketch kernels, with
+ * PMH_FP32_RECHECK the per-family FP64 redo kernels (they return at once when
+ * no item overflowed its contender log) and, when grid mode is on, its reset
+ * kernel and per-family grid kernels).
  */
 pmh_status pmh_last_launches(pmh_handle h, int32_t *launches);
 
@@ -305,6 +326,27 @@ pmh_status pmh_last_launches(pmh_handle h, int32_t *launches);
  * rounds outside [0, 64].
  */
 pmh_status pmh_set_thresholds(pmh_handle h, double t_c, double t_c_grid, int32_t rounds, int64_t grid_min);
+
+/*
+ * pmh_set_limits -- resource caps of later pmh_sketch_batch calls on `h`
+ * (the iteration limits that keep the paper's loops finite, Sec.
+ * Experiments).  Results of items that stay within them do not change.
+ *
+ *   cap_points      points one element may generate in warp-cooperative
+ *                   expansion (sequences longer than the lane-sequential caps
+ *                   of 32 points for ProbMinHash1/1a and 64 for ProbMinHash3/3a
+ *                   go there); an element that needs more fails its item with
+ *                   PMH_ERR_ITER_LIMIT.  0 = the default 64 m ln(m+1) + 4096.
+ *                   ProbMinHash2/4 sequences have m points and no cap.
+ *   max_contenders  FP32 candidate path: contender records kept per item (two
+ *                   per near-margin event; -1 = the defaults, 64 per team and
+ *                   1024 per grid-mode item; at most 1024).  An item whose log
+ *                   overflows is not failed: it is sketched again by the FP64
+ *                   kernel that follows its family's kernels in the same call
+ *                   (counter PMH_CNT_REDO), with the same result as PMH_FP64.
+ * Errors: PMH_ERR_INVALID_ARG for NULL h or max_contenders outside [-1, 1024].
+ */
+pmh_status pmh_set_limits(pmh_handle h, uint32_t cap_points, int32_t max_contenders);
 
 /*
  * pmh_bbit_reduce -- Algorithm "Reduction to a b-bit signature": component k
@@ -351,7 +393,7 @@ pmh_status pmh_check_exp1(const uint64_t *words, int64_t n, float *out, void *st
 pmh_status pmh_check_texp(const uint64_t *words, int64_t n, float c, float inv, float *out, void *stream);
 
 /*
- * pmh_estimate_allpairs -- numerators of the J_P estimator (Eq. jaccard_estimator)
+ * pmh_estimate_jp -- numerators of the J_P estimator (Eq. jaccard_estimator)
  * for every pair of signatures: counts[a*num_sigs + b] = #{k : sigs[a][k] == sigs[b][k]}.
  *
  *   sigs      device uint64[num_sigs * m], row-major (one signature per row).
@@ -359,8 +401,13 @@ pmh_status pmh_check_texp(const uint64_t *words, int64_t n, float c, float inv, 
  *   upper_only 0: the full matrix is written.  1: only entries with a <= b are
  *             written (the rest of `counts` is left untouched).
  *   counts    device uint16[num_sigs * num_sigs].
- * Exact integer counts; J_P estimate = counts / m.
+ * Exact integer counts; J_P estimate = counts / m.  Errors: PMH_ERR_INVALID_ARG
+ * (NULL pointers, num_sigs < 0), PMH_ERR_UNSUPPORTED (m > 65535, more than
+ * 65535 tiles of 64 rows), PMH_ERR_CUDA.
+ * pmh_estimate_allpairs is the same call under its earlier name.
  */
+pmh_status pmh_estimate_jp(pmh_handle h, const uint64_t *sigs, int64_t num_sigs, uint32_t m, int32_t upper_only,
+                           uint16_t *counts, void *stream);
 pmh_status pmh_estimate_allpairs(pmh_handle h, const uint64_t *sigs, int64_t num_sigs, uint32_t m,
                                  int32_t upper_only, uint16_t *counts, void *stream);
 
@@ -380,7 +427,8 @@ pmh_status pmh_estimate_pairs(pmh_handle h, const uint64_t *sig_a, const uint64_
  * its parts: per component the lexicographic minimum of (q, id) over `parts`
  * partial signatures (Eq. signature_def; the minimum over a union is the
  * minimum of the parts' minima, and q_max only decreases).
- *   q, z      device float64 / uint64 [parts * m] (part-major).
+ *   q, z      device float64 / uint64 [parts * m] (part-major); q >= 0 or +inf
+ *             (component minima as pmh_sketch_batch writes them).
  *   out_q, out_z device [m].
  * Bit-exact with sketching the union when the parts were sketched with the
  * same (m, seed, variant family) and exact q (out_q).

@@ -28,7 +28,7 @@
  *   - the binary-weight specialisations of ProbMinHash3, 3a and 4 (Sec.
  *     Conventional Jaccard Similarity): uniform variates, gamma_i = i
  *
- * Readings of the paper taken here (also listed in the design doc):
+ * Readings of the paper taken here:
  *   - Ties: components keep the lexicographic minimum of (value, element id);
  *     the stop test is strict (stop when a point is > q_max), so an equal
  *     value with a smaller id is still examined.  The paper's "<" / ">=" make

@@ -50,6 +50,7 @@ struct TuneKey {
 // per-set statistics, grid-mode state.
 struct Workspace {
     uint64_t *queue = nullptr;
+    uint64_t *redo = nullptr;        // FP32 items redone in FP64, per family segment (capacity queue_cap)
     int64_t queue_cap = 0;
     unsigned int *qmeta = nullptr;   // histogram, running starts, per-family heads, big-set list
     SetStat *stats = nullptr;
@@ -98,6 +99,7 @@ struct pmh_handle_s {
     bool autotune = true;
     std::map<TuneKey, int> tuned;            // best TeamShape per key
     cudaEvent_t tev[3 + 4] = {};             // autotuning: queue/sketch brackets + one per family
+    unsigned long long *status_scratch = nullptr;   // pmh_sync_status: 8 counts + the first failing (index, code)
     // profiling events
     bool profiling = false;
     bool prof_recorded = false;        // the most recent call was profiled
@@ -147,10 +149,13 @@ static pmh_status ensure_queue(pmh_handle h, Workspace &w, int64_t items) {
     if (items > w.queue_cap) {
         if (w.queue) cudaFree(w.queue);
         w.queue = nullptr;
+        w.redo = nullptr;
         w.queue_cap = 0;
         int64_t cap = items < 1024 ? 1024 : items;
-        cudaError_t e = cudaMalloc(&w.queue, (size_t)cap * sizeof(uint64_t));
+        // the work queue and, behind it, the FP64 redo list of the same capacity
+        cudaError_t e = cudaMalloc(&w.queue, (size_t)cap * 2 * sizeof(uint64_t));
         if (e != cudaSuccess) return fail(h, PMH_ERR_NO_MEMORY, "queue allocation (%lld items): %s", (long long)cap, cudaGetErrorString(e));
+        w.redo = w.queue + cap;
         w.queue_cap = cap;
         h->graph_valid = false;
     }
@@ -211,7 +216,7 @@ static pmh_status enqueue_sketch(pmh_handle h, Workspace &w, const SketchParams 
         pmh_status rc = ensure_fork(h);
         if (rc) return rc;
     }
-    cudaError_t e = enqueue_batch(p, plan, precision, h->sm_count, w.queue, w.qmeta, w.stats, st, prof_ev, fam_ev,
+    cudaError_t e = enqueue_batch(p, plan, precision, h->sm_count, w.queue, w.redo, w.qmeta, w.stats, st, prof_ev, fam_ev,
                                   fork ? &h->ff : nullptr);
     if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "sketch launch: %s", cudaGetErrorString(e));
     return PMH_OK;
@@ -249,6 +254,7 @@ extern "C" void pmh_destroy(pmh_handle h) {
     for (cudaEvent_t e : h->ring) cudaEventDestroy(e);
     for (int i = 0; i < 7; i++) if (h->tev[i]) cudaEventDestroy(h->tev[i]);
     for (auto &kv : h->tables) cudaFree(kv.second.dev);
+    if (h->status_scratch) cudaFree(h->status_scratch);
     for (Workspace &w : h->ws) {
         if (w.queue) cudaFree(w.queue);
         if (w.qmeta) cudaFree(w.qmeta);
@@ -293,6 +299,17 @@ extern "C" pmh_status pmh_set_thresholds(pmh_handle h, double t_c, double t_c_gr
     h->th.t_c_grid = t_c_grid;
     h->th.rounds = rounds;
     h->th.grid_min = grid_min;
+    h->graph_valid = false;
+    return PMH_OK;
+}
+
+extern "C" pmh_status pmh_set_limits(pmh_handle h, uint32_t cap_points, int32_t max_contenders) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    if (max_contenders < -1 || max_contenders > kGridCont)
+        return fail(h, PMH_ERR_INVALID_ARG, "max_contenders = %d outside [-1, %d]", max_contenders, kGridCont);
+    h->th.cap_points = cap_points;
+    h->th.max_cont = max_contenders;
     h->graph_valid = false;
     return PMH_OK;
 }
@@ -381,9 +398,10 @@ static pmh_status autotune_shapes(pmh_handle h, Workspace &w, SketchParams p, ui
         if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
         if (!fits) continue;
         SketchParams q = p;
+        q.counters = nullptr;   // the trials are not the call's work
         for (int j = 0; j < plan.nfam && q.gctl; j++)
             if (plan.ggrid[j] <= 0) { q.gctl = nullptr; q.gstate = nullptr; q.gsig = nullptr; }
-        e = enqueue_batch(q, plan, precision, h->sm_count, w.queue, w.qmeta, w.stats, st, h->tev, h->tev + 3);
+        e = enqueue_batch(q, plan, precision, h->sm_count, w.queue, w.redo, w.qmeta, w.stats, st, h->tev, h->tev + 3);
         if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(e));
         CUDA_TRY(h, cudaEventSynchronize(h->tev[2]));
         for (int j = 0; j < plan.nfam; j++) {
@@ -484,7 +502,7 @@ static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, cons
     // takes are skipped by the ordinary kernels)
     for (int j = 0; j < plan.nfam && p.gctl; j++)
         if (plan.ggrid[j] <= 0) { p.gctl = nullptr; p.gstate = nullptr; p.gsig = nullptr; }
-    h->last_launches = launch_count(plan, p.gctl != nullptr);
+    h->last_launches = launch_count(plan, p.gctl != nullptr, precision == PMH_FP32_RECHECK);
     for (int f = 0; f < 4; f++) h->last_shape[f] = -1;
     for (int j = 0; j < plan.nfam; j++) h->last_shape[plan.fam[j] - 1] = plan.shape[j].kind;
     cudaEvent_t *prof_ev = nullptr;
@@ -817,23 +835,29 @@ __global__ void pairs_kernel(const uint64_t *__restrict__ sa, const uint64_t *__
     }
 }
 
+// Component minima are non-negative doubles or +inf, which order like their
+// bit patterns as unsigned integers: the comparison runs on the integer pipe
+// (an FP64 comparison would make this HBM-bound kernel FP64-pipe bound).
 __global__ void merge_kernel(const double *__restrict__ q, const uint64_t *__restrict__ z, int64_t parts, uint32_t m,
                              double *__restrict__ oq, uint64_t *__restrict__ oz) {
+    const unsigned long long *qb = (const unsigned long long *)q;
+    constexpr unsigned long long kInf = 0x7FF0000000000000ull;
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
-        double bq = __longlong_as_double(0x7FF0000000000000ll);
+        unsigned long long bq = kInf;
         uint64_t bz = 0;
+#pragma unroll 8
         for (int64_t p = 0; p < parts; p++) {
-            const double x = q[p * m + k];
-            const uint64_t d = z[p * m + k];
-            if (x < bq || (x == bq && !isinf(x) && d < bz)) { bq = x; bz = d; }
+            const unsigned long long x = __ldcs(qb + p * m + k);
+            const uint64_t d = __ldcs(z + p * m + k);
+            if (x < bq || (x == bq && x != kInf && d < bz)) { bq = x; bz = d; }
         }
-        oq[k] = bq;
-        oz[k] = isinf(bq) ? 0 : bz;
+        oq[k] = __longlong_as_double((long long)bq);
+        oz[k] = bq == kInf ? 0 : bz;
     }
 }
 
-extern "C" pmh_status pmh_estimate_allpairs(pmh_handle h, const uint64_t *sigs, int64_t num_sigs, uint32_t m,
-                                            int32_t upper_only, uint16_t *counts, void *stream) {
+extern "C" pmh_status pmh_estimate_jp(pmh_handle h, const uint64_t *sigs, int64_t num_sigs, uint32_t m,
+                                      int32_t upper_only, uint16_t *counts, void *stream) {
     if (!h) return PMH_ERR_INVALID_ARG;
     h->err.clear();
     if (num_sigs < 0) return fail(h, PMH_ERR_INVALID_ARG, "num_sigs < 0");
@@ -847,6 +871,58 @@ extern "C" pmh_status pmh_estimate_allpairs(pmh_handle h, const uint64_t *sigs, 
     allpairs_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(sigs, num_sigs, m, upper_only ? 1 : 0, counts);
     CUDA_TRY(h, cudaGetLastError());
     return PMH_OK;
+}
+
+extern "C" pmh_status pmh_estimate_allpairs(pmh_handle h, const uint64_t *sigs, int64_t num_sigs, uint32_t m,
+                                            int32_t upper_only, uint16_t *counts, void *stream) {
+    return pmh_estimate_jp(h, sigs, num_sigs, m, upper_only, counts, stream);
+}
+
+// ------------------------------------------------------------------ status reduction
+// Per-code item counts (codes outside 0..6 in slot 7) and the minimum of
+// (index << 8 | code) over the items that are not PMH_OK.
+static __global__ void status_reduce_kernel(const int32_t *__restrict__ st, int64_t n, unsigned long long *out) {
+    __shared__ unsigned long long cnt[8];
+    if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    unsigned long long first = ~0ull;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = st[i];
+        const int slot = (c >= 0 && c <= 6) ? c : 7;
+        atomicAdd(&cnt[slot], 1ull);
+        if (c != PMH_OK) first = min(first, ((unsigned long long)i << 8) | (unsigned long long)(slot == 7 ? 255 : c));
+    }
+    for (int o = 16; o; o >>= 1) first = min(first, __shfl_xor_sync(0xFFFFFFFFu, first, o));
+    if ((threadIdx.x & 31) == 0 && first != ~0ull) atomicMin(&out[8], first);
+    __syncthreads();
+    if (threadIdx.x < 8 && cnt[threadIdx.x]) atomicAdd(&out[threadIdx.x], cnt[threadIdx.x]);
+}
+
+extern "C" pmh_status pmh_sync_status(pmh_handle h, const int32_t *set_status, int64_t n, int64_t *counts,
+                                      int64_t *first_bad, void *stream) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    if (n < 0 || (n > 0 && !set_status)) return fail(h, PMH_ERR_INVALID_ARG, "n < 0 or NULL set_status");
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long host[9];
+    for (int i = 0; i < 8; i++) host[i] = 0;
+    host[8] = ~0ull;
+    if (n > 0) {
+        if (!h->status_scratch) CUDA_TRY(h, cudaMalloc(&h->status_scratch, 9 * sizeof(unsigned long long)));
+        CUDA_TRY(h, cudaMemcpyAsync(h->status_scratch, host, sizeof(host), cudaMemcpyHostToDevice, st));
+        const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)h->sm_count * 4);
+        status_reduce_kernel<<<grid, 256, 0, st>>>(set_status, n, h->status_scratch);
+        CUDA_TRY(h, cudaGetLastError());
+        CUDA_TRY(h, cudaMemcpyAsync(host, h->status_scratch, sizeof(host), cudaMemcpyDeviceToHost, st));
+    }
+    CUDA_TRY(h, cudaStreamSynchronize(st));
+    if (counts)
+        for (int i = 0; i < 8; i++) counts[i] = (int64_t)host[i];
+    if (first_bad) *first_bad = host[8] == ~0ull ? -1 : (int64_t)(host[8] >> 8);
+    if (host[8] == ~0ull) return PMH_OK;
+    const int code = (int)(host[8] & 0xFF);
+    return code == 255 ? PMH_ERR_INVALID_ARG : (pmh_status)code;
 }
 
 // ------------------------------------------------------------------ b-bit signatures

@@ -97,9 +97,12 @@ inline uint64_t host_mix64(uint64_t z) {
 // each family sorted by decreasing floor(log2(n+1)) (largest sets first).
 // Meta layout: [0, 256) histogram per (family, bucket), [256, 512) running
 // starts, [512, 516) per-family head counters of the persistent kernels.
-// [516] counts the sets whose statistics are split over all blocks; [520, ...)
-// lists them (u64 set indices, kBigCap of them).
-constexpr int kQHist = 0, kQStart = 256, kQHead = 512, kQBigCount = 516, kQStatNext = 518, kQBigList = 520;
+// [516] counts the sets whose statistics are split over all blocks, [518, 520)
+// is the statistics kernel's set counter (u64), [520, 524) the per-family
+// lengths of the FP64 redo lists and [524, 528) the head counters of the redo
+// kernels; [528, ...) lists the split sets (u64 set indices, kBigCap of them).
+constexpr int kQHist = 0, kQStart = 256, kQHead = 512, kQBigCount = 516, kQStatNext = 518, kQRedoCount = 520,
+              kQRedoHead = 524, kQBigList = 528;
 constexpr int kBigCap = 1024;
 constexpr int kQMetaWords = kQBigList + 2 * kBigCap;
 constexpr int kQMetaClearWords = kQBigList;     // words cleared per call
@@ -335,7 +338,37 @@ struct Plan {
     int grid[4];
     LaunchShape gshape[4];   // grid-mode kernel (blocks_per_sm = 0: grid mode off for this family)
     int ggrid[4];
+    LaunchShape rshape[4];   // FP32 calls: the FP64 kernel that redoes items whose contender log overflowed
+    int rgrid[4];
 };
+
+// Default team shape of a family: teams of 2 warps when 16 warps per SM fit,
+// else warp teams when 12 fit, else CTA teams of 8; when none of these fits in
+// shared memory (FP64 signatures at m = 8192), the shape with the most
+// resident warps among those that fit (blocks_per_sm = 0: nothing fits).
+inline cudaError_t default_shape(bool f32, int f, uint32_t m, LaunchShape *out) {
+    LaunchShape pair_s{}, warp_s{}, cta_s{};
+    cudaError_t e = sketch_shape_any(f32, f, kShapePair, m, &pair_s);
+    if (e != cudaSuccess) return e;
+    e = sketch_shape_any(f32, f, kShapeWarp, m, &warp_s);
+    if (e != cudaSuccess) return e;
+    LaunchShape shape = pair_s.blocks_per_sm * 8 >= 16 ? pair_s : warp_s;
+    if (shape.blocks_per_sm * (shape.block / 32) < 12) {
+        e = sketch_shape_any(f32, f, kShapeCta8, m, &cta_s);
+        if (e != cudaSuccess) return e;
+        if (cta_s.blocks_per_sm > 0) shape = cta_s;
+    }
+    if (shape.blocks_per_sm <= 0) {
+        for (int k = 0; k < kNumShapes; k++) {
+            LaunchShape t{};
+            e = sketch_shape_any(f32, f, k, m, &t);
+            if (e != cudaSuccess) return e;
+            if (t.blocks_per_sm * (t.block / 32) > shape.blocks_per_sm * (shape.block / 32)) shape = t;
+        }
+    }
+    *out = shape;
+    return cudaSuccess;
+}
 
 // Returns cudaSuccess and sets *fits = false when m does not fit in shared memory.
 // kinds[f-1]: team shape for family f (TeamShape), or -1 for the default
@@ -360,26 +393,8 @@ inline cudaError_t plan_batch(int sm_count, int precision, uint32_t m, const int
             if (e != cudaSuccess) return e;
         }
         if (shape.blocks_per_sm <= 0) {
-            LaunchShape pair_s{}, warp_s{}, cta_s{};
-            e = sketch_shape_any(f32, f, kShapePair, m, &pair_s);
+            e = default_shape(f32, f, m, &shape);
             if (e != cudaSuccess) return e;
-            e = sketch_shape_any(f32, f, kShapeWarp, m, &warp_s);
-            if (e != cudaSuccess) return e;
-            shape = pair_s.blocks_per_sm * 8 >= 16 ? pair_s : warp_s;
-            if (shape.blocks_per_sm * (shape.block / 32) < 12) {
-                e = sketch_shape_any(f32, f, kShapeCta8, m, &cta_s);
-                if (e != cudaSuccess) return e;
-                if (cta_s.blocks_per_sm > 0) shape = cta_s;
-            }
-        }
-        if (shape.blocks_per_sm <= 0) {
-            // large m: the shape with the most resident warps among those that fit at all
-            for (int k = 0; k < kNumShapes; k++) {
-                LaunchShape t{};
-                e = sketch_shape_any(f32, f, k, m, &t);
-                if (e != cudaSuccess) return e;
-                if (t.blocks_per_sm * (t.block / 32) > shape.blocks_per_sm * (shape.block / 32)) shape = t;
-            }
         }
         if (shape.blocks_per_sm <= 0) { *fits = false; return cudaSuccess; }
         int grid = sm_count * shape.blocks_per_sm;
@@ -397,6 +412,14 @@ inline cudaError_t plan_batch(int sm_count, int precision, uint32_t m, const int
         if (e != cudaSuccess) return e;
         out->gshape[j] = gs;
         out->ggrid[j] = sm_count * gs.blocks_per_sm;
+        // the FP64 redo kernel: one block per SM at most (redone items are rare), none when it does not fit
+        LaunchShape rs{};
+        if (f32) {
+            e = default_shape(false, f, m, &rs);
+            if (e != cudaSuccess) return e;
+        }
+        out->rshape[j] = rs;
+        out->rgrid[j] = rs.blocks_per_sm > 0 ? sm_count : 0;
         base += items;
     }
     return cudaSuccess;
@@ -416,7 +439,7 @@ struct FamilyFork {
 };
 
 inline cudaError_t enqueue_batch(SketchParams p, const Plan &plan, int precision, int sm_count, uint64_t *queue,
-                                 unsigned int *qmeta, SetStat *stats, cudaStream_t st, cudaEvent_t *ev,
+                                 uint64_t *redo, unsigned int *qmeta, SetStat *stats, cudaStream_t st, cudaEvent_t *ev,
                                  cudaEvent_t *fam_ev = nullptr, const FamilyFork *ff = nullptr) {
     const int64_t items = p.num_sets * p.num_variants;
     FamOfVariant fv{};
@@ -444,15 +467,36 @@ inline cudaError_t enqueue_batch(SketchParams p, const Plan &plan, int precision
         for (int j = 0; j < plan.nfam; j++)
             if ((e = cudaStreamWaitEvent(ff->s[j], ff->fork, 0)) != cudaSuccess) return e;
     }
+    const bool f32 = precision == PMH_FP32_RECHECK;
     for (int j = 0; j < plan.nfam; j++) {
         cudaStream_t sj = forked ? ff->s[j] : st;
-        p.queue = queue + plan.qbase[j];
-        p.queue_len = plan.qlen[j];
-        p.head = qmeta + kQHead + (plan.fam[j] - 1);
-        e = sketch_launch_any(precision == PMH_FP32_RECHECK, plan.fam[j], plan.shape[j], plan.grid[j], p, sj);
+        const int f = plan.fam[j];
+        SketchParams pj = p;
+        pj.queue = queue + plan.qbase[j];
+        pj.queue_len = plan.qlen[j];
+        pj.head = qmeta + kQHead + (f - 1);
+        if (f32 && redo && plan.rgrid[j] > 0) {
+            pj.redo = redo + plan.qbase[j];
+            pj.redo_count = qmeta + kQRedoCount + (f - 1);
+            pj.redo_cap = plan.qlen[j];
+        }
+        e = sketch_launch_any(f32, f, plan.shape[j], plan.grid[j], pj, sj);
         if (e != cudaSuccess) return e;
-        if (p.gctl && plan.ggrid[j] > 0) {
-            e = grid_launch_any(precision == PMH_FP32_RECHECK, plan.fam[j], plan.gshape[j], plan.ggrid[j], p, sj);
+        if (pj.gctl && plan.ggrid[j] > 0) {
+            e = grid_launch_any(f32, f, plan.gshape[j], plan.ggrid[j], pj, sj);
+            if (e != cudaSuccess) return e;
+        }
+        if (pj.redo) {
+            // items whose contender log overflowed, sketched again in FP64 (the list is usually empty)
+            SketchParams pr = pj;
+            pr.queue = pj.redo;
+            pr.queue_len = pj.redo_cap;
+            pr.queue_len_dev = pj.redo_count;
+            pr.head = qmeta + kQRedoHead + (f - 1);
+            pr.redo = nullptr;
+            pr.redo_count = nullptr;
+            pr.redo_cap = 0;
+            e = sketch_launch_any(false, f, plan.rshape[j], plan.rgrid[j], pr, sj);
             if (e != cudaSuccess) return e;
         }
         if (fam_ev && (e = cudaEventRecord(fam_ev[j], sj)) != cudaSuccess) return e;
@@ -475,12 +519,14 @@ struct Thresholds {
     double t_c_grid = 8.0;
     int rounds = 5;
     int64_t grid_min = kGridMinDefault;
+    uint32_t cap_points = 0;   // points per element in warp-cooperative expansion (0: 64 m ln(m+1) + 4096)
+    int max_cont = -1;         // contender records per team / grid item (-1: kMaxCont / kGridCont)
 };
 
 // Kernel launches of one enqueue_batch call (fixed by the plan).
-inline int launch_count(const Plan &plan, bool grid) {
+inline int launch_count(const Plan &plan, bool grid, bool redo) {
     int n = 5 + plan.nfam + (grid ? 1 : 0);
-    for (int j = 0; j < plan.nfam; j++) n += (grid && plan.ggrid[j] > 0) ? 1 : 0;
+    for (int j = 0; j < plan.nfam; j++) n += ((grid && plan.ggrid[j] > 0) ? 1 : 0) + ((redo && plan.rgrid[j] > 0) ? 1 : 0);
     return n;
 }
 
@@ -503,7 +549,13 @@ inline void fill_params(SketchParams *p, const uint64_t *ids, const double *weig
     p->counters = (unsigned long long *)counters;
     p->t_factor = (float)(std::log((double)m) + th.t_c);
     p->rounds = th.rounds;
-    p->cap_points = (uint32_t)(64.0 * m * std::log((double)m + 1.0)) + 4096;
+    p->cap_points = th.cap_points ? th.cap_points : (uint32_t)(64.0 * m * std::log((double)m + 1.0)) + 4096;
+    p->max_cont = th.max_cont < 0 ? kMaxCont : std::min(th.max_cont, kMaxCont);
+    p->max_cont_grid = th.max_cont < 0 ? kGridCont : std::min(th.max_cont, kGridCont);
+    p->redo = nullptr;
+    p->redo_count = nullptr;
+    p->redo_cap = 0;
+    p->queue_len_dev = nullptr;
     p->t_factor_grid = (float)(std::log((double)m) + th.t_c_grid);
     p->grid_min = th.grid_min;
     p->gctl = nullptr;

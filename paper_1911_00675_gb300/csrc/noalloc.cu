@@ -5,7 +5,9 @@
 // tables, work queue and per-set statistics) lives in one file-scope device
 // array of fixed size that every GPU holds from the moment the library is
 // loaded until the process exits.  No call here allocates or frees device
-// memory, and no CUDA graph is built.
+// memory, and no CUDA graph is built.  Grid mode (all SMs on one huge set)
+// needs workspace sized by m and is off here: a set of 2^20 elements or more
+// runs on one team, with the same result but far more slowly.
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
@@ -17,13 +19,14 @@ using namespace pmh;
 
 namespace {
 
-// Scratch layout: tables for m <= PMH_MAX_M | queue metadata | work queue | per-set statistics.
+// Scratch layout: tables for m <= PMH_MAX_M | queue metadata | work queue | FP64 redo list (items whose
+// contender log overflowed) | per-set statistics.
 constexpr size_t kTableRegion = 640u * 1024u;                                  // >= table_bytes(PMH_MAX_M)
 static_assert(kTableRegion >= table_bytes(PMH_MAX_M), "table region too small");
 constexpr size_t kMetaRegion = 16384;                                           // >= kQMetaWords * 4
 constexpr size_t kQueueRegion = (size_t)PMH_NOALLOC_MAX_ITEMS * sizeof(uint64_t);
 constexpr size_t kStatsRegion = (size_t)PMH_NOALLOC_MAX_SETS * 16;
-constexpr size_t kScratchBytes = kTableRegion + kMetaRegion + kQueueRegion + kStatsRegion;
+constexpr size_t kScratchBytes = kTableRegion + kMetaRegion + 2 * kQueueRegion + kStatsRegion;
 static_assert(kMetaRegion >= kQMetaWords * sizeof(unsigned int), "queue metadata region too small");
 static_assert(sizeof(SetStat) == 16, "per-set statistics entry is 16 bytes");
 
@@ -33,10 +36,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 struct DeviceState {
-    bool ready = false;
-    unsigned char *base = nullptr;   // device address of g_noalloc_scratch on this device
-    int sm_count = 0;
-    uint32_t table_m = 0;            // m whose tables the table region holds (0 = none)
+    int sm_count = 0;                // 0 until the first call on this device
 };
 DeviceState g_state[kMaxDevices];
 std::mutex g_mu;
@@ -84,31 +84,38 @@ extern "C" pmh_status pmh_sketch_batch_noalloc(const uint64_t *ids, const double
     if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail_na(PMH_ERR_UNSUPPORTED, "device %d beyond %d", dev, kMaxDevices);
     cudaStream_t st = (cudaStream_t)stream;
+    // The tables are staged through one static host buffer that later calls rewrite, so a call
+    // recorded into a CUDA graph would replay with whatever the buffer holds then: refused.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail_na(PMH_ERR_UNSUPPORTED, "pmh_sketch_batch_noalloc cannot be called while its stream is being captured");
     std::lock_guard<std::mutex> lock(g_mu);
     DeviceState &ds = g_state[dev];
-    if (!ds.ready) {
-        // first call on this device: resolve the array's device address (do this before any stream capture)
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    if (!ds.sm_count) {
         e = cudaDeviceGetAttribute(&ds.sm_count, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "device attribute: %s", cudaGetErrorString(e));
-        ds.base = (unsigned char *)ptr;
-        ds.ready = true;
+        if (e != cudaSuccess) { ds.sm_count = 0; return fail_na(PMH_ERR_CUDA, "device attribute: %s", cudaGetErrorString(e)); }
     }
-    unsigned char *tables = ds.base;
-    unsigned int *qmeta = (unsigned int *)(ds.base + kTableRegion);
-    uint64_t *queue = (uint64_t *)(ds.base + kTableRegion + kMetaRegion);
-    SetStat *stats = (SetStat *)(ds.base + kTableRegion + kMetaRegion + kQueueRegion);
+    // the array's device address on the current device, resolved on every call (cheap, and still
+    // right after a cudaDeviceReset has replaced the context)
+    void *ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    unsigned char *base = (unsigned char *)ptr;
+    unsigned char *tables = base;
+    unsigned int *qmeta = (unsigned int *)(base + kTableRegion);
+    uint64_t *queue = (uint64_t *)(base + kTableRegion + kMetaRegion);
+    uint64_t *redo = (uint64_t *)(base + kTableRegion + kMetaRegion + kQueueRegion);
+    SetStat *stats = (SetStat *)(base + kTableRegion + kMetaRegion + 2 * kQueueRegion);
 
+    // The tables of this m are uploaded on every call (76 KiB at m = 1024), in stream order before
+    // the kernels: nothing on the host has to know what the array held before.  The copy from this
+    // pageable buffer has read it by the time cudaMemcpyAsync returns, so the next call may refill it.
     Tables tab;
     build_tables(m, g_host_tables, tables, &tab);
-    if (ds.table_m != m) {
-        // the table region keeps the last call's contents; upload only when m changes
-        e = cudaMemcpyAsync(tables, g_host_tables, table_bytes(m), cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
-        ds.table_m = m;
-    }
+    e = cudaMemcpyAsync(tables, g_host_tables, table_bytes(m), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
     SketchParams p;
     Thresholds th;
     th.grid_min = 0;   // grid mode needs workspace sized by m: off here
@@ -121,7 +128,7 @@ extern "C" pmh_status pmh_sketch_batch_noalloc(const uint64_t *ids, const double
     if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
     if (!fits) return fail_na(PMH_ERR_UNSUPPORTED, "m = %u does not fit in shared memory", m);
     // enqueue_batch clears the queue metadata; the queue and the statistics are rewritten in full
-    e = enqueue_batch(p, plan, precision, ds.sm_count, queue, qmeta, stats, st, nullptr);
+    e = enqueue_batch(p, plan, precision, ds.sm_count, queue, redo, qmeta, stats, st, nullptr);
     if (e != cudaSuccess) return fail_na(PMH_ERR_CUDA, "sketch launch: %s", cudaGetErrorString(e));
     return PMH_OK;
 }

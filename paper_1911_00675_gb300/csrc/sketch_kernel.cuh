@@ -45,7 +45,7 @@
 
 namespace pmh {
 
-constexpr int kMaxCont = 64;       // contender records per team (overflow -> PMH_ERR_ITER_LIMIT)
+constexpr int kMaxCont = 64;       // contender records per team (overflow: the item is redone in FP64)
 constexpr int kCasLimit = 1 << 16; // CAS retries per offer (each failure means another offer succeeded)
 constexpr int kSurvCap = 128;      // survivor buffer per warp: < 64 left over + <= 64 new per filter step
 #ifndef PMH_SURV_BATCH
@@ -77,7 +77,7 @@ struct GridState {
     int status;
     unsigned long long bound64;    // FP64 path: shared stop bound (double bits)
     int cont_n;
-    int pad;
+    int redo;                      // a CTA's contender log overflowed: the item goes to the FP64 redo
     unsigned int cont_k[kGridCont];
     unsigned int cont_e[kGridCont];
 };
@@ -115,6 +115,14 @@ struct SketchParams {
     float t_factor;               // ln m + c
     int rounds;                   // finite-T rounds before the T = +inf round
     uint32_t cap_points;          // iteration cap (with replacement)
+    int32_t max_cont;             // contender records kept per team (<= kMaxCont)
+    int32_t max_cont_grid;        // contender records kept per grid item (<= kGridCont)
+    // FP32 path: items whose contender log overflowed are listed here (this family's segment, of
+    // redo_cap entries) and sketched again by the FP64 kernel; null: overflow fails the item
+    uint64_t *redo;
+    unsigned int *redo_count;
+    int64_t redo_cap;
+    const unsigned int *queue_len_dev;   // FP64 redo launch: the queue's length in device memory (else null)
     // grid mode (null when disabled)
     GridCtl *gctl;
     GridState *gstate;            // [4][kMaxGrid]
@@ -128,6 +136,7 @@ struct TeamShared {
     int unfilled;
     int status;
     int cont_n;
+    int redo;           // FP32: the item was handed to the FP64 redo (outputs are written there)
     float bound32;      // stop bound in scaled FP32 units (x * 2^sigma)
     int sigma;
     double bound64;     // FP64 path: exact stop bound
@@ -231,7 +240,7 @@ template <> struct Offer<true> {
         // re-offers (deep mode restarts from point 1, later rounds repeat) are idempotent
         if ((uint32_t)(old & 0xFFFFFFFFu) != e && fabsf(x32 - xo) <= kEta * (x32 + xo)) {
             int at = atomicAdd(&c.ts->cont_n, 2);
-            if (at + 1 < kMaxCont) {
+            if (at + 1 < c.p->max_cont) {
                 c.ts->cont_k[at] = k;
                 c.ts->cont_e[at] = e;
                 c.ts->cont_k[at + 1] = k;
@@ -548,9 +557,20 @@ __device__ __noinline__ uint32_t resolve_list(Ctx<true> c, const uint32_t *ck, c
 template <int FAM>
 __device__ __forceinline__ uint32_t resolve_contenders(Ctx<true> &c) {
     TeamShared *ts = c.ts;
-    const int ncont_all = ld_volatile(&ts->cont_n);
-    if (ncont_all > kMaxCont) { if ((threadIdx.x & 31) == 0) ts->status = PMH_ERR_ITER_LIMIT; }
-    return resolve_list<FAM>(c, ts->cont_k, ts->cont_e, min(ncont_all, kMaxCont), (uint64_t *)c.sig);
+    const int ncont = min(ld_volatile(&ts->cont_n), c.p->max_cont);   // the caller redoes an item that overflowed
+    return resolve_list<FAM>(c, ts->cont_k, ts->cont_e, ncont, (uint64_t *)c.sig);
+}
+
+// FP32 path: hands an item whose contender log overflowed to the FP64 kernel
+// that runs after this family's kernels (its queue is the redo list).  Returns
+// false when there is no list or it is full; the item then fails with
+// PMH_ERR_ITER_LIMIT.  Called by one thread.
+__device__ __forceinline__ bool push_redo(const SketchParams &P, int item_v, int64_t set) {
+    if (!P.redo) return false;
+    const unsigned int at = atomicAdd(P.redo_count, 1u);
+    if ((int64_t)at >= P.redo_cap) return false;
+    P.redo[at] = ((uint64_t)item_v << 40) | (uint64_t)set;
+    return true;
 }
 
 // ------------------------------------------------------------ survivors
@@ -985,6 +1005,7 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
         ts->status = st0.bad ? PMH_ERR_BAD_WEIGHT : PMH_OK;
         ts->unfilled = (int)m;
         ts->cont_n = 0;
+        ts->redo = 0;
         int sigma = 0;
         float t_s = __int_as_float(0x7F800000);   // no usable estimate: a single unbounded round
         const double T = (double)m * (double)P.t_factor / st0.wsum;
@@ -1036,8 +1057,18 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
     }
     team_sync<TW>();
 
-    // ---- FP32: resolve contenders exactly
+    // ---- FP32: resolve contenders exactly, or redo the item in FP64 when they overflowed the log
     if constexpr (F32) {
+        if (leader && ld_volatile(&ts->cont_n) > P.max_cont && ld_volatile(&ts->status) == PMH_OK) {
+            if (push_redo(P, item_v, set)) ts->redo = 1;
+            else ts->status = PMH_ERR_ITER_LIMIT;
+        }
+        team_sync<TW>();
+        if (ld_volatile(&ts->redo)) {
+            count(c, PMH_CNT_REDO, leader);
+            count(c, PMH_CNT_CYC_FINISH, (unsigned long long)(clock64() - t_ph));
+            return;   // the FP64 kernel writes this item's outputs
+        }
         if (tw == 0 && ld_volatile(&ts->cont_n) > 0) {
             const uint32_t ev = resolve_contenders<FAM>(c);
             count(c, PMH_CNT_RESOLVED, ev);
@@ -1079,7 +1110,7 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
 // Merges a CTA-local FP32 key into the item's global signature (atomicMin),
 // logging both sides as contenders when they are within the error bound of
 // each other (same rule as an offer).
-__device__ __forceinline__ void merge_key_global(uint64_t *gsig, uint32_t k, uint64_t key, GridState *g) {
+__device__ __forceinline__ void merge_key_global(uint64_t *gsig, uint32_t k, uint64_t key, GridState *g, int max_cont) {
     const uint64_t cur = ld_volatile(&gsig[k]);
     const float x32 = __uint_as_float((uint32_t)(key >> 32));
     if (cur != kEmptyKey && __uint_as_float((uint32_t)(cur >> 32)) < x32 * (1.0f - 2.0f * kEta)) return;
@@ -1089,7 +1120,7 @@ __device__ __forceinline__ void merge_key_global(uint64_t *gsig, uint32_t k, uin
     const uint32_t e = (uint32_t)(key & 0xFFFFFFFFu), eo = (uint32_t)(old & 0xFFFFFFFFu);
     if (eo != e && fabsf(x32 - xo) <= kEta * (x32 + xo)) {
         const int at = atomicAdd(&g->cont_n, 2);
-        if (at + 1 < kGridCont) {
+        if (at + 1 < max_cont) {
             g->cont_k[at] = k; g->cont_e[at] = e;
             g->cont_k[at + 1] = k; g->cont_e[at + 1] = eo;
         }
@@ -1129,9 +1160,21 @@ __device__ void grid_finalize(Ctx<F32> &c, GridState *g, void *gsig_v, int item_
     if constexpr (F32) {
         uint64_t *gsig = (uint64_t *)gsig_v;
         const int nc = ld_volatile(&g->cont_n);
-        if (nc > kGridCont && st == PMH_OK) st = PMH_ERR_ITER_LIMIT;
+        if ((nc > P.max_cont_grid || ld_volatile(&g->redo)) && st == PMH_OK) {
+            // a contender log overflowed: the FP64 kernel of this family redoes the item
+            if (threadIdx.x == 0) {
+                if (push_redo(P, item_v, set)) ts->redo = 1;
+                else { ts->redo = 0; g->status = PMH_ERR_ITER_LIMIT; }
+            }
+            __syncthreads();
+            if (ts->redo) {
+                count(c, PMH_CNT_REDO, threadIdx.x == 0);
+                return;
+            }
+            st = PMH_ERR_ITER_LIMIT;
+        }
         if (tw == 0 && nc > 0 && st == PMH_OK) {
-            const uint32_t ev = resolve_list<FAM>(c, g->cont_k, g->cont_e, min(nc, kGridCont), gsig);
+            const uint32_t ev = resolve_list<FAM>(c, g->cont_k, g->cont_e, nc, gsig);
             count(c, PMH_CNT_RESOLVED, ev);
         }
     }
@@ -1240,7 +1283,7 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
         for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
             if constexpr (F32) {
                 const uint64_t key = ((const uint64_t *)c.sig)[k];
-                if (key != kEmptyKey) merge_key_global((uint64_t *)gsig_v, k, key, g);
+                if (key != kEmptyKey) merge_key_global((uint64_t *)gsig_v, k, key, g, P.max_cont_grid);
             } else {
                 merge_rec_global((Rec64 *)gsig_v, k, ((const Rec64 *)c.sig)[k], g);
             }
@@ -1248,11 +1291,11 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
         if (leader) {
             // local contenders join the item's list
             const int nl = ts->cont_n;
-            if (nl > kMaxCont) g->status = PMH_ERR_ITER_LIMIT;
-            const int nk = min(nl, kMaxCont);
+            if (nl > P.max_cont) g->redo = 1;
+            const int nk = min(nl, P.max_cont);
             if (nk > 0) {
                 const int at = atomicAdd(&g->cont_n, nk);
-                for (int j = 0; j < nk && at + j < kGridCont; ++j) { g->cont_k[at + j] = ts->cont_k[j]; g->cont_e[at + j] = ts->cont_e[j]; }
+                for (int j = 0; j < nk && at + j < P.max_cont_grid; ++j) { g->cont_k[at + j] = ts->cont_k[j]; g->cont_e[at + j] = ts->cont_e[j]; }
             }
             if (ts->status != PMH_OK) g->status = ts->status;
         }
@@ -1325,6 +1368,7 @@ static __global__ void grid_init_kernel(GridCtl *ctl, GridState *gs, void *gsig,
         g->status = PMH_OK;
         g->bound64 = 0x7FF0000000000000ull;
         g->cont_n = 0;
+        g->redo = 0;
     }
     unsigned char *sig = (unsigned char *)gsig + (size_t)slot * m * 16;
     for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
@@ -1362,13 +1406,15 @@ __global__ void __launch_bounds__(NW * 32, MINB) sketch_kernel(const __grid_cons
     const int tt = (warp % TW) * 32 + lane;   // thread index within the team
     const bool team_leader = tt == 0;
     const long long t_warp = clock64();
+    // the FP64 redo launch reads its queue's length (the FP32 kernels' redo count) from the device
+    const int64_t qlen = p.queue_len_dev ? min(p.queue_len, (int64_t)ld_volatile((const int *)p.queue_len_dev)) : p.queue_len;
     for (;;) {
         const long long t_item = clock64();
         if (team_leader) ts->item_idx = (int)atomicAdd(p.head, 1u);
         team_sync<TW>();
         const int64_t qi = ts->item_idx;
         team_sync<TW>();
-        if (qi >= p.queue_len) break;
+        if (qi >= qlen) break;
         const uint64_t it = p.queue[qi];
         if (it & kSkipBit) continue;     // processed in grid mode
         const int v = (int)(it >> 40);

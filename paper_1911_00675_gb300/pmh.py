@@ -23,14 +23,14 @@ FP64, FP32_RECHECK = 0, 1
 SHAPE_WARP, SHAPE_CTA8, SHAPE_QUAD, SHAPE_PAIR, SHAPE_QUAD8, SHAPE_QUAD8L = range(6)
 COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "rounds", "deep", "prefiltered",
             "cyc_pass0", "cyc_first", "cyc_deep", "cyc_refresh", "cyc_finish", "items", "cyc_surv", "cyc_item",
-            "cyc_warp", "cyc_barrier", "seq_steps", "seq_points")
+            "cyc_warp", "cyc_barrier", "seq_steps", "seq_points", "redo")
 EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_sketch_batch_host",
            "pmh_last_host_span_ms", "pmh_sketch_batch_noalloc",
            "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_kernel_ms_history", "pmh_last_launches",
-           "pmh_set_thresholds",
+           "pmh_set_thresholds", "pmh_set_limits", "pmh_sync_status",
            "pmh_set_team_shape", "pmh_set_autotune", "pmh_last_team_shapes",
-           "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge", "pmh_check_exp1", "pmh_check_texp",
-           "pmh_bbit_reduce", "pmh_bbit_allpairs")
+           "pmh_estimate_jp", "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge", "pmh_check_exp1",
+           "pmh_check_texp", "pmh_bbit_reduce", "pmh_bbit_allpairs")
 
 _lib = None
 _lock = threading.Lock()
@@ -85,6 +85,12 @@ def load(path: str = LIB_PATH):
             lib.pmh_last_team_shapes.argtypes = [vp, ctypes.POINTER(i32)]
             lib.pmh_set_thresholds.restype = i32
             lib.pmh_set_thresholds.argtypes = [vp, ctypes.c_double, ctypes.c_double, i32, i64]
+            lib.pmh_set_limits.restype = i32
+            lib.pmh_set_limits.argtypes = [vp, u32, i32]
+            lib.pmh_sync_status.restype = i32
+            lib.pmh_sync_status.argtypes = [vp, vp, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), vp]
+            lib.pmh_estimate_jp.restype = i32
+            lib.pmh_estimate_jp.argtypes = [vp, vp, i64, u32, i32, vp, vp]
             lib.pmh_estimate_allpairs.restype = i32
             lib.pmh_estimate_allpairs.argtypes = [vp, vp, i64, u32, i32, vp, vp]
             lib.pmh_estimate_pairs.restype = i32
@@ -250,6 +256,22 @@ class Handle:
         """Work-only tuning of later sketch_batch calls (results never depend on it)."""
         self._raise(load().pmh_set_thresholds(self._h, float(t_c), float(t_c_grid), int(rounds), int(grid_min)))
 
+    def set_limits(self, cap_points: int = 0, max_contenders: int = -1):
+        """Iteration cap of warp-cooperative expansion (0 = default) and contender records kept per
+        item (-1 = default); an item whose contender log overflows is redone in FP64."""
+        self._raise(load().pmh_set_limits(self._h, int(cap_points), int(max_contenders)))
+
+    def sync_status(self, status, stream=None):
+        """Waits for the stream, then (first failing status or 0, counts per code [8], first bad index)."""
+        _check(status, "status", (torch.int32,), self.device)
+        counts = (ctypes.c_int64 * 8)()
+        first = ctypes.c_int64()
+        rc = load().pmh_sync_status(self._h, _ptr(status), status.numel(), counts, ctypes.byref(first),
+                                    _stream(stream))
+        if rc in (ERR_CUDA,) or (rc and first.value < 0):
+            self._raise(rc)
+        return rc, list(counts), first.value
+
     def last_kernel_ms(self):
         """(queue build ms, sketch kernel ms) of the last profiled pmh_sketch_batch call."""
         a, b = ctypes.c_float(), ctypes.c_float()
@@ -278,12 +300,24 @@ class Handle:
                                              _ptr(counts), _stream(stream)))
         return counts
 
-    # -- pmh_estimate_allpairs ---------------------------------------------
-    def estimate_allpairs(self, sigs, upper_only: bool = False, counts=None, stream=None):
+    # -- pmh_estimate_jp ---------------------------------------------------
+    def estimate_jp(self, sigs, upper_only: bool = False, counts=None, stream=None):
+        """Equal-component counts of all signature pairs (int16 view of uint16); J_P estimate = counts / m."""
         _check(sigs, "sigs", _I64, self.device)
         n, m = sigs.shape
         if counts is None:
             counts = torch.zeros((n, n), dtype=torch.int16, device=self.device)   # uint16 storage
+        _check(counts, "counts", (torch.int16, getattr(torch, "uint16", torch.int16)), self.device)
+        rc = load().pmh_estimate_jp(self._h, _ptr(sigs), n, m, 1 if upper_only else 0, _ptr(counts), _stream(stream))
+        self._raise(rc)
+        return counts
+
+    def estimate_allpairs(self, sigs, upper_only: bool = False, counts=None, stream=None):
+        """pmh_estimate_allpairs: the same call as estimate_jp under its earlier name."""
+        _check(sigs, "sigs", _I64, self.device)
+        n, m = sigs.shape
+        if counts is None:
+            counts = torch.zeros((n, n), dtype=torch.int16, device=self.device)
         _check(counts, "counts", (torch.int16, getattr(torch, "uint16", torch.int16)), self.device)
         rc = load().pmh_estimate_allpairs(self._h, _ptr(sigs), n, m, 1 if upper_only else 0, _ptr(counts),
                                           _stream(stream))
@@ -363,6 +397,10 @@ def sketch_batch_noalloc(ids, weights, offsets, m, variants=("1",), precision=FP
     if rc:
         raise PmhError(rc, load().pmh_last_error(None).decode())
     return out_ids, out_q, status
+
+
+def estimate_jp(sigs, upper_only=False, **kw):
+    return handle(sigs.device.index).estimate_jp(sigs, upper_only, **kw)
 
 
 def estimate_allpairs(sigs, upper_only=False, **kw):

@@ -24,9 +24,12 @@ def lib():
 
 
 def test_header_declares_the_boundary():
+    # the calls of the hot path's boundary: handle, batch sketch, estimator counts (all pairs and
+    # listed pairs), merge of partial signatures, status reduction and the resource caps
     names = _declared()
-    for n in ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_estimate_allpairs",
-              "pmh_estimate_pairs", "pmh_merge"):
+    for n in ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_estimate_jp",
+              "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge", "pmh_sync_status", "pmh_set_limits",
+              "pmh_sketch_batch_host", "pmh_sketch_batch_noalloc"):
         assert n in names
 
 
@@ -52,6 +55,12 @@ def test_null_handle_and_bad_arguments_rejected_on_host(lib):
     assert rc == 1   # PMH_ERR_INVALID_ARG
     assert lib.pmh_estimate_allpairs(vp(0), vp(0), ctypes.c_int64(1), ctypes.c_uint32(8), 0, vp(0), vp(0)) == 1
     assert lib.pmh_merge(vp(0), vp(0), vp(0), ctypes.c_int64(1), ctypes.c_uint32(8), vp(0), vp(0), vp(0)) == 1
+    lib.pmh_estimate_jp.restype = ctypes.c_int32
+    assert lib.pmh_estimate_jp(vp(0), vp(0), ctypes.c_int64(1), ctypes.c_uint32(8), 0, vp(0), vp(0)) == 1
+    lib.pmh_sync_status.restype = ctypes.c_int32
+    assert lib.pmh_sync_status(vp(0), vp(0), ctypes.c_int64(1), vp(0), vp(0), vp(0)) == 1
+    lib.pmh_set_limits.restype = ctypes.c_int32
+    assert lib.pmh_set_limits(vp(0), ctypes.c_uint32(0), ctypes.c_int32(-1)) == 1
 
 
 def test_create_without_device_reports_an_error(lib):

@@ -116,6 +116,27 @@ def test_counters_and_repeat_calls(H):
     c = dict(zip(pmh.COUNTERS, cnt.cpu().tolist()))
     assert c["elements"] >= 3 * 6 * 2105      # every positive element is visited at least once per call
     assert c["points32"] > 0
+    assert c["items"] == 3 * 6 * b.num_sets   # each call counts its own items once
+
+
+def test_counters_exclude_autotuning_trials(H):
+    # the first call of a new batch shape runs every team shape twice before its own launch; the
+    # counters report the call's work only, so it equals that of the next (tuned) call
+    from paper_1911_00675_gb300 import pmh
+    b = W.random_batch(13, [300, 40, 7000, 9], 128, "pareto")
+    ids, w, off = to_dev(b)
+    H.set_autotune(-1)
+    try:
+        got = []
+        for _ in range(2):
+            cnt = torch.zeros(len(pmh.COUNTERS), dtype=torch.int64, device="cuda")
+            H.sketch_batch(ids, w, off, 128, ["1", "2", "3", "4"], 1, 0, counters=cnt)
+            torch.cuda.synchronize()
+            got.append(dict(zip(pmh.COUNTERS, cnt.cpu().tolist())))
+        assert got[0]["items"] == got[1]["items"] == 4 * b.num_sets
+        assert got[0]["elements"] == got[1]["elements"]
+    finally:
+        H.set_autotune(1)
 
 
 # --------------------------------------------------------------- full sizes
