@@ -62,6 +62,14 @@ def _load():
             lib.or_offer_run.restype = i32; lib.or_offer_run.argtypes = [u32, vp, vp, vp, i64, vp, vp]
             lib.or_perm_labels.restype = i32; lib.or_perm_labels.argtypes = [u32, u64, u32, vp]
             lib.or_sketch.restype = i32; lib.or_sketch.argtypes = [i32, i32, vp, vp, i64, u32, u64, vp, vp, vp]
+            lib.or_sketch_opt.restype = i32
+            lib.or_sketch_opt.argtypes = [i32, i32, i32, vp, vp, i64, u32, u64, vp, vp, vp]
+            lib.or_near_ties_opt.restype = i64
+            lib.or_near_ties_opt.argtypes = [i32, i32, vp, vp, i64, u32, u64, vp, vp, dbl, vp, vp]
+            lib.or_texp_rej.restype = dbl
+            lib.or_texp_rej.argtypes = [u64, u64, u64, dbl, ctypes.POINTER(ctypes.c_int)]
+            lib.or_rej_consts.restype = None
+            lib.or_rej_consts.argtypes = [dbl, vp]
             lib.or_sketch_batch.restype = i32
             lib.or_sketch_batch.argtypes = [i32, vp, vp, vp, i64, u32, u64, vp, vp, vp]
             lib.or_near_ties.restype = i64
@@ -161,7 +169,10 @@ def perm_labels(m: int, k: int, steps: int):
 
 
 # -- sketches ----------------------------------------------------------------
-def sketch(variant, ids, weights, m: int, seed: int = 0, brute: bool = False):
+TE_REJECTION = 1   # option flag: Exp(lambda;0,1) by the paper's rejection sampler (ProbMinHash3/3a/4)
+
+
+def sketch(variant, ids, weights, m: int, seed: int = 0, brute: bool = False, te_rejection: bool = False):
     """Signature of one weighted set.  Returns (q[m], z[m], stats dict); raises on error codes."""
     v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     ids = _u64(ids)
@@ -169,7 +180,8 @@ def sketch(variant, ids, weights, m: int, seed: int = 0, brute: bool = False):
     q = np.zeros(m)
     z = np.zeros(m, dtype=np.uint64)
     st = np.zeros(5, dtype=np.uint64)
-    rc = _load().or_sketch(v, 1 if brute else 0, _p(ids), _p(w), len(ids), m, seed, _p(q), _p(z), _p(st))
+    rc = _load().or_sketch_opt(v, 1 if brute else 0, TE_REJECTION if te_rejection else 0, _p(ids), _p(w), len(ids),
+                               m, seed, _p(q), _p(z), _p(st))
     if rc:
         raise OracleError(rc)
     stats = dict(zip(("elements", "points", "updates", "buffer_max", "passes"), (int(x) for x in st)))
@@ -200,7 +212,7 @@ def sketch_batch(variant, ids, weights, offsets, m: int, seed: int = 0, with_q: 
     return q, z, st
 
 
-def near_ties(variant, ids, weights, m: int, seed: int, q, z, rel: float = 1e-12):
+def near_ties(variant, ids, weights, m: int, seed: int, q, z, rel: float = 1e-12, te_rejection: bool = False):
     """(flags[m] uint8, runner_up[m]).  Raises if the scan disagrees with (q, z)."""
     v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     ids = _u64(ids)
@@ -209,10 +221,26 @@ def near_ties(variant, ids, weights, m: int, seed: int, q, z, rel: float = 1e-12
     z = _u64(z)
     flags = np.zeros(m, dtype=np.uint8)
     ru = np.zeros(m)
-    rc = _load().or_near_ties(v, _p(ids), _p(w), len(ids), m, seed, _p(q), _p(z), rel, _p(flags), _p(ru))
+    rc = _load().or_near_ties_opt(v, TE_REJECTION if te_rejection else 0, _p(ids), _p(w), len(ids), m, seed, _p(q),
+                                  _p(z), rel, _p(flags), _p(ru))
     if rc < 0:
         raise OracleError(-rc)
     return flags, ru
+
+
+def texp_rej(key: int, i: int, vw: int, lam: float):
+    """(x, attempts): Exp(lam;0,1) by the rejection sampler for point i of the element with `key`,
+    whose value word is vw (attempts = rejection-loop iterations, 0 when the first draw lands in A1)."""
+    att = ctypes.c_int()
+    x = _load().or_texp_rej(key, i, vw, lam, ctypes.byref(att))
+    return x, att.value
+
+
+def rej_consts(lam: float):
+    """(c1, c2, c3) of the rejection sampler for rate lam."""
+    out = np.zeros(3)
+    _load().or_rej_consts(lam, _p(out))
+    return tuple(out)
 
 
 def pminhash(ids, weights, m: int, seed: int = 0):

@@ -27,6 +27,9 @@
  *     work on b-bit minwise hashing) and the collision-corrected estimate
  *   - the binary-weight specialisations of ProbMinHash3, 3a and 4 (Sec.
  *     Conventional Jaccard Similarity): uniform variates, gamma_i = i
+ *   - the rejection sampler for Exp(lambda;0,1) of Sec. Truncated Exponential
+ *     Sampling (Algorithm "Fast generation of random values from
+ *     Exp(lambda;0,1)") as an alternative to inversion for ProbMinHash3/3a/4
  *
  * Readings of the paper taken here:
  *   - Ties: components keep the lexicographic minimum of (value, element id);
@@ -35,9 +38,16 @@
  *     ties order dependent; ties have probability ~0.
  *   - Labels are 0-based internally (paper: 1..m).
  *   - Uniform integers use a multiply-high without rejection.
- *   - Truncated exponentials use inverse-transform sampling, the direct method
- *     the paper gives before its rejection sampler (Sec. Truncated Exponential
- *     Sampling).
+ *   - Truncated exponentials use inverse-transform sampling by default, the
+ *     direct method the paper gives before its rejection sampler (Sec.
+ *     Truncated Exponential Sampling).  With the rejection sampler (flag
+ *     OR_TE_REJECTION) point i's first uniform is its value word; the
+ *     rejection loop's uniforms sit at fixed stream words 2^40 + 256 (i-1) + j
+ *     (attempt t uses j = 2t for x and 2t+1 for y), so consumption stays
+ *     independent of order and precision; after 64 rejected attempts
+ *     (probability below 2^-190) inversion of the value word is used.  The
+ *     last test of the loop compares with expm1(lambda (1 - x)), the paper's
+ *     exp(lambda (1 - x)) - 1.
  *   - Fixed FP64 evaluation order t = b*c, s = a + t, x = w_inv * s; compile
  *     with -ffp-contract=off so no FMA contraction changes the rounding.
  */
@@ -51,6 +61,7 @@ enum { OR_V1 = 0, OR_V1A = 1, OR_V2 = 2, OR_V3 = 3, OR_V3A = 4, OR_V4 = 5,
        /* binary-weight specialisations (Sec. Conventional Jaccard Similarity) */
        OR_V3U = 6, OR_V3AU = 7, OR_V4U = 8 };
 static int is_unweighted(int variant) { return variant == OR_V3U || variant == OR_V3AU || variant == OR_V4U; }
+enum { OR_TE_REJECTION = 1 };   /* option flag: Exp(lambda;0,1) by the paper's rejection sampler */
 
 /* ------------------------------------------------------------------------ */
 /* Random stream.  SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output j of
@@ -102,11 +113,23 @@ typedef struct {
     double *c4, *inv4;         /* expm1(-lambda_i), 1/lambda_i, i = 1..m-1 */
     double delta;              /* 1/lambda_1 */
     int unweighted;            /* binary weights: uniform variates, gamma_i = i */
+    int te_rej;                /* Exp(lambda;0,1) by the rejection sampler */
+    /* rejection sampler constants per rate lambda_i, i = 1..m-1 (ProbMinHash3 uses i = 1):
+     * c1 = (e^lambda - 1)/lambda, c2 = log(2/(1+e^-lambda))/lambda, c3 = (1-e^-lambda)/lambda */
+    double *rl, *rc1, *rc2, *rc3;
 } or_consts;
 
 static void consts_free(or_consts *c)
 {
     free(c->beta); free(c->gamma); free(c->dgamma); free(c->c4); free(c->inv4);
+    free(c->rl); free(c->rc1); free(c->rc2); free(c->rc3);
+}
+
+static void rej_consts(double lambda, double *c1, double *c2, double *c3)
+{
+    *c1 = expm1(lambda) / lambda;
+    *c2 = log(2.0 / (1.0 + exp(-lambda))) / lambda;
+    *c3 = -expm1(-lambda) / lambda;
 }
 
 static int consts_init(or_consts *c, uint32_t m)
@@ -118,7 +141,14 @@ static int consts_init(or_consts *c, uint32_t m)
     c->dgamma = (double *)calloc(m + 1, sizeof(double));
     c->c4 = (double *)calloc(m + 1, sizeof(double));
     c->inv4 = (double *)calloc(m + 1, sizeof(double));
-    if (!c->beta || !c->gamma || !c->dgamma || !c->c4 || !c->inv4) { consts_free(c); return OR_ERR_NO_MEMORY; }
+    c->rl = (double *)calloc(m + 1, sizeof(double));
+    c->rc1 = (double *)calloc(m + 1, sizeof(double));
+    c->rc2 = (double *)calloc(m + 1, sizeof(double));
+    c->rc3 = (double *)calloc(m + 1, sizeof(double));
+    if (!c->beta || !c->gamma || !c->dgamma || !c->c4 || !c->inv4 || !c->rl || !c->rc1 || !c->rc2 || !c->rc3) {
+        consts_free(c);
+        return OR_ERR_NO_MEMORY;
+    }
     for (uint32_t i = 1; i <= m; i++) c->beta[i] = (double)m / (double)(m - i + 1);
     if (m >= 2) {
         c->lambda3 = log1p(1.0 / (double)(m - 1));
@@ -132,6 +162,8 @@ static int consts_init(or_consts *c, uint32_t m)
             c->inv4[i] = 1.0 / li;
             c->gamma[i] = log1p((double)i / (double)(m - i)) / lambda1;
             c->dgamma[i] = c->gamma[i] - c->gamma[i - 1];
+            c->rl[i] = li;
+            rej_consts(li, &c->rc1[i], &c->rc2[i], &c->rc3[i]);
         }
         c->delta = 1.0 / lambda1;
     }
@@ -156,6 +188,58 @@ int or_tables(uint32_t m, double *beta, double *gamma, double *dgamma, double *l
 }
 
 /* ------------------------------------------------------------------------ */
+/* Algorithm "Fast generation of random values from Exp(lambda;0,1)" (Sec.
+ * Truncated Exponential Sampling).  Under the density e^{-lambda x} on [0,1)
+ * the region splits into the rectangle A1 = [0,1) x [0, e^{-lambda}) and the
+ * rest A2.  A draw x = c1 U (c1 = |A1 u A2| / |A1|) below 1 falls in A1 and is
+ * returned as it is.  Otherwise a point of A2 is drawn by rejection, in the
+ * rescaled coordinate y~ = (y - e^{-lambda}) / (1 - e^{-lambda}): x uniform on
+ * [0,1) is accepted at once below c2 (the part of the rectangle
+ * [0,1) x [0, 1/2) under the density); else y~ is uniform on [0, 1/2), a point
+ * above the anti-diagonal is reflected through (1/2, 1/2), and the point is
+ * accepted below the tangent at 0, below the tangent at 1, or below the density
+ * itself.  Returns x; *attempts (optional) the number of rejection attempts. */
+#define TE_REJ_MAX 64
+static uint64_t te_aux_word(uint64_t key, uint64_t i, uint32_t j)
+{
+    return or_word(key, (1ULL << 40) + ((i - 1) << 8) + j);
+}
+
+static double texp_rejection(uint64_t key, uint64_t i, uint64_t vw, double lambda, double c1, double c2, double c3,
+                             int *attempts)
+{
+    if (attempts) *attempts = 0;
+    double x = c1 * or_unif(vw);
+    if (x < 1.0) return x;                                   /* A1 */
+    for (uint32_t t = 0; t < TE_REJ_MAX; t++) {
+        if (attempts) *attempts = (int)t + 1;
+        x = or_unif(te_aux_word(key, i, 2 * t));
+        if (x < c2) return x;                                /* entirely below the density */
+        double y = 0.5 * or_unif(te_aux_word(key, i, 2 * t + 1));
+        if (y > 1.0 - x) { x = 1.0 - x; y = 1.0 - y; }       /* reflection through (1/2, 1/2) */
+        if (x <= c3 * (1.0 - y)) return x;                   /* below the tangent at 0 */
+        if (y * c1 <= 1.0 - x) return x;                     /* below the tangent at 1 */
+        if (y * c1 * lambda <= expm1(lambda * (1.0 - x))) return x;   /* below the density */
+    }
+    return or_texp(vw, expm1(-lambda), 1.0 / lambda);
+}
+
+/* Exposed for tests: one variate of the rejection sampler for rate lambda
+ * (point i of the element with key `key`, value word vw). */
+double or_texp_rej(uint64_t key, uint64_t i, uint64_t vw, double lambda, int *attempts)
+{
+    double c1, c2, c3;
+    rej_consts(lambda, &c1, &c2, &c3);
+    return texp_rejection(key, i, vw, lambda, c1, c2, c3, attempts);
+}
+
+/* Exposed for tests: the sampler's constants for rate lambda. */
+void or_rej_consts(double lambda, double *out3)
+{
+    rej_consts(lambda, &out3[0], &out3[1], &out3[2]);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Point values x_i(d), Sec. Sequence Generation.  For the correlated variants
  * the i-th point is a direct function of i; for the uncorrelated ones it is
  * the running sum of the paper's recursion. */
@@ -166,7 +250,11 @@ int or_tables(uint32_t m, double *beta, double *gamma, double *dgamma, double *l
  * replaced by Uniform([0,1)). */
 static double pmh3_point(const or_consts *c, uint64_t key, double w_inv, uint64_t i)
 {
-    double te = c->unweighted ? or_unif(or_word(key, 2 * i - 2)) : or_texp(or_word(key, 2 * i - 2), c->c3, c->inv3);
+    uint64_t vw = or_word(key, 2 * i - 2);
+    double te;
+    if (c->unweighted) te = or_unif(vw);
+    else if (c->te_rej) te = texp_rejection(key, i, vw, c->rl[1], c->rc1[1], c->rc2[1], c->rc3[1], NULL);
+    else te = or_texp(vw, c->c3, c->inv3);
     double s = (double)(i - 1) + te;
     return w_inv * s;
 }
@@ -182,7 +270,9 @@ static double pmh4_point(const or_consts *c, uint64_t key, double w_inv, uint64_
          * point's delta * Exp(1) become Uniform([0,1)) (Sec. Conventional Jaccard Similarity) */
         s = (double)(i - 1) + or_unif(vw);
     } else if (i < c->m) {
-        double t = c->dgamma[i] * or_texp(vw, c->c4[i], c->inv4[i]);
+        double te = c->te_rej ? texp_rejection(key, i, vw, c->rl[i], c->rc1[i], c->rc2[i], c->rc3[i], NULL)
+                              : or_texp(vw, c->c4[i], c->inv4[i]);
+        double t = c->dgamma[i] * te;
         s = c->gamma[i - 1] + t;
     } else {
         double t = c->delta * or_exp1(vw);
@@ -700,8 +790,8 @@ static int run_brute(int variant, or_sig *s, const or_consts *c, const uint64_t 
 /* Public entry: signature of one weighted set.
  * mode 0: the paper's algorithm for `variant`; mode 1: brute force.
  * Outputs q[m] (component minima, +inf if empty) and z[m] (ids, 0 if empty). */
-int or_sketch(int variant, int mode, const uint64_t *ids, const double *w, int64_t n, uint32_t m, uint64_t seed,
-              double *q_out, uint64_t *z_out, uint64_t *stats_out)
+int or_sketch_opt(int variant, int mode, int flags, const uint64_t *ids, const double *w, int64_t n, uint32_t m,
+                  uint64_t seed, double *q_out, uint64_t *z_out, uint64_t *stats_out)
 {
     if (m < 1 || n < 0 || variant < 0 || variant > 8 || mode < 0 || mode > 1) return OR_ERR_INVALID_ARG;
     if ((variant == OR_V3 || variant == OR_V3A || variant == OR_V4) && m < 2) return OR_ERR_INVALID_ARG;
@@ -711,6 +801,7 @@ int or_sketch(int variant, int mode, const uint64_t *ids, const double *w, int64
     or_stats st;
     memset(&st, 0, sizeof(st));
     if (consts_init(&c, m)) return OR_ERR_NO_MEMORY;
+    c.te_rej = (flags & OR_TE_REJECTION) != 0;
     if (sig_init(&s, m)) { consts_free(&c); return OR_ERR_NO_MEMORY; }
     /* binary weights: every element with w > 0 counts with weight 1 */
     const double *wu = w;
@@ -748,6 +839,12 @@ int or_sketch(int variant, int mode, const uint64_t *ids, const double *w, int64
     return rc;
 }
 
+int or_sketch(int variant, int mode, const uint64_t *ids, const double *w, int64_t n, uint32_t m, uint64_t seed,
+              double *q_out, uint64_t *z_out, uint64_t *stats_out)
+{
+    return or_sketch_opt(variant, mode, 0, ids, w, n, m, seed, q_out, z_out, stats_out);
+}
+
 /* Signatures of a CSR batch of sets (offsets[num_sets+1]), one after another;
  * status[s] receives each set's code.  Single-threaded. */
 int or_sketch_batch(int variant, const uint64_t *ids, const double *w, const int64_t *offsets, int64_t num_sets,
@@ -775,8 +872,19 @@ int or_sketch_batch(int variant, const uint64_t *ids, const double *w, const int
  * flags[k] = 1 when runner-up - q_k < rel * q_k.  Returns the number flagged,
  * or a negative error code.  Also verifies that the scan's minimum equals the
  * given signature (returns -100 if not). */
+int64_t or_near_ties_opt(int variant, int opt, const uint64_t *ids, const double *w, int64_t n, uint32_t m,
+                         uint64_t seed, const double *q, const uint64_t *z, double rel, uint8_t *flags,
+                         double *runner_up);
+
 int64_t or_near_ties(int variant, const uint64_t *ids, const double *w, int64_t n, uint32_t m, uint64_t seed,
                      const double *q, const uint64_t *z, double rel, uint8_t *flags, double *runner_up)
+{
+    return or_near_ties_opt(variant, 0, ids, w, n, m, seed, q, z, rel, flags, runner_up);
+}
+
+int64_t or_near_ties_opt(int variant, int opt, const uint64_t *ids, const double *w, int64_t n, uint32_t m,
+                         uint64_t seed, const double *q, const uint64_t *z, double rel, uint8_t *flags,
+                         double *runner_up)
 {
     if ((variant == OR_V3 || variant == OR_V3A || variant == OR_V4) && m < 2) return -OR_ERR_INVALID_ARG;
     const int unw = is_unweighted(variant);
@@ -788,6 +896,7 @@ int64_t or_near_ties(int variant, const uint64_t *ids, const double *w, int64_t 
     elem_scratch es;
     if (consts_init(&c, m)) return -OR_ERR_NO_MEMORY;
     c.unweighted = unw;
+    c.te_rej = (opt & OR_TE_REJECTION) != 0;
     if (perm_init(&p, m)) { consts_free(&c); return -OR_ERR_NO_MEMORY; }
     if (scratch_init(&es, m)) { perm_free(&p); consts_free(&c); return -OR_ERR_NO_MEMORY; }
     double *b1 = (double *)malloc(sizeof(double) * m), *b2 = (double *)malloc(sizeof(double) * m);

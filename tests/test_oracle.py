@@ -668,3 +668,143 @@ def test_pmh3u_estimator_unbiased_for_jaccard():
         _, zb, _ = oracle.sketch("3u", b, np.ones(20), m, seed=t)
         est.append(oracle.count_equal(za, zb) / m)
     assert abs(np.mean(est) - 1 / 3) < 5 * np.std(est) / np.sqrt(len(est))
+
+
+# ------------------------------------------------- rejection sampler for Exp(lambda;0,1) --
+# Sec. Truncated Exponential Sampling: Exp(lambda;0,1) (density proportional to e^{-lambda x} on
+# [0,1)) drawn without a logarithm: a first uniform scaled by c1 is returned when below 1,
+# otherwise a rejection loop over the region between e^{-lambda} and the density.
+
+RATES = [1e-3, 0.1, 0.5, math.log(2.0)]
+
+
+def _rej_samples(lam, n, salt):
+    xs, att = np.empty(n), np.empty(n, dtype=int)
+    for j in range(n):
+        k = oracle.key(j, salt)
+        xs[j], att[j] = oracle.texp_rej(k, 1 + j % 7, oracle.word(k, 2 * (j % 7)), lam)
+    return xs, att
+
+
+def _te_cdf(lam):
+    return lambda x: -np.expm1(-lam * np.asarray(x)) / -math.expm1(-lam)
+
+
+@pytest.mark.parametrize("lam", RATES)
+def test_texp_rejection_distribution(lam):
+    # the variates follow Exp(lam;0,1): F(x) = (1 - e^{-lam x}) / (1 - e^{-lam})
+    xs, _ = _rej_samples(lam, 20000, 91)
+    assert ((xs >= 0) & (xs < 1)).all()
+    assert stats.kstest(xs, _te_cdf(lam)).pvalue > 1e-4
+
+
+@pytest.mark.parametrize("lam", [0.5, math.log(2.0)])
+def test_texp_rejection_loop_distribution(lam):
+    # the draws that went through the rejection loop follow the region between e^{-lam} and the
+    # density: density proportional to e^{-lam x} - e^{-lam}, CDF
+    # ((1 - e^{-lam x})/lam - x e^{-lam}) / ((1 - e^{-lam})/lam - e^{-lam})
+    xs, att = _rej_samples(lam, 60000, 92)
+    loop = xs[att > 0]
+    assert len(loop) > 5000
+    el = math.exp(-lam)
+    norm = -math.expm1(-lam) / lam - el
+    cdf = lambda x: (-np.expm1(-lam * np.asarray(x)) / lam - np.asarray(x) * el) / norm  # noqa: E731
+    assert stats.kstest(loop, cdf).pvalue > 1e-4
+
+
+@pytest.mark.parametrize("lam", RATES)
+def test_texp_rejection_first_draw_and_attempt_rates(lam):
+    # P(first draw below 1) = lam / (e^lam - 1) (Sec. Truncated Exponential Sampling); one loop
+    # attempt succeeds with the area under the density above e^{-lam} (rescaled to [0,1] in y)
+    # over the sampled rectangle's 1/2, so attempts are geometric with that success rate
+    n = 40000
+    _, att = _rej_samples(lam, n, 93)
+    p1 = lam / math.expm1(lam)
+    hit = np.count_nonzero(att == 0)
+    assert abs(hit - n * p1) < 5 * math.sqrt(n * p1 * (1 - p1)) + 1
+    loop = att[att > 0]
+    if len(loop) > 500:
+        el = math.exp(-lam)
+        p_acc = 2.0 * (-math.expm1(-lam) / lam - el) / (1.0 - el)
+        mean = loop.mean()
+        sd = math.sqrt((1 - p_acc) / p_acc**2 / len(loop))
+        assert abs(mean - 1 / p_acc) < 5 * sd
+
+
+@pytest.mark.parametrize("lam", RATES)
+def test_rejection_constants_fit_the_geometry(lam):
+    # c1 = |A1 u A2| / |A1| (the first draw lands in A1 = [0,1) x [0, e^-lam) with P = 1/c1);
+    # at x = c2 the density, rescaled y~ = (y - e^-lam)/(1 - e^-lam), is exactly 1/2; the
+    # tangent of the rescaled density at 0 meets y~ = 0 at x = c3
+    c1, c2, c3 = oracle.rej_consts(lam)
+    el = math.exp(-lam)
+    area = (1 - el) / lam            # integral of e^{-lam x} over [0, 1)
+    assert c1 == pytest.approx(area / el, rel=1e-13)
+    ytil = lambda x: (math.exp(-lam * x) - el) / (1 - el)  # noqa: E731
+    assert ytil(c2) == pytest.approx(0.5, rel=1e-12)
+    h = 1e-6
+    slope0 = (ytil(h) - ytil(0.0)) / h
+    assert 1.0 / -slope0 == pytest.approx(c3, rel=1e-5)
+
+
+@pytest.mark.parametrize("variant", ["3", "3a", "4"])
+def test_rejection_sampler_early_stop_equals_brute_force(variant):
+    rng = np.random.default_rng(140 + ["3", "3a", "4"].index(variant))
+    for trial in range(30):
+        n = int(rng.integers(1, 80))
+        m = int(rng.integers(2, 70))
+        ids, w = _rand_set(rng, n, ["uniform", "pareto", "lognormal", "unit"][trial % 4])
+        q, z, _ = oracle.sketch(variant, ids, w, m, seed=trial, te_rejection=True)
+        qb, zb, _ = oracle.sketch(variant, ids, w, m, seed=trial, brute=True, te_rejection=True)
+        assert np.array_equal(z, zb) and np.array_equal(q, qb)
+
+
+def test_rejection_sampler_interleaved_equals_sequential_and_order_free():
+    rng = np.random.default_rng(150)
+    for trial in range(12):
+        ids, w = _rand_set(rng, int(rng.integers(1, 2000)), ["uniform", "pareto", "lognormal"][trial % 3])
+        m = int(rng.choice([2, 16, 256]))
+        qa, za, _ = oracle.sketch("3", ids, w, m, seed=trial, te_rejection=True)
+        qb, zb, _ = oracle.sketch("3a", ids, w, m, seed=trial, te_rejection=True)
+        assert np.array_equal(za, zb) and np.array_equal(qa, qb)
+        perm = rng.permutation(len(ids))
+        qc, zc, _ = oracle.sketch("3", ids[perm], w[perm], m, seed=trial, te_rejection=True)
+        assert np.array_equal(za, zc) and np.array_equal(qa, qc)
+
+
+@pytest.mark.parametrize("variant", ["3", "4"])
+def test_rejection_sampler_marginals_and_hash_values(variant):
+    # the exponential race and h_k(d) ~ Exp(lambda w) hold with any exact Exp(lambda;0,1) sampler
+    ids = np.array([11, 22, 33, 44], dtype=np.uint64)
+    w = np.array([1.0, 2.0, 3.0, 4.0])
+    counts = np.zeros(4)
+    for seed in range(400):
+        _, z, _ = oracle.sketch(variant, ids, w, 32, seed=seed, te_rejection=True)
+        for j, d in enumerate(ids):
+            counts[j] += np.count_nonzero(z == d)
+    assert stats.chisquare(counts, w / w.sum() * counts.sum()).pvalue > 1e-6
+    m, wt = 16, 2.5
+    lam = math.log1p(1.0 / (m - 1))
+    vals = [oracle.sketch(variant, np.array([9], dtype=np.uint64), np.array([wt]), m, seed=s,
+                          te_rejection=True)[0][s % m] * lam * wt for s in range(3000)]
+    assert stats.kstest(vals, "expon").pvalue > 1e-4
+
+
+@pytest.mark.parametrize("variant", ["3", "4"])
+def test_rejection_sampler_changes_signatures_and_scan_matches_singletons(variant):
+    # the sampler draws other variates than inversion; the near-tie scan follows the sampler
+    rng = np.random.default_rng(160)
+    ids, w = _rand_set(rng, 40, "pareto")
+    m, seed = 33, 4
+    q0, z0, _ = oracle.sketch(variant, ids, w, m, seed=seed)
+    q, z, _ = oracle.sketch(variant, ids, w, m, seed=seed, te_rejection=True)
+    assert not np.array_equal(q, q0)
+    h = np.array([oracle.sketch(variant, ids[j:j + 1], w[j:j + 1], m, seed=seed, te_rejection=True)[0]
+                  for j in range(len(ids))])
+    flags, ru = oracle.near_ties(variant, ids, w, m, seed, q, z, 3.0, te_rejection=True)
+    bound = q.max() * 4.0
+    for k in range(m):
+        order = np.lexsort((ids, h[:, k]))
+        assert ids[order[0]] == z[k] and h[order[0], k] == q[k]
+        second = h[order[1], k]
+        assert ru[k] == (second if second <= bound else np.inf)
