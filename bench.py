@@ -206,6 +206,34 @@ def alu_peak(n_sms, sm_mhz):
 
 
 # ------------------------------------------------------------------ secondary kernels
+def te_sampler_comparison(h, ids, w, off, m, work_per_variant, steps=5):
+    """ProbMinHash3/3a/4 on the headline batch with Exp(lambda;0,1) by inversion (the default) and by
+    the paper's rejection sampler (Sec. Truncated Exponential Sampling): device time of the sketch
+    kernels from the library's events, FP32 candidates + FP64 recheck."""
+    import statistics
+
+    from paper_1911_00675_gb300 import pmh
+    vs = ["3", "3a", "4"]
+    out = {"workload": "the headline batch, variants 3, 3a, 4 (FP32 + recheck)"}
+    h.set_profiling(True)
+    try:
+        for name, mode in (("inversion", pmh.TE_INVERSION), ("rejection", pmh.TE_REJECTION)):
+            h.set_te_sampler(mode)
+            for _ in range(2):
+                _, _, st = h.sketch_batch(ids, w, off, m, vs, pmh.FP32_RECHECK, 0)
+            for _ in range(steps):
+                _, _, st = h.sketch_batch(ids, w, off, m, vs, pmh.FP32_RECHECK, 0)
+            k = h.kernel_ms_history(steps)[1]
+            ms = statistics.mean(k)
+            out[name] = {"sketch_kernel_ms": ms, "elements_per_s": 3 * work_per_variant / (ms * 1e-3),
+                         "status_ok": bool((st == 0).all().item())}
+    finally:
+        h.set_te_sampler(pmh.TE_INVERSION)
+        h.set_profiling(False)
+    out["speedup_rejection_vs_inversion"] = out["inversion"]["sketch_kernel_ms"] / out["rejection"]["sketch_kernel_ms"]
+    return out
+
+
 def secondary(h, dev, n_sms, sm_mhz, peaks, steps=3):
     """Per-kernel measurements beside the headline: the precision config (FP32 + recheck against FP64
     at m = 4096), grid mode on one huge set (HBM-bound) and the all-pairs equal-component count
@@ -600,6 +628,7 @@ def main():
     sec_res = None
     if not args.no_secondary:
         sec_res = secondary(h, dev, n_sms, sm_mhz, peaks)
+        sec_res["te_sampler"] = te_sampler_comparison(h, ids, w, off, m, n_elem)
 
     # ---------------- CPU baseline (rank 0, N=1 only), and the GPU's point work on the same tasks
     cpu = None

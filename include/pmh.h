@@ -219,7 +219,7 @@ pmh_status pmh_last_host_span_ms(pmh_handle h, float *ms, int32_t *chunks);
  * is off: a set of 2^20 elements or more is sketched by one team instead of
  * the whole GPU (same result, far slower).  Its scratch memory (constant
  * tables, work queue, FP64 redo list, per-set statistics) is one fixed array
- * of about 5.6 MiB that every GPU holds for as long as the library is loaded;
+ * of about 6 MiB that every GPU holds for as long as the library is loaded;
  * the call itself allocates and frees no device memory and builds no CUDA
  * graph.  Limits: num_sets <= PMH_NOALLOC_MAX_SETS and
  * num_sets * num_variants <= PMH_NOALLOC_MAX_ITEMS; larger batches return
@@ -349,6 +349,27 @@ pmh_status pmh_set_thresholds(pmh_handle h, double t_c, double t_c_grid, int32_t
 pmh_status pmh_set_limits(pmh_handle h, uint32_t cap_points, int32_t max_contenders);
 
 /*
+ * pmh_set_te_sampler -- how later pmh_sketch_batch calls on `h` draw the
+ * truncated exponentials Exp(lambda;0,1) of ProbMinHash3/3a/4 (weighted
+ * variants; the binary-weight ones draw uniforms either way).
+ *   PMH_TE_INVERSION (default): -log1p(U expm1(-lambda)) / lambda, U from
+ *     point i's value word (stream word 2i-2).
+ *   PMH_TE_REJECTION: Algorithm "Fast generation of random values from
+ *     Exp(lambda;0,1)" (Sec. Truncated Exponential Sampling): x = c1 U with
+ *     c1 = (e^lambda - 1)/lambda from the same value word, returned when below
+ *     1; otherwise the paper's rejection loop, whose uniforms are stream words
+ *     2^40 + 256 (i-1) + j (attempt t: j = 2t, 2t+1), so that the draws do not
+ *     depend on order or precision.  After 64 rejected attempts (probability
+ *     below 2^-190) the inversion of the value word is used.
+ * The two samplers give different (equally distributed) signatures; both
+ * precisions give the same signature for either.  Errors: PMH_ERR_INVALID_ARG
+ * for NULL h or another value.
+ */
+#define PMH_TE_INVERSION 0
+#define PMH_TE_REJECTION 1
+pmh_status pmh_set_te_sampler(pmh_handle h, int32_t sampler);
+
+/*
  * pmh_bbit_reduce -- Algorithm "Reduction to a b-bit signature": component k
  * (0-based) of every signature keeps the least significant b bits of a hash
  * of the pair (z_k, k): mix(z_k ^ mix(mix(seed) + (k+1) phi)), mix the
@@ -421,6 +442,27 @@ pmh_status pmh_estimate_allpairs(pmh_handle h, const uint64_t *sigs, int64_t num
 pmh_status pmh_estimate_pairs(pmh_handle h, const uint64_t *sig_a, const uint64_t *sig_b, const int64_t *pairs_a,
                               const int64_t *pairs_b, int64_t num_pairs, uint32_t m, uint32_t *counts,
                               void *stream);
+
+/*
+ * pmh_pminhash_batch -- Algorithm P-MinHash (the paper's reference method for
+ * J_P, Sec. Probability Jaccard Similarity): for every element d with
+ * w(d) > 0 and every component k, h_k(d) = Exp(1)/w(d) from word k (0-based)
+ * of the element's stream (key mix(id ^ mix(seed)), word_k = mix(key + (k+1)
+ * phi), Exp(1) = -log1p(-U)); component k keeps the lexicographically smallest
+ * (h_k(d), d).  No early stop: n m hash values per set.  For comparison with
+ * the ProbMinHash algorithms, which reach signatures of the same distribution
+ * with far fewer values for large n.
+ *   ids, weights, offsets, num_sets, m (1..PMH_MAX_M), seed: as pmh_sketch_batch.
+ *   out_ids   device uint64[num_sets * m]; out_q device float64[same] or NULL
+ *             (exact FP64 minima); set_status device int32[num_sets] or NULL.
+ * Candidates are screened in FP32 and compared exactly in FP64, so the result
+ * is that of an all-FP64 evaluation.  Empty sets: ids 0, q +inf.  Errors: as
+ * pmh_sketch_batch (bad weights per set in set_status).  Asynchronous on
+ * `stream`; a 4-byte device counter stays with the handle.
+ */
+pmh_status pmh_pminhash_batch(pmh_handle h, const uint64_t *ids, const double *weights, const int64_t *offsets,
+                              int64_t num_sets, uint32_t m, uint64_t seed, uint64_t *out_ids, double *out_q,
+                              int32_t *set_status, void *stream);
 
 /*
  * pmh_merge -- signature of a union of disjoint sets from the signatures of

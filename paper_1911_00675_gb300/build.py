@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpmh.so")
-SOURCES = ["api.cu", "noalloc.cu", "sketch_dispatch.cu"] + [f"sketch_{p}_f{f}.cu" for p in ("f32", "f64") for f in (1, 2, 3, 4)]
+SOURCES = ["api.cu", "noalloc.cu", "pminhash.cu", "sketch_dispatch.cu"] + [f"sketch_{p}_f{f}.cu" for p in ("f32", "f64") for f in (1, 2, 3, 4)]
 HEADERS = ["pmh_device.cuh", "sketch_kernel.cuh", "sketch_inst.cuh", "launch.h", "batch_common.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",

@@ -100,6 +100,7 @@ struct pmh_handle_s {
     std::map<TuneKey, int> tuned;            // best TeamShape per key
     cudaEvent_t tev[3 + 4] = {};             // autotuning: queue/sketch brackets + one per family
     unsigned long long *status_scratch = nullptr;   // pmh_sync_status: 8 counts + the first failing (index, code)
+    unsigned int *pm_counter = nullptr;              // pmh_pminhash_batch: the blocks' set counter
     // profiling events
     bool profiling = false;
     bool prof_recorded = false;        // the most recent call was profiled
@@ -255,6 +256,7 @@ extern "C" void pmh_destroy(pmh_handle h) {
     for (int i = 0; i < 7; i++) if (h->tev[i]) cudaEventDestroy(h->tev[i]);
     for (auto &kv : h->tables) cudaFree(kv.second.dev);
     if (h->status_scratch) cudaFree(h->status_scratch);
+    if (h->pm_counter) cudaFree(h->pm_counter);
     for (Workspace &w : h->ws) {
         if (w.queue) cudaFree(w.queue);
         if (w.qmeta) cudaFree(w.qmeta);
@@ -310,6 +312,16 @@ extern "C" pmh_status pmh_set_limits(pmh_handle h, uint32_t cap_points, int32_t 
         return fail(h, PMH_ERR_INVALID_ARG, "max_contenders = %d outside [-1, %d]", max_contenders, kGridCont);
     h->th.cap_points = cap_points;
     h->th.max_cont = max_contenders;
+    h->graph_valid = false;
+    return PMH_OK;
+}
+
+extern "C" pmh_status pmh_set_te_sampler(pmh_handle h, int32_t sampler) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    if (sampler != PMH_TE_INVERSION && sampler != PMH_TE_REJECTION)
+        return fail(h, PMH_ERR_INVALID_ARG, "sampler %d is neither PMH_TE_INVERSION nor PMH_TE_REJECTION", sampler);
+    h->th.te_rej = sampler == PMH_TE_REJECTION;
     h->graph_valid = false;
     return PMH_OK;
 }
@@ -876,6 +888,26 @@ extern "C" pmh_status pmh_estimate_jp(pmh_handle h, const uint64_t *sigs, int64_
 extern "C" pmh_status pmh_estimate_allpairs(pmh_handle h, const uint64_t *sigs, int64_t num_sigs, uint32_t m,
                                             int32_t upper_only, uint16_t *counts, void *stream) {
     return pmh_estimate_jp(h, sigs, num_sigs, m, upper_only, counts, stream);
+}
+
+// ------------------------------------------------------------------ P-MinHash
+extern "C" pmh_status pmh_pminhash_batch(pmh_handle h, const uint64_t *ids, const double *weights,
+                                         const int64_t *offsets, int64_t num_sets, uint32_t m, uint64_t seed,
+                                         uint64_t *out_ids, double *out_q, int32_t *set_status, void *stream) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    if (num_sets < 0) return fail(h, PMH_ERR_INVALID_ARG, "num_sets < 0");
+    if (m < 1 || m > PMH_MAX_M) return fail(h, PMH_ERR_UNSUPPORTED, "m = %u outside [1, %u]", m, PMH_MAX_M);
+    if (num_sets == 0) return PMH_OK;
+    if (!ids || !weights || !offsets || !out_ids) return fail(h, PMH_ERR_INVALID_ARG, "NULL ids/weights/offsets/out_ids");
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    if (!h->pm_counter) CUDA_TRY(h, cudaMalloc(&h->pm_counter, sizeof(unsigned int)));
+    bool fits = true;
+    cudaError_t e = pminhash_launch(ids, weights, offsets, num_sets, m, seed, out_ids, out_q, set_status, h->pm_counter,
+                                    h->sm_count, (cudaStream_t)stream, &fits);
+    if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "P-MinHash launch: %s", cudaGetErrorString(e));
+    if (!fits) return fail(h, PMH_ERR_UNSUPPORTED, "m = %u does not fit in shared memory", m);
+    return PMH_OK;
 }
 
 // ------------------------------------------------------------------ status reduction

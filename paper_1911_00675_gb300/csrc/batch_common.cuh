@@ -17,9 +17,12 @@ namespace pmh {
 // Per-m constants of Sec. ProbMinHash2/3/4 in FP64 (host libm), plus FP32
 // copies for the filter: five FP64 arrays then five FP32 arrays of m+1 entries,
 // then (16-byte aligned) the ProbMinHash4 FP32 constants of each point packed
-// in one float4.
+// in one float4, then the rejection sampler's constants per rate (Sec.
+// Truncated Exponential Sampling): k1, k2 (u64), c1, c3, lambda (FP64) and c1
+// in FP32, m+1 entries each.
 constexpr size_t table_f4_off(uint32_t m) { return ((5 * ((size_t)m + 1) * (sizeof(double) + sizeof(float))) + 15) & ~(size_t)15; }
-constexpr size_t table_bytes(uint32_t m) { return table_f4_off(m) + ((size_t)m + 1) * 16; }
+constexpr size_t table_rej_off(uint32_t m) { return table_f4_off(m) + ((size_t)m + 1) * 16; }
+constexpr size_t table_bytes(uint32_t m) { return table_rej_off(m) + ((size_t)m + 1) * (5 * 8 + 4); }
 
 // Fills `host` (table_bytes(m) bytes) and sets `out` to point into the same
 // layout at device address `dev`.
@@ -84,6 +87,46 @@ inline void build_tables(uint32_t m, unsigned char *host, const void *dev, Table
     if ((double)lo32 > lo) lo32 = std::nextafterf(lo32, 0.0f);
     t.te_lo = lo32;
     t.lambda1_32 = (float)lambda1;
+
+    // rejection sampler constants, i = 1..m-1 (entry i for the rate lambda_i; ProbMinHash3 uses i = 1)
+    uint64_t *k1 = (uint64_t *)(host + table_rej_off(m)), *k2 = k1 + n;
+    double *rc1 = (double *)(k2 + n), *rc3 = rc1 + n, *rlam = rc3 + n;
+    float *rc1f = (float *)(rlam + n);
+    for (size_t i = 0; i < n; i++) { k1[i] = 0; k2[i] = 0; rc1[i] = 0.0; rc3[i] = 0.0; rlam[i] = 0.0; rc1f[i] = 0.0f; }
+    for (uint32_t i = 1; i < m; i++) {
+        const double l = std::log1p(1.0 / (double)(m - i));
+        const double c1 = std::expm1(l) / l;
+        const double c2 = std::log(2.0 / (1.0 + std::exp(-l))) / l;
+        const double c3 = -std::expm1(-l) / l;
+        // smallest k with fl(fl(k 2^-53) c1) >= 1: the product is monotone in k
+        uint64_t lo_k = 0, hi_k = 1ull << 53;
+        while (lo_k < hi_k) {
+            const uint64_t mid = lo_k + (hi_k - lo_k) / 2;
+            const double u = (double)mid * 0x1p-53;
+            if (c1 * u >= 1.0) hi_k = mid; else lo_k = mid + 1;
+        }
+        k1[i] = lo_k;
+        k2[i] = (uint64_t)std::ceil(std::ldexp(c2, 53));
+        rc1[i] = c1;
+        rc3[i] = c3;
+        rlam[i] = l;
+        rc1f[i] = (float)c1;
+    }
+    t.rej_k1 = (const uint64_t *)(d + table_rej_off(m));
+    t.rej_k2 = t.rej_k1 + n;
+    t.rej_c1 = (const double *)(t.rej_k2 + n);
+    t.rej_c3 = t.rej_c1 + n;
+    t.rej_lam = t.rej_c3 + n;
+    t.rej_c1_32 = (const float *)(t.rej_lam + n);
+    // filter at point 1: a 23-bit lower bound ulo of U with ulo < u1 guarantees U < k1 2^-53
+    // (U < ulo + 2^-23); u1 = the largest float at most k1 2^-53 - 2^-23
+    t.rej_u1_32 = 0.0f;
+    if (m >= 2) {
+        const double lim = (double)k1[1] * 0x1p-53 - 0x1p-23;
+        float u1 = (float)lim;
+        if ((double)u1 > lim) u1 = std::nextafterf(u1, 0.0f);
+        t.rej_u1_32 = lim > 0.0 ? u1 : 0.0f;
+    }
 }
 
 inline uint64_t host_mix64(uint64_t z) {
@@ -521,6 +564,7 @@ struct Thresholds {
     int64_t grid_min = kGridMinDefault;
     uint32_t cap_points = 0;   // points per element in warp-cooperative expansion (0: 64 m ln(m+1) + 4096)
     int max_cont = -1;         // contender records per team / grid item (-1: kMaxCont / kGridCont)
+    bool te_rej = false;       // ProbMinHash3/3a/4: Exp(lambda;0,1) by the rejection sampler instead of inversion
 };
 
 // Kernel launches of one enqueue_batch call (fixed by the plan).
@@ -556,6 +600,7 @@ inline void fill_params(SketchParams *p, const uint64_t *ids, const double *weig
     p->redo_count = nullptr;
     p->redo_cap = 0;
     p->queue_len_dev = nullptr;
+    p->te_rej = th.te_rej;
     p->t_factor_grid = (float)(std::log((double)m) + th.t_c_grid);
     p->grid_min = th.grid_min;
     p->gctl = nullptr;

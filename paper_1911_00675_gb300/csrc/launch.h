@@ -46,6 +46,11 @@ cudaError_t sketch_launch(const LaunchShape &s, int grid, const SketchParams &p,
 // Records the message returned by pmh_last_error(NULL) on this host thread.
 void set_thread_error(const char *msg);
 
+// Algorithm P-MinHash over a CSR batch (pminhash.cu).
+cudaError_t pminhash_launch(const uint64_t *ids, const double *weights, const int64_t *offsets, int64_t num_sets,
+                            uint32_t m, uint64_t seed, uint64_t *out_ids, double *out_q, int32_t *set_status,
+                            unsigned int *set_counter, int sm_count, cudaStream_t st, bool *fits);
+
 // Grid-mode kernel of one (precision, family): a CTA-team launch shape.
 template <bool F32, int FAM>
 cudaError_t grid_shape(uint32_t m, LaunchShape *out);

@@ -21,7 +21,7 @@ namespace {
 
 // Scratch layout: tables for m <= PMH_MAX_M | queue metadata | work queue | FP64 redo list (items whose
 // contender log overflowed) | per-set statistics.
-constexpr size_t kTableRegion = 640u * 1024u;                                  // >= table_bytes(PMH_MAX_M)
+constexpr size_t kTableRegion = 1024u * 1024u;                                 // >= table_bytes(PMH_MAX_M)
 static_assert(kTableRegion >= table_bytes(PMH_MAX_M), "table region too small");
 constexpr size_t kMetaRegion = 16384;                                           // >= kQMetaWords * 4
 constexpr size_t kQueueRegion = (size_t)PMH_NOALLOC_MAX_ITEMS * sizeof(uint64_t);
@@ -109,7 +109,7 @@ extern "C" pmh_status pmh_sketch_batch_noalloc(const uint64_t *ids, const double
     uint64_t *redo = (uint64_t *)(base + kTableRegion + kMetaRegion + kQueueRegion);
     SetStat *stats = (SetStat *)(base + kTableRegion + kMetaRegion + 2 * kQueueRegion);
 
-    // The tables of this m are uploaded on every call (76 KiB at m = 1024), in stream order before
+    // The tables of this m are uploaded on every call (120 KiB at m = 1024), in stream order before
     // the kernels: nothing on the host has to know what the array held before.  The copy from this
     // pageable buffer has read it by the time cudaMemcpyAsync returns, so the next call may refill it.
     Tables tab;

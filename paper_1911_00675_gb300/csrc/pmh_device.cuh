@@ -59,6 +59,14 @@ struct Tables {
     float c3_32, inv3_32, delta32;
     float te_lo;            // (1-e^{-lambda_1})/lambda_1 rounded down: Exp(lambda_1;0,1) >= U * te_lo
     float lambda1_32;       // lambda_1 = log(1 + 1/(m-1))
+    // Rejection sampler for Exp(lambda_i;0,1) (Sec. Truncated Exponential Sampling), i = 1..m-1
+    // (ProbMinHash3 uses i = 1): c1 = (e^l - 1)/l, c3 = (1 - e^-l)/l, the rate l itself; k1 = the
+    // smallest 53-bit k with fl(k 2^-53 c1) >= 1 (the first draw c1 U lands below 1 iff U's 53-bit
+    // integer is below k1); k2 = ceil(c2 2^53), c2 = log(2/(1+e^-l))/l (U < c2 iff k < k2)
+    const uint64_t *rej_k1, *rej_k2;
+    const double *rej_c1, *rej_c3, *rej_lam;
+    const float *rej_c1_32;
+    float rej_u1_32;        // filter: a 23-bit uniform below this has k < k1 at point 1 (else TE may be ~0)
 };
 
 // ------------------------------------------------------------------ stream
@@ -120,6 +128,52 @@ __device__ __forceinline__ double point_unw_64(uint64_t vw, uint64_t i, double w
 __device__ __forceinline__ double lower3_64(uint64_t i, double w_inv) { return __dmul_rn(w_inv, (double)(i - 1)); }
 __device__ __forceinline__ double lower4_64(const Tables &T, uint32_t i, double w_inv) {
     return __dmul_rn(w_inv, T.gamma[i - 1]);
+}
+
+// ------------------------------------------------ Exp(lambda;0,1) by rejection
+// Algorithm "Fast generation of random values from Exp(lambda;0,1)" (Sec.
+// Truncated Exponential Sampling), point i of an element with stream key
+// `key`, table index ti (the rate lambda_ti).  The first uniform is the value
+// word vw: c1 U below 1 is returned as it is (the rectangle under e^-lambda).
+// Otherwise the rejection loop draws from the region between e^-lambda and
+// the density; its uniforms are stream words 2^40 + 256 (i-1) + j (attempt t:
+// j = 2t for x, 2t+1 for y), and after 64 rejected attempts (probability below
+// 2^-190) the inversion of vw is returned.  The loop's uniforms are exact in
+// FP64 and so are 1 - x and 1 - y; the comparisons are evaluated in FP64 with
+// every operation rounded on its own, so both precisions return the same value.
+constexpr int kTeRejMax = 64;
+__device__ __forceinline__ uint64_t te_aux_word(uint64_t key, uint64_t i, uint32_t j) {
+    return mix64(key + ((1ull << 40) + ((i - 1) << 8) + (uint64_t)j + 1ull) * kPhi);
+}
+static __device__ __noinline__ double texp_rej_loop(const Tables &T, uint32_t ti, uint64_t key, uint64_t i, uint64_t vw) {
+    const double c1 = T.rej_c1[ti], c3 = T.rej_c3[ti], lam = T.rej_lam[ti];
+    const uint64_t k2 = T.rej_k2[ti];
+    for (int t = 0; t < kTeRejMax; ++t) {
+        const uint64_t kx = te_aux_word(key, i, 2u * t) >> 11;
+        double x = __dmul_rn((double)kx, 0x1p-53);
+        if (kx < k2) return x;                                        // below c2: under the density
+        double y = __dmul_rn(0.5, unif53(te_aux_word(key, i, 2u * t + 1u)));
+        if (y > __dsub_rn(1.0, x)) { x = __dsub_rn(1.0, x); y = __dsub_rn(1.0, y); }   // reflection
+        if (x <= __dmul_rn(c3, __dsub_rn(1.0, y))) return x;          // below the tangent at 0
+        const double yc = __dmul_rn(y, c1);
+        if (yc <= __dsub_rn(1.0, x)) return x;                        // below the tangent at 1
+        if (__dmul_rn(yc, lam) <= expm1(__dmul_rn(lam, __dsub_rn(1.0, x)))) return x;   // below the density
+    }
+    return texp_64(vw, T.c4[ti], T.inv4[ti]);
+}
+__device__ __forceinline__ double texp_rej_64(const Tables &T, uint32_t ti, uint64_t key, uint64_t i, uint64_t vw) {
+    if ((vw >> 11) < T.rej_k1[ti]) return __dmul_rn(unif53(vw), T.rej_c1[ti]);
+    return texp_rej_loop(T, ti, key, i, vw);
+}
+// F3 / F4 points with the rejection sampler (same order of operations as point3_64 / point4_64)
+__device__ __forceinline__ double point3r_64(const Tables &T, uint64_t key, uint64_t vw, uint64_t i, double w_inv) {
+    const double s = __dadd_rn((double)(i - 1), texp_rej_64(T, 1, key, i, vw));
+    return __dmul_rn(w_inv, s);
+}
+__device__ __forceinline__ double point4r_64(const Tables &T, uint64_t key, uint64_t vw, uint32_t i, double w_inv) {
+    if (i >= T.m) return point4_64(T, vw, i, w_inv);   // the last point uses delta * Exp(1)
+    const double t = __dmul_rn(T.dgamma[i], texp_rej_64(T, i, key, i, vw));
+    return __dmul_rn(w_inv, __dadd_rn(T.gamma[i - 1], t));
 }
 
 // ------------------------------------------------------------ FP32 (filter)
@@ -186,6 +240,14 @@ __device__ __forceinline__ float texp_32(uint64_t w, float c, float inv) {
     const float x = __fmul_rn(u53_to_float(w >> 11), c);
     const float l = x >= -0.29289321f ? log1p_reduced(x) : log1pf(x);
     return __fmul_rn(-l, inv);
+}
+// FP32 candidate of the rejection sampler: the first draw c1 U (u53_to_float of U
+// within 2u, c1 rounded to FP32 within u/2, one product rounding: below 4u of the
+// FP64 value), or the FP64 loop's value rounded once.
+__device__ __forceinline__ float texp_rej_32(const Tables &T, uint32_t ti, uint64_t key, uint64_t i, uint64_t vw) {
+    const uint64_t k = vw >> 11;
+    if (k < T.rej_k1[ti]) return __fmul_rn(u53_to_float(k), T.rej_c1_32[ti]);
+    return __double2float_rn(texp_rej_loop(T, ti, key, i, vw));
 }
 // A positive, finite weight (the item's weights are validated before use):
 // the sign bit is clear and the bits are not all zero (rejects +-0).

@@ -1,5 +1,8 @@
 // Instantiation of the persistent sketch kernel for one (precision, family);
 // included by sketch_<precision>_f<family>.cu with PMH_F32 and PMH_FAM defined.
+// ProbMinHash3/3a/4 also get kernels drawing Exp(lambda;0,1) with the
+// rejection sampler (REJ = true), launched when the call asks for it, so that
+// the default kernels carry none of its code.
 #include "launch.h"
 
 namespace pmh {
@@ -20,14 +23,25 @@ cudaError_t shape_impl(uint32_t m, LaunchShape *out) {
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     if (L.total > (size_t)optin) return cudaSuccess;
-    auto kern = sketch_kernel<PMH_F32, NW, TW, MINB, PMH_FAM>;
+    auto kern = sketch_kernel<PMH_F32, NW, TW, MINB, PMH_FAM, false>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
+    if constexpr (PMH_FAM >= 3) {
+        e = cudaFuncSetAttribute(sketch_kernel<PMH_F32, NW, TW, MINB, PMH_FAM, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+        if (e != cudaSuccess) return e;
+    }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->blocks_per_sm, kern, NW * 32, L.total);
 }
 template <int S>
 void launch_impl(const LaunchShape &s, int grid, const SketchParams &p, cudaStream_t st) {
-    sketch_kernel<PMH_F32, shape_nw(S), shape_tw(S), shape_minb(S), PMH_FAM><<<grid, s.block, s.smem, st>>>(p);
+    if constexpr (PMH_FAM >= 3) {
+        if (p.te_rej) {
+            sketch_kernel<PMH_F32, shape_nw(S), shape_tw(S), shape_minb(S), PMH_FAM, true><<<grid, s.block, s.smem, st>>>(p);
+            return;
+        }
+    }
+    sketch_kernel<PMH_F32, shape_nw(S), shape_tw(S), shape_minb(S), PMH_FAM, false><<<grid, s.block, s.smem, st>>>(p);
 }
 }  // namespace
 
@@ -70,15 +84,26 @@ cudaError_t grid_shape<PMH_F32, PMH_FAM>(uint32_t m, LaunchShape *out) {
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     if (L.total > (size_t)optin) return cudaSuccess;
-    auto kern = grid_kernel<PMH_F32, PMH_FAM>;
+    auto kern = grid_kernel<PMH_F32, PMH_FAM, false>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
+    if constexpr (PMH_FAM >= 3) {
+        e = cudaFuncSetAttribute(grid_kernel<PMH_F32, PMH_FAM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)L.total);
+        if (e != cudaSuccess) return e;
+    }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->blocks_per_sm, kern, 256, L.total);
 }
 
 template <>
 cudaError_t grid_launch<PMH_F32, PMH_FAM>(const LaunchShape &s, int grid, const SketchParams &p, cudaStream_t st) {
-    grid_kernel<PMH_F32, PMH_FAM><<<grid, s.block, s.smem, st>>>(p);
+    if constexpr (PMH_FAM >= 3) {
+        if (p.te_rej) {
+            grid_kernel<PMH_F32, PMH_FAM, true><<<grid, s.block, s.smem, st>>>(p);
+            return cudaGetLastError();
+        }
+    }
+    grid_kernel<PMH_F32, PMH_FAM, false><<<grid, s.block, s.smem, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -123,6 +123,7 @@ struct SketchParams {
     unsigned int *redo_count;
     int64_t redo_cap;
     const unsigned int *queue_len_dev;   // FP64 redo launch: the queue's length in device memory (else null)
+    bool te_rej;                  // ProbMinHash3/3a/4: Exp(lambda;0,1) by the rejection sampler
     // grid mode (null when disabled)
     GridCtl *gctl;
     GridState *gstate;            // [4][kMaxGrid]
@@ -197,6 +198,7 @@ struct Ctx {
     unsigned int *gbound32;        // grid mode: the item's bound shared by all CTAs (float bits), else null
     unsigned long long *gbound64;  //   and its FP64 bound (double bits)
     bool unw;                      // binary-weight variant: w_inv = 1, uniform variates, gamma_i = i
+    bool rej;                      // weighted ProbMinHash3/3a/4 with Exp(lambda;0,1) by the rejection sampler
 };
 
 __device__ __forceinline__ float ld_volatile(const float *p) { return *(volatile const float *)p; }
@@ -364,7 +366,7 @@ __device__ __forceinline__ double shfl_d(double v, int src) {
 // Warp-cooperative expansion of one element from point 1, 32 points per step.
 // EXACT = false: offer points <= bound.  EXACT = true (exact search): stop at
 // the first point with label `want` and return its canonical FP64 value.
-template <int FAM, bool F32, bool EXACT>
+template <int FAM, bool F32, bool EXACT, bool REJ>
 __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
     const SketchParams &P = *c.p;
     const Tables &T = P.tab;
@@ -431,6 +433,7 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
             } else if (hit) {
                 int src = __ffs(hit) - 1;
                 if (lane == src) x = c.unw ? point_unw_64(vw, i, w_inv)
+                                     : (REJ && c.rej) ? ((FAM == 3) ? point3r_64(T, key, vw, i, w_inv) : point4r_64(T, key, vw, i, w_inv))
                                            : (FAM == 3) ? point3_64(T, vw, i, w_inv) : point4_64(T, vw, i, w_inv);
             }
             if (hit) return __shfl_sync(kFull, x, __ffs(hit) - 1);
@@ -457,12 +460,13 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
             } else if (c.unw) {
                 x32 = act ? __fmul_rn(winv32, __fadd_rn((float)(i - 1), u53_to_float(vw >> 11))) : 0.0f;
             } else if (FAM == 3) {
-                x32 = act ? __fmul_rn(winv32, __fadd_rn((float)(i - 1), texp_32(vw, T.c3_32, T.inv3_32))) : 0.0f;
+                const float te = (REJ && c.rej) ? texp_rej_32(T, 1, key, i, vw) : texp_32(vw, T.c3_32, T.inv3_32);
+                x32 = act ? __fmul_rn(winv32, __fadd_rn((float)(i - 1), te)) : 0.0f;
             } else {
                 float sv = 0.0f;
                 if (act) {
                     const float4 q = T.p4[i];
-                    if (i < m) sv = __fadd_rn(q.x, __fmul_rn(q.y, texp_32(vw, q.z, q.w)));
+                    if (i < m) sv = __fadd_rn(q.x, __fmul_rn(q.y, (REJ && c.rej) ? texp_rej_32(T, i, key, i, vw) : texp_32(vw, q.z, q.w)));
                     else sv = __fadd_rn(q.x, __fmul_rn(T.delta32, exp1_32(vw)));
                 }
                 x32 = __fmul_rn(winv32, sv);
@@ -488,9 +492,9 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
             } else if (c.unw) {
                 x = act ? point_unw_64(vw, i, w_inv) : 0.0;
             } else if (FAM == 3) {
-                x = act ? point3_64(T, vw, i, w_inv) : 0.0;
+                x = act ? ((REJ && c.rej) ? point3r_64(T, key, vw, i, w_inv) : point3_64(T, vw, i, w_inv)) : 0.0;
             } else {
-                x = act ? point4_64(T, vw, i, w_inv) : 0.0;
+                x = act ? ((REJ && c.rej) ? point4r_64(T, key, vw, i, w_inv) : point4_64(T, vw, i, w_inv)) : 0.0;
             }
             if (P.counters) count(c, PMH_CNT_POINTS64, popc_ballot(act));
             const bool beyond = x > ld_volatile(&c.ts->bound64);
@@ -514,16 +518,16 @@ __device__ double deep(Ctx<F32> &c, uint32_t e, uint32_t want) {
 
 // Exact FP64 value of h_k(e) (the first point of element e with label k).
 // Cold path (contender resolution, exact q output): kept out of line.
-template <int FAM, bool F32>
+template <int FAM, bool F32, bool REJ>
 __device__ __noinline__ double exact_h(Ctx<F32> c, uint32_t e, uint32_t k) {
-    return deep<FAM, F32, true>(c, e, k);
+    return deep<FAM, F32, true, REJ>(c, e, k);
 }
 
 // FP32 path: re-evaluates every logged contender (and the holder of its
 // component) exactly in FP64 and installs the lexicographic (value, id)
 // minimum in `sig`.  Runs in one warp.  Returns the number of exact
 // evaluations.
-template <int FAM>
+template <int FAM, bool REJ>
 __device__ __noinline__ uint32_t resolve_list(Ctx<true> c, const uint32_t *ck, const uint32_t *ce, int ncont,
                                               uint64_t *sig) {
     const SketchParams &P = *c.p;
@@ -536,14 +540,14 @@ __device__ __noinline__ uint32_t resolve_list(Ctx<true> c, const uint32_t *ck, c
         if (seen) continue;
         const uint64_t hk = ld_volatile(&sig[k]);
         uint32_t best_e = (uint32_t)(hk & 0xFFFFFFFFu);
-        double best_x = exact_h<FAM, true>(c, best_e, k);
+        double best_x = exact_h<FAM, true, REJ>(c, best_e, k);
         uint64_t best_id = P.ids[c.beg + best_e];
         evals++;
         for (int b = a; b < ncont; ++b) {
             if (ck[b] != k) continue;
             const uint32_t e = ce[b];
             if (e == best_e) continue;
-            double x = exact_h<FAM, true>(c, e, k);
+            double x = exact_h<FAM, true, REJ>(c, e, k);
             evals++;
             uint64_t cid = P.ids[c.beg + e];
             if (x < best_x || (x == best_x && cid < best_id)) { best_x = x; best_id = cid; best_e = e; }
@@ -554,11 +558,11 @@ __device__ __noinline__ uint32_t resolve_list(Ctx<true> c, const uint32_t *ck, c
     return evals;
 }
 
-template <int FAM>
+template <int FAM, bool REJ>
 __device__ __forceinline__ uint32_t resolve_contenders(Ctx<true> &c) {
     TeamShared *ts = c.ts;
     const int ncont = min(ld_volatile(&ts->cont_n), c.p->max_cont);   // the caller redoes an item that overflowed
-    return resolve_list<FAM>(c, ts->cont_k, ts->cont_e, ncont, (uint64_t *)c.sig);
+    return resolve_list<FAM, REJ>(c, ts->cont_k, ts->cont_e, ncont, (uint64_t *)c.sig);
 }
 
 // FP32 path: hands an item whose contender log overflowed to the FP64 kernel
@@ -643,7 +647,7 @@ struct SeqLane {
 // Expands the n buffered survivors (ws->sb_e[32 + j], sb_key[j], sb_winv[j];
 // the filter leaves w * 2^-sigma in sb_winv, replaced by its scaled reciprocal
 // on entry).  fin: the last call of the pass (every sequence ends in it).
-template <int FAM, bool F32>
+template <int FAM, bool F32, bool REJ>
 __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, int n, bool fin) {
     const long long t_sv = clock64();
     const SketchParams &P = *c.p;
@@ -738,11 +742,13 @@ __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, 
                     if (FAM == 1) { L.s32 = __fadd_rn(L.s32, exp1_32(vw)); x32 = __fmul_rn(L.winv32, L.s32); }
                     else if (FAM == 2) { L.s32 = __fadd_rn(L.s32, __fmul_rn(T.beta32[L.i], exp1_32(vw))); x32 = __fmul_rn(L.winv32, L.s32); }
                     else if (c.unw) x32 = __fmul_rn(L.winv32, __fadd_rn((float)(L.i - 1), u53_to_float(vw >> 11)));
-                    else if (FAM == 3) x32 = __fmul_rn(L.winv32, __fadd_rn((float)(L.i - 1), texp_32(vw, T.c3_32, T.inv3_32)));
-                    else {
+                    else if (FAM == 3) {
+                        const float te = (REJ && c.rej) ? texp_rej_32(T, 1, L.key, L.i, vw) : texp_32(vw, T.c3_32, T.inv3_32);
+                        x32 = __fmul_rn(L.winv32, __fadd_rn((float)(L.i - 1), te));
+                    } else {
                         float sv;
                         const float4 q = T.p4[L.i];
-                        if (L.i < m) sv = __fadd_rn(q.x, __fmul_rn(q.y, texp_32(vw, q.z, q.w)));
+                        if (L.i < m) sv = __fadd_rn(q.x, __fmul_rn(q.y, (REJ && c.rej) ? texp_rej_32(T, L.i, L.key, L.i, vw) : texp_32(vw, q.z, q.w)));
                         else sv = __fadd_rn(q.x, __fmul_rn(T.delta32, exp1_32(vw)));
                         x32 = __fmul_rn(L.winv32, sv);
                     }
@@ -758,8 +764,8 @@ __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, 
                     if (FAM == 1) L.x64 = __dadd_rn(L.x64, term1_64(vw, L.w_inv));
                     else if (FAM == 2) L.x64 = __dadd_rn(L.x64, term2_64(T, vw, L.i, L.w_inv));
                     else if (c.unw) L.x64 = point_unw_64(vw, L.i, L.w_inv);
-                    else if (FAM == 3) L.x64 = point3_64(T, vw, L.i, L.w_inv);
-                    else L.x64 = point4_64(T, vw, L.i, L.w_inv);
+                    else if (FAM == 3) L.x64 = (REJ && c.rej) ? point3r_64(T, L.key, vw, L.i, L.w_inv) : point3_64(T, vw, L.i, L.w_inv);
+                    else L.x64 = (REJ && c.rej) ? point4r_64(T, L.key, vw, L.i, L.w_inv) : point4_64(T, vw, L.i, L.w_inv);
                     const double b64 = ld_volatile(&c.ts->bound64);
                     beyond = L.x64 > b64;
                     if (!beyond) won |= Offer<false>::run(c, k, L.x64, L.id);
@@ -809,7 +815,7 @@ __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, 
     const int total_deep = min(ws->dq_n, 32 + kSurvCap);
     if (total_deep && (!kPerm || !__any_sync(kFull, L.has))) {
         const long long td = clock64();
-        for (int j = 0; j < total_deep; ++j) deep<FAM, F32, false>(c, ws->sb_e[j], 0);
+        for (int j = 0; j < total_deep; ++j) deep<FAM, F32, false, REJ>(c, ws->sb_e[j], 0);
         count(c, PMH_CNT_CYC_DEEP, (unsigned long long)(clock64() - td));
         __syncwarp();
         if (lane == 0) ws->dq_n = 0;
@@ -835,14 +841,19 @@ __device__ __forceinline__ void team_sync() {
 // One pass over the elements [lo, hi) of the current item with the team's
 // current bound: filter, compacted survivors, q_max refreshes.  Every warp of
 // the team takes 64-element steps.
-template <int FAM, bool F32, int TW>
+template <int FAM, bool F32, int TW, bool REJ>
 __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
     const SketchParams &P = *c.p;
     const int lane = threadIdx.x & 31;
     constexpr int team_warps = TW;
     TeamShared *ts = c.ts;
     WarpShared *ws = c.ws;
-    const float te_lo = (FAM >= 3 && !c.unw) ? P.tab.te_lo : 1.0f;
+    // Lower bound of the first point's variate: Exp(1) >= U and, by inversion, Exp(lambda;0,1) >=
+    // U (1-e^-lambda)/lambda.  With the rejection sampler (REJ) the first draw c1 U >= U holds when
+    // U's 53-bit integer is below k1 and nothing is known otherwise; u1: a 23-bit U below it has k < k1.
+    const bool rej = REJ && c.rej;
+    const float te_lo = (FAM >= 3 && !c.unw && !rej) ? P.tab.te_lo : 1.0f;
+    const float u1 = rej ? P.tab.rej_u1_32 : 2.0f;
     if (lane == 0) { ws->sb_n = 0; ws->dq_n = 0; }
     __syncwarp();
     bool refreshed = false;
@@ -921,12 +932,16 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
                     // Conservative: the products' roundings and the truncated mantissa are
                     // within the 16-ulp slack.
                     winv[h] = ws_scaled(c.unw ? 1.0 : wv[h], c.sigma);
-                    const float ulo = __fmul_rn(unif_lo(value_word(key[h], 1)), te_lo);
+                    const float u = unif_lo(value_word(key[h], 1));
+                    const float ulo = __fmul_rn(u, te_lo);
                     surv[h] = !(__fmul_rn(ulo, 1.0f - 16.0f * 0x1p-24f) > __fmul_rn(b32, winv[h]));
+                    if constexpr (REJ) surv[h] = surv[h] || !(u < u1);
 #else
                     winv[h] = winv_scaled(c.unw ? 1.0 : wv[h], c.sigma);
-                    const float xlo = winv[h] * unif_lo(value_word(key[h], 1)) * te_lo;
+                    const float u = unif_lo(value_word(key[h], 1));
+                    const float xlo = winv[h] * u * te_lo;
                     surv[h] = !(xlo * (1.0f - 8.0f * 0x1p-24f) > b32);
+                    if constexpr (REJ) surv[h] = surv[h] || !(u < u1);
 #endif
                 }
             }
@@ -957,7 +972,7 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
         // expand a full batch of survivors; at the end of the pass, whatever is left
         bool any_win = false;
         if (fin ? (n > 0 || __any_sync(kFull, L.has)) : n >= kSurvBatch) {
-            any_win = process_survivors<FAM, F32>(c, L, n, fin);
+            any_win = process_survivors<FAM, F32, REJ>(c, L, n, fin);
             n = 0;
         }
         if (lane == 0) ws->sb_n = n;
@@ -977,7 +992,7 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
 }
 
 // ------------------------------------------------------------ one item
-template <int FAM, bool F32, int TW>
+template <int FAM, bool F32, int TW, bool REJ>
 __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
     const SketchParams &P = *c.p;
     const uint32_t m = P.m;
@@ -999,6 +1014,7 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
         else { ((Rec64 *)c.sig)[k].q = __longlong_as_double(0x7FF0000000000000ll); ((Rec64 *)c.sig)[k].id = 0; }
     }
     c.unw = variant_unweighted(P.variants[item_v]);
+    c.rej = REJ && FAM >= 3 && !c.unw;
     SetStat st0 = P.stats[set];
     if (c.unw) st0.wsum = (double)st0.npos;   // binary weights: each element counts 1
     if (leader) {
@@ -1046,7 +1062,7 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
         }
         if (round > 0) count(c, PMH_CNT_ROUNDS, leader);
         team_sync<TW>();
-        run_range<FAM, F32, TW>(c, 0, c.n);
+        run_range<FAM, F32, TW, REJ>(c, 0, c.n);
         const long long t_bar = clock64();
         team_sync<TW>();
         count(c, PMH_CNT_CYC_BARRIER, (unsigned long long)(clock64() - t_bar));
@@ -1070,7 +1086,7 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
             return;   // the FP64 kernel writes this item's outputs
         }
         if (tw == 0 && ld_volatile(&ts->cont_n) > 0) {
-            const uint32_t ev = resolve_contenders<FAM>(c);
+            const uint32_t ev = resolve_contenders<FAM, REJ>(c);
             count(c, PMH_CNT_RESOLVED, ev);
         }
     }
@@ -1089,7 +1105,7 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
             for (uint32_t k = tw; k < m; k += team_warps) {
                 uint64_t key = sig[k];
                 double q = __longlong_as_double(0x7FF0000000000000ll);
-                if (key != kEmptyKey && st == PMH_OK) q = exact_h<FAM, F32>(c, (uint32_t)(key & 0xFFFFFFFFu), k);
+                if (key != kEmptyKey && st == PMH_OK) q = exact_h<FAM, F32, REJ>(c, (uint32_t)(key & 0xFFFFFFFFu), k);
                 if (lane == 0) P.out_q[out_row * m + k] = q;
             }
         }
@@ -1147,7 +1163,7 @@ __device__ __forceinline__ void merge_rec_global(Rec64 *gsig, uint32_t k, Rec64 
 // Finalisation by the last CTA of a grid item: exact resolution of the logged
 // contenders (FP32), write-out, and a single-CTA rerun with growing
 // thresholds if a component is still empty (probability ~e^-c per item).
-template <int FAM, bool F32>
+template <int FAM, bool F32, bool REJ>
 __device__ void grid_finalize(Ctx<F32> &c, GridState *g, void *gsig_v, int item_v, int64_t set) {
     const SketchParams &P = *c.p;
     const uint32_t m = P.m;
@@ -1174,7 +1190,7 @@ __device__ void grid_finalize(Ctx<F32> &c, GridState *g, void *gsig_v, int item_
             st = PMH_ERR_ITER_LIMIT;
         }
         if (tw == 0 && nc > 0 && st == PMH_OK) {
-            const uint32_t ev = resolve_list<FAM>(c, g->cont_k, g->cont_e, nc, gsig);
+            const uint32_t ev = resolve_list<FAM, REJ>(c, g->cont_k, g->cont_e, nc, gsig);
             count(c, PMH_CNT_RESOLVED, ev);
         }
     }
@@ -1189,7 +1205,7 @@ __device__ void grid_finalize(Ctx<F32> &c, GridState *g, void *gsig_v, int item_
     if (empty && st == PMH_OK) {
         c.gbound32 = nullptr;
         c.gbound64 = nullptr;
-        process_item<FAM, F32, 8>(c, item_v, set);
+        process_item<FAM, F32, 8, REJ>(c, item_v, set);
         return;
     }
     if constexpr (F32) {
@@ -1203,7 +1219,7 @@ __device__ void grid_finalize(Ctx<F32> &c, GridState *g, void *gsig_v, int item_
             for (uint32_t k = tw; k < m; k += team_warps) {
                 const uint64_t key = __ldcg(&gsig[k]);
                 double q = __longlong_as_double(0x7FF0000000000000ll);
-                if (key != kEmptyKey && st == PMH_OK) q = exact_h<FAM, F32>(c, (uint32_t)(key & 0xFFFFFFFFu), k);
+                if (key != kEmptyKey && st == PMH_OK) q = exact_h<FAM, F32, REJ>(c, (uint32_t)(key & 0xFFFFFFFFu), k);
                 if (lane == 0) P.out_q[out_row * m + k] = q;
             }
         }
@@ -1225,13 +1241,14 @@ __device__ void grid_finalize(Ctx<F32> &c, GridState *g, void *gsig_v, int item_
 // One CTA's share of a grid item: chunks of the item's elements with a local
 // signature, then the merge into the global signature; the last CTA to
 // finish finalises the item.
-template <int FAM, bool F32>
+template <int FAM, bool F32, bool REJ>
 __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int item_v, int64_t set) {
     const SketchParams &P = *c.p;
     const uint32_t m = P.m;
     TeamShared *ts = c.ts;
     const bool leader = threadIdx.x == 0;
     c.unw = variant_unweighted(P.variants[item_v]);
+    c.rej = REJ && FAM >= 3 && !c.unw;
     SetStat st0 = P.stats[set];
     if (c.unw) st0.wsum = (double)st0.npos;   // binary weights: each element counts 1
     const bool live = !st0.bad && st0.npos > 0;
@@ -1276,7 +1293,7 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
             __syncthreads();
             if (lo >= c.n) break;
             const uint32_t hi = (uint32_t)min((uint64_t)c.n, lo + chunk);
-            run_range<FAM, F32, 8>(c, (uint32_t)lo, hi);
+            run_range<FAM, F32, 8, REJ>(c, (uint32_t)lo, hi);
             __syncthreads();
         }
         // merge the local signature into the item's global one
@@ -1308,7 +1325,7 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
     __syncthreads();
     if (last) {
         __threadfence();
-        grid_finalize<FAM, F32>(c, g, gsig_v, item_v, set);
+        grid_finalize<FAM, F32, REJ>(c, g, gsig_v, item_v, set);
     }
     c.gbound32 = nullptr;
     c.gbound64 = nullptr;
@@ -1318,7 +1335,7 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
 // grid item of that family, in list order.  Registers are budgeted for four
 // 8-warp CTAs per SM (32 warps): the filter that dominates a huge set is
 // latency bound, so warps count more than the few spills.
-template <bool F32, int FAM>
+template <bool F32, int FAM, bool REJ = false>
 __global__ void __launch_bounds__(256, 4) grid_kernel(const __grid_constant__ SketchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool kPerm = (FAM == 2 || FAM == 4);
@@ -1348,7 +1365,7 @@ __global__ void __launch_bounds__(256, 4) grid_kernel(const __grid_constant__ Sk
         const int slot = (FAM - 1) * kMaxGrid + j;
         c.beg = p.offsets[set];
         c.n = (uint32_t)(p.offsets[set + 1] - c.beg);
-        grid_participate<FAM, F32>(c, &p.gstate[slot], (unsigned char *)p.gsig + (size_t)slot * p.m * 16, v, set);
+        grid_participate<FAM, F32, REJ>(c, &p.gstate[slot], (unsigned char *)p.gsig + (size_t)slot * p.m * 16, v, set);
         __syncthreads();
     }
     __syncwarp();
@@ -1381,7 +1398,7 @@ static __global__ void grid_init_kernel(GridCtl *ctl, GridState *gs, void *gsig,
 // NW warps per block in teams of TW warps (TW = 1: every warp sketches its own
 // items; TW = NW: the whole block shares one signature); MINB = the blocks per
 // SM the register budget is sized for.
-template <bool F32, int NW, int TW, int MINB, int FAM>
+template <bool F32, int NW, int TW, int MINB, int FAM, bool REJ = false>
 __global__ void __launch_bounds__(NW * 32, MINB) sketch_kernel(const __grid_constant__ SketchParams p) {
     static_assert(NW % TW == 0 && NW / TW <= 15, "teams must tile the block (named barriers 1..15)");
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1432,7 +1449,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) sketch_kernel(const __grid_cons
         }
         c.beg = b;
         c.n = (uint32_t)(e - b);
-        process_item<FAM, F32, TW>(c, v, set);
+        process_item<FAM, F32, TW, REJ>(c, v, set);
         team_sync<TW>();
         count(c, PMH_CNT_CYC_ITEM, (unsigned long long)(clock64() - t_item));
     }

@@ -20,6 +20,7 @@ OK, ERR_INVALID_ARG, ERR_BAD_WEIGHT, ERR_ITER_LIMIT, ERR_CUDA, ERR_NO_MEMORY, ER
 V1, V1A, V2, V3, V3A, V4, V3U, V3AU, V4U = range(9)
 VARIANTS = {"1": V1, "1a": V1A, "2": V2, "3": V3, "3a": V3A, "4": V4, "3u": V3U, "3au": V3AU, "4u": V4U}
 FP64, FP32_RECHECK = 0, 1
+TE_INVERSION, TE_REJECTION = 0, 1
 SHAPE_WARP, SHAPE_CTA8, SHAPE_QUAD, SHAPE_PAIR, SHAPE_QUAD8, SHAPE_QUAD8L = range(6)
 COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "rounds", "deep", "prefiltered",
             "cyc_pass0", "cyc_first", "cyc_deep", "cyc_refresh", "cyc_finish", "items", "cyc_surv", "cyc_item",
@@ -27,10 +28,10 @@ COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "round
 EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_sketch_batch_host",
            "pmh_last_host_span_ms", "pmh_sketch_batch_noalloc",
            "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_kernel_ms_history", "pmh_last_launches",
-           "pmh_set_thresholds", "pmh_set_limits", "pmh_sync_status",
+           "pmh_set_thresholds", "pmh_set_limits", "pmh_sync_status", "pmh_set_te_sampler",
            "pmh_set_team_shape", "pmh_set_autotune", "pmh_last_team_shapes",
            "pmh_estimate_jp", "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge", "pmh_check_exp1",
-           "pmh_check_texp", "pmh_bbit_reduce", "pmh_bbit_allpairs")
+           "pmh_check_texp", "pmh_bbit_reduce", "pmh_bbit_allpairs", "pmh_pminhash_batch")
 
 _lib = None
 _lock = threading.Lock()
@@ -85,6 +86,8 @@ def load(path: str = LIB_PATH):
             lib.pmh_last_team_shapes.argtypes = [vp, ctypes.POINTER(i32)]
             lib.pmh_set_thresholds.restype = i32
             lib.pmh_set_thresholds.argtypes = [vp, ctypes.c_double, ctypes.c_double, i32, i64]
+            lib.pmh_set_te_sampler.restype = i32
+            lib.pmh_set_te_sampler.argtypes = [vp, i32]
             lib.pmh_set_limits.restype = i32
             lib.pmh_set_limits.argtypes = [vp, u32, i32]
             lib.pmh_sync_status.restype = i32
@@ -103,6 +106,8 @@ def load(path: str = LIB_PATH):
             lib.pmh_bbit_reduce.argtypes = [vp, vp, i64, u32, u32, u64, vp, vp]
             lib.pmh_bbit_allpairs.restype = i32
             lib.pmh_bbit_allpairs.argtypes = [vp, vp, i64, u32, u32, i32, vp, vp]
+            lib.pmh_pminhash_batch.restype = i32
+            lib.pmh_pminhash_batch.argtypes = [vp, vp, vp, vp, i64, u32, u64, vp, vp, vp, vp]
             lib.pmh_merge.restype = i32
             lib.pmh_merge.argtypes = [vp, vp, vp, i64, u32, vp, vp, vp]
             _lib = lib
@@ -261,6 +266,10 @@ class Handle:
         item (-1 = default); an item whose contender log overflows is redone in FP64."""
         self._raise(load().pmh_set_limits(self._h, int(cap_points), int(max_contenders)))
 
+    def set_te_sampler(self, sampler: int = TE_INVERSION):
+        """Exp(lambda;0,1) of ProbMinHash3/3a/4 by inversion (default) or by the paper's rejection sampler."""
+        self._raise(load().pmh_set_te_sampler(self._h, int(sampler)))
+
     def sync_status(self, status, stream=None):
         """Waits for the stream, then (first failing status or 0, counts per code [8], first bad index)."""
         _check(status, "status", (torch.int32,), self.device)
@@ -337,6 +346,27 @@ class Handle:
                                        pairs_a.numel(), m, _ptr(counts), _stream(stream))
         self._raise(rc)
         return counts
+
+    # -- pmh_pminhash_batch -------------------------------------------------
+    def pminhash_batch(self, ids, weights, offsets, m: int, seed: int = 0, out_ids=None, out_q=None, status=None,
+                       with_q: bool = False, stream=None):
+        """Algorithm P-MinHash on a CSR batch: (out_ids [S, m], out_q or None, status [S])."""
+        dev = self.device
+        _check(ids, "ids", _I64, dev)
+        _check(weights, "weights", (torch.float64,), dev)
+        _check(offsets, "offsets", (torch.int64,), dev)
+        s = offsets.numel() - 1
+        if out_ids is None:
+            out_ids = torch.empty((s, m), dtype=torch.int64, device=dev)
+        if out_q is None and with_q:
+            out_q = torch.empty((s, m), dtype=torch.float64, device=dev)
+        if status is None:
+            status = torch.empty(s, dtype=torch.int32, device=dev)
+        rc = load().pmh_pminhash_batch(self._h, _ptr(ids), _ptr(weights), _ptr(offsets), s, m,
+                                       int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out_ids), _ptr(out_q), _ptr(status),
+                                       _stream(stream))
+        self._raise(rc)
+        return out_ids, out_q, status
 
     # -- pmh_merge ----------------------------------------------------------
     def merge(self, q, z, out_q=None, out_z=None, stream=None):

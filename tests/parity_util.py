@@ -41,20 +41,21 @@ def run(H, batch, variants, precision, with_q=True, seed=0, counters=None):
     return (pmh.to_u64(z), q.cpu().numpy() if q is not None else None, st.cpu().numpy())
 
 
-def check_sets(batch, variant, z, q, sets, seed=0, stats=None, scan=False):
+def check_sets(batch, variant, z, q, sets, seed=0, stats=None, scan=False, te_rejection=False):
     """Compares GPU rows z[s], q[s] with the oracle for the listed sets.
 
     stats (optional dict): "near" counts the oracle's near ties, "components" the components
     compared, "mismatch" the exempted id mismatches.  Without `scan` near ties are counted only
     in sets with a mismatch; with `scan` every set is scanned, so "near" / "components" is the
-    near-tie rate of the sample."""
+    near-tie rate of the sample.  te_rejection: the GPU drew Exp(lambda;0,1) with the rejection
+    sampler, and so does the oracle."""
     m = batch.m
     for s in sets:
         ids, w = batch.set(s)
-        qo, zo, _ = oracle.sketch(variant, ids, w, m, seed=seed)
+        qo, zo, _ = oracle.sketch(variant, ids, w, m, seed=seed, te_rejection=te_rejection)
         diff = np.nonzero(z[s] != zo)[0]
         if len(diff) or (scan and stats is not None):
-            flags, _ = oracle.near_ties(variant, ids, w, m, seed, qo, zo, NEAR_REL)
+            flags, _ = oracle.near_ties(variant, ids, w, m, seed, qo, zo, NEAR_REL, te_rejection=te_rejection)
             assert flags[diff].all(), f"set {s} variant {variant}: {len(diff)} unflagged id mismatches, e.g. k={diff[:5]}"
             if stats is not None:
                 stats["near"] += int(flags.sum())

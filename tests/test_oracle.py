@@ -808,3 +808,41 @@ def test_rejection_sampler_changes_signatures_and_scan_matches_singletons(varian
         assert ids[order[0]] == z[k] and h[order[0], k] == q[k]
         second = h[order[1], k]
         assert ru[k] == (second if second <= bound else np.inf)
+
+
+# ------------------------------------------------------------------ P-MinHash --
+# Algorithm P-MinHash: h_k(d) = Exp(1)/w(d) independently per component (no early stop); the
+# reference method the ProbMinHash algorithms are compared with, also built on the GPU.
+
+def test_pminhash_exponential_race_and_hash_values():
+    ids = np.array([11, 22, 33, 44], dtype=np.uint64)
+    w = np.array([1.0, 2.0, 3.0, 4.0])
+    counts = np.zeros(4)
+    for seed in range(300):
+        _, z = oracle.pminhash(ids, w, 32, seed=seed)
+        for j, d in enumerate(ids):
+            counts[j] += np.count_nonzero(z == d)
+    assert stats.chisquare(counts, w / w.sum() * counts.sum()).pvalue > 1e-4
+    # a single element: every component holds an independent Exp(1)/w
+    q, z = oracle.pminhash(np.array([9], dtype=np.uint64), np.array([2.5]), 4000, seed=1)
+    assert (z == 9).all()
+    assert stats.kstest(q * 2.5, "expon").pvalue > 1e-4
+    assert abs(np.corrcoef(q[:-1], q[1:])[0, 1]) < 0.06
+
+
+def test_pminhash_invariants():
+    rng = np.random.default_rng(170)
+    for trial in range(8):
+        ids, w = _rand_set(rng, int(rng.integers(1, 300)), ["uniform", "pareto", "lognormal", "unit"][trial % 4])
+        q, z = oracle.pminhash(ids, w, 64, seed=trial)
+        perm = rng.permutation(len(ids))
+        q2, z2 = oracle.pminhash(ids[perm], w[perm], 64, seed=trial)
+        assert np.array_equal(q, q2) and np.array_equal(z, z2)
+        q3, z3 = oracle.pminhash(ids, w * 4.0, 64, seed=trial)
+        assert np.array_equal(z, z3) and np.array_equal(q3, q / 4.0)
+        # the signature of a disjoint union is the lexicographic minimum of the parts' (Eq. signature_def)
+        cut = len(ids) // 2
+        qa, za = oracle.pminhash(ids[:cut], w[:cut], 64, seed=trial)
+        qb, zb = oracle.pminhash(ids[cut:], w[cut:], 64, seed=trial)
+        take_b = (qb < qa) | ((qb == qa) & (zb < za))
+        assert np.array_equal(np.where(take_b, zb, za), z) and np.array_equal(np.where(take_b, qb, qa), q)
