@@ -234,6 +234,50 @@ def te_sampler_comparison(h, ids, w, off, m, work_per_variant, steps=5):
     return out
 
 
+def pminhash_comparison(h, dev, m=1024, steps=3):
+    """Time per signature of Algorithm P-MinHash (n m hash values per set) against ProbMinHash1 and 3
+    (FP32 + recheck) over set sizes n = 1 .. 1e5 at m = 1024, Uniform(0,1] weights: the comparison of
+    the paper's experiments (fig:speed), on the GPU.  Device time by CUDA events around each call."""
+    import numpy as np
+    import torch
+    from paper_1911_00675_gb300 import pmh
+    from paper_1911_00675_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    rows = []
+    for n in (1, 10, 100, 1000, 10000, 100000):
+        S = int(min(100000, max(100, 2e10 / (n * m))))
+        b = W.random_batch(9000 + n, [n] * S, m, "uniform")
+        ids = torch.from_numpy(b.ids.view(np.int64)).to(dev)
+        w = torch.from_numpy(b.weights).to(dev)
+        off = torch.from_numpy(b.offsets).to(dev)
+        zp = torch.empty((S, m), dtype=torch.int64, device=dev)
+        stp = torch.empty(S, dtype=torch.int32, device=dev)
+        z1 = torch.empty((1, S, m), dtype=torch.int64, device=dev)
+        st1 = torch.empty((1, S), dtype=torch.int32, device=dev)
+        ms_p = timed(lambda: h.pminhash_batch(ids, w, off, m, 0, out_ids=zp, status=stp))
+        ms_1 = timed(lambda: h.sketch_batch(ids, w, off, m, ["1"], pmh.FP32_RECHECK, 0, out_ids=z1, status=st1))
+        ms_3 = timed(lambda: h.sketch_batch(ids, w, off, m, ["3"], pmh.FP32_RECHECK, 0, out_ids=z1, status=st1))
+        rows.append({"n": n, "sets": S, "pminhash_us_per_sig": ms_p * 1e3 / S, "pmh1_us_per_sig": ms_1 * 1e3 / S,
+                     "pmh3_us_per_sig": ms_3 * 1e3 / S, "speedup_pmh1_vs_pminhash": ms_p / ms_1,
+                     "speedup_pmh3_vs_pminhash": ms_p / ms_3,
+                     "status_ok": bool((stp == 0).all().item() and (st1 == 0).all().item())})
+        del ids, w, off, zp, z1
+    return {"workload": f"sets of n elements (Uniform(0,1] weights), m={m}; per n about 2e10 / (n m) sets "
+                        "(at least 100, at most 100,000)", "rows": rows}
+
+
 def secondary(h, dev, n_sms, sm_mhz, peaks, steps=3):
     """Per-kernel measurements beside the headline: the precision config (FP32 + recheck against FP64
     at m = 4096), grid mode on one huge set (HBM-bound) and the all-pairs equal-component count
@@ -629,6 +673,7 @@ def main():
     if not args.no_secondary:
         sec_res = secondary(h, dev, n_sms, sm_mhz, peaks)
         sec_res["te_sampler"] = te_sampler_comparison(h, ids, w, off, m, n_elem)
+        sec_res["pminhash_vs_probminhash"] = pminhash_comparison(h, dev)
 
     # ---------------- CPU baseline (rank 0, N=1 only), and the GPU's point work on the same tasks
     cpu = None

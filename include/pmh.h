@@ -433,6 +433,20 @@ pmh_status pmh_estimate_allpairs(pmh_handle h, const uint64_t *sigs, int64_t num
                                  int32_t upper_only, uint16_t *counts, void *stream);
 
 /*
+ * pmh_estimate_jp_block -- the same counts (Eq. jaccard_estimator) between the
+ * rows of two signature tables, one block of the pair matrix:
+ * counts[a * ld_counts + b] = #{k : sig_a[a][k] == sig_b[b][k]}.  Used to split
+ * the all-pairs matrix into tiles (one or several per GPU).
+ *   sig_a, sig_b device uint64[num_a * m], [num_b * m] row-major (may alias).
+ *   counts    device uint16, num_a rows of ld_counts >= num_b entries.
+ * Errors: PMH_ERR_INVALID_ARG (NULL pointers, negative sizes, ld_counts <
+ * num_b), PMH_ERR_UNSUPPORTED (m > 65535, more than 65535 tiles of 64 rows
+ * of sig_a), PMH_ERR_CUDA.
+ */
+pmh_status pmh_estimate_jp_block(pmh_handle h, const uint64_t *sig_a, int64_t num_a, const uint64_t *sig_b,
+                                 int64_t num_b, uint32_t m, uint16_t *counts, int64_t ld_counts, void *stream);
+
+/*
  * pmh_estimate_pairs -- the same count for listed pairs (Eq. jaccard_estimator):
  * counts[i] = #{k : sig_a[pairs_a[i]][k] == sig_b[pairs_b[i]][k]}.
  *   sig_a, sig_b  device uint64[* x m] row-major signature tables (may alias).

@@ -774,13 +774,16 @@ extern "C" pmh_status pmh_check_exp1(const uint64_t *words, int64_t n, float *ou
 }
 
 // ------------------------------------------------------------------ estimation
-// All-pairs equal-component counts, Eq. jaccard_estimator.  64x64 tile of
-// pairs per CTA, 16 components per shared-memory stage, 4x4 pairs per thread
-// (rows ty + 16i, columns tx + 16j: conflict-free shared reads).
+// Equal-component counts of every pair (a, b) of rows of two signature tables,
+// Eq. jaccard_estimator: out[a * ldo + b].  64x64 tile of pairs per CTA, 16
+// components per shared-memory stage, 4x4 pairs per thread (rows ty + 16i,
+// columns tx + 16j: conflict-free shared reads).  With upper_only (one table
+// against itself) only b >= a is written.
 constexpr int kTile = 64, kKc = 16;
 
-__global__ void __launch_bounds__(256) allpairs_kernel(const uint64_t *__restrict__ sig, int64_t n, uint32_t m,
-                                                       int upper_only, uint16_t *__restrict__ out) {
+__global__ void __launch_bounds__(256) allpairs_kernel(const uint64_t *__restrict__ sa, int64_t na,
+                                                       const uint64_t *__restrict__ sb, int64_t nb, uint32_t m,
+                                                       int upper_only, uint16_t *__restrict__ out, int64_t ldo) {
     __shared__ uint64_t As[kKc][kTile + 1];
     __shared__ uint64_t Bs[kKc][kTile + 1];
     const int64_t ta = blockIdx.y, tb = blockIdx.x;
@@ -800,8 +803,8 @@ __global__ void __launch_bounds__(256) allpairs_kernel(const uint64_t *__restric
             const uint32_t k = kc + kk;
             const int64_t ra = a0 + r, rb = b0 + r;
             // out-of-range rows/components load two different sentinels so they never match
-            As[kk][r] = (ra < n && k < m) ? sig[ra * m + k] : 0xFFFFFFFFFFFFFFFFull;
-            Bs[kk][r] = (rb < n && k < m) ? sig[rb * m + k] : 0xFFFFFFFFFFFFFFFEull;
+            As[kk][r] = (ra < na && k < m) ? sa[ra * m + k] : 0xFFFFFFFFFFFFFFFFull;
+            Bs[kk][r] = (rb < nb && k < m) ? sb[rb * m + k] : 0xFFFFFFFFFFFFFFFEull;
         }
         __syncthreads();
 #pragma unroll
@@ -821,12 +824,12 @@ __global__ void __launch_bounds__(256) allpairs_kernel(const uint64_t *__restric
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         const int64_t a = a0 + ty + 16 * i;
-        if (a >= n) continue;
+        if (a >= na) continue;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             const int64_t b = b0 + tx + 16 * j;
-            if (b >= n || (upper_only && a > b)) continue;
-            out[a * n + b] = (uint16_t)cnt[i][j];
+            if (b >= nb || (upper_only && a > b)) continue;
+            out[a * ldo + b] = (uint16_t)cnt[i][j];
         }
     }
 }
@@ -880,7 +883,27 @@ extern "C" pmh_status pmh_estimate_jp(pmh_handle h, const uint64_t *sigs, int64_
     if (tiles > 65535) return fail(h, PMH_ERR_UNSUPPORTED, "num_sigs too large for one launch");
     CUDA_TRY(h, cudaSetDevice(h->device));
     dim3 grid((unsigned)tiles, (unsigned)tiles);
-    allpairs_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(sigs, num_sigs, m, upper_only ? 1 : 0, counts);
+    allpairs_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(sigs, num_sigs, sigs, num_sigs, m, upper_only ? 1 : 0,
+                                                            counts, num_sigs);
+    CUDA_TRY(h, cudaGetLastError());
+    return PMH_OK;
+}
+
+extern "C" pmh_status pmh_estimate_jp_block(pmh_handle h, const uint64_t *sig_a, int64_t num_a, const uint64_t *sig_b,
+                                            int64_t num_b, uint32_t m, uint16_t *counts, int64_t ld_counts,
+                                            void *stream) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    if (num_a < 0 || num_b < 0) return fail(h, PMH_ERR_INVALID_ARG, "num_a < 0 or num_b < 0");
+    if (m < 1 || m > 65535) return fail(h, PMH_ERR_UNSUPPORTED, "m = %u outside [1, 65535]", m);
+    if (num_a == 0 || num_b == 0) return PMH_OK;
+    if (!sig_a || !sig_b || !counts) return fail(h, PMH_ERR_INVALID_ARG, "NULL sig_a/sig_b/counts");
+    if (ld_counts < num_b) return fail(h, PMH_ERR_INVALID_ARG, "ld_counts < num_b");
+    const int64_t ta = (num_a + kTile - 1) / kTile, tb = (num_b + kTile - 1) / kTile;
+    if (ta > 65535 || tb > 2147483647ll) return fail(h, PMH_ERR_UNSUPPORTED, "tables too large for one launch");
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    dim3 grid((unsigned)tb, (unsigned)ta);
+    allpairs_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(sig_a, num_a, sig_b, num_b, m, 0, counts, ld_counts);
     CUDA_TRY(h, cudaGetLastError());
     return PMH_OK;
 }

@@ -1335,8 +1335,11 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
 // grid item of that family, in list order.  Registers are budgeted for four
 // 8-warp CTAs per SM (32 warps): the filter that dominates a huge set is
 // latency bound, so warps count more than the few spills.
+#ifndef PMH_GRID_MINB
+#define PMH_GRID_MINB 4
+#endif
 template <bool F32, int FAM, bool REJ = false>
-__global__ void __launch_bounds__(256, 4) grid_kernel(const __grid_constant__ SketchParams p) {
+__global__ void __launch_bounds__(256, PMH_GRID_MINB) grid_kernel(const __grid_constant__ SketchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool kPerm = (FAM == 2 || FAM == 4);
     constexpr int NW = 8;

@@ -30,7 +30,7 @@ EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "p
            "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_kernel_ms_history", "pmh_last_launches",
            "pmh_set_thresholds", "pmh_set_limits", "pmh_sync_status", "pmh_set_te_sampler",
            "pmh_set_team_shape", "pmh_set_autotune", "pmh_last_team_shapes",
-           "pmh_estimate_jp", "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge", "pmh_check_exp1",
+           "pmh_estimate_jp", "pmh_estimate_jp_block", "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge", "pmh_check_exp1",
            "pmh_check_texp", "pmh_bbit_reduce", "pmh_bbit_allpairs", "pmh_pminhash_batch")
 
 _lib = None
@@ -94,6 +94,8 @@ def load(path: str = LIB_PATH):
             lib.pmh_sync_status.argtypes = [vp, vp, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), vp]
             lib.pmh_estimate_jp.restype = i32
             lib.pmh_estimate_jp.argtypes = [vp, vp, i64, u32, i32, vp, vp]
+            lib.pmh_estimate_jp_block.restype = i32
+            lib.pmh_estimate_jp_block.argtypes = [vp, vp, i64, vp, i64, u32, vp, i64, vp]
             lib.pmh_estimate_allpairs.restype = i32
             lib.pmh_estimate_allpairs.argtypes = [vp, vp, i64, u32, i32, vp, vp]
             lib.pmh_estimate_pairs.restype = i32
@@ -318,6 +320,22 @@ class Handle:
             counts = torch.zeros((n, n), dtype=torch.int16, device=self.device)   # uint16 storage
         _check(counts, "counts", (torch.int16, getattr(torch, "uint16", torch.int16)), self.device)
         rc = load().pmh_estimate_jp(self._h, _ptr(sigs), n, m, 1 if upper_only else 0, _ptr(counts), _stream(stream))
+        self._raise(rc)
+        return counts
+
+    def estimate_jp_block(self, sig_a, sig_b, counts=None, stream=None):
+        """Equal-component counts between the rows of two signature tables [na, nb] (int16 view of uint16)."""
+        _check(sig_a, "sig_a", _I64, self.device)
+        _check(sig_b, "sig_b", _I64, self.device)
+        na, m = sig_a.shape
+        nb = sig_b.shape[0]
+        if sig_b.shape[1] != m:
+            raise ValueError("sig_a and sig_b need the same m")
+        if counts is None:
+            counts = torch.zeros((na, nb), dtype=torch.int16, device=self.device)
+        _check(counts, "counts", (torch.int16, getattr(torch, "uint16", torch.int16)), self.device)
+        rc = load().pmh_estimate_jp_block(self._h, _ptr(sig_a), na, _ptr(sig_b), nb, m, _ptr(counts), counts.shape[1],
+                                          _stream(stream))
         self._raise(rc)
         return counts
 

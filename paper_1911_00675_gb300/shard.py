@@ -9,6 +9,11 @@ One huge set shards by element range.  Its signature is the lexicographic (value
 component by component, of the partial signatures of disjoint parts (Eq. signature_def over a
 disjoint union), so each rank sketches its range with exact values (out_q), the partials are
 gathered with one all_gather, and `pmh_merge` combines them.
+
+The all-pairs estimator counts (Eq. jaccard_estimator) shard as a 2-D partition of the pair
+matrix: `pair_tiles` cuts its upper triangle into square tiles dealt to the ranks by pair count;
+`estimate_jp_sharded` all-gathers the signature rows (each rank holds those of its own sets: the
+one exchange step) and counts the pairs of this rank's tiles with pmh_estimate_jp_block.
 """
 from __future__ import annotations
 
@@ -87,6 +92,82 @@ def sketch_set_sharded(handle, ids, weights, m: int, variant: str, precision: in
     return handle.merge(Q.contiguous(), Z.contiguous())
 
 
+def pair_tiles(n: int, world: int, tile: int | None = None):
+    """2-D partition of the upper triangle (diagonal included) of the n x n pair matrix.
+
+    The rows are cut into blocks of `tile` rows (default: enough blocks for about four tiles per
+    rank); tile (I, J), I <= J, covers rows of block I against rows of block J, and a diagonal tile
+    holds the pairs a <= b.  Tiles go to ranks longest first, each to the rank with the fewest pairs
+    so far.  Returns per rank a list of (r0, r1, c0, c1)."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    n = int(n)
+    if n == 0:
+        return [[] for _ in range(world)]
+    if tile is None:
+        blocks = max(1, int(np.ceil(np.sqrt(8.0 * world))))
+        tile = max(1, -(-n // blocks))
+    edges = list(range(0, n, tile)) + [n]
+    tiles = []
+    for i in range(len(edges) - 1):
+        for j in range(i, len(edges) - 1):
+            r0, r1, c0, c1 = edges[i], edges[i + 1], edges[j], edges[j + 1]
+            k = r1 - r0
+            pairs = k * (k + 1) // 2 if i == j else k * (c1 - c0)
+            tiles.append((pairs, r0, r1, c0, c1))
+    tiles.sort(key=lambda t: (-t[0], t[1], t[3]))
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for pairs, r0, r1, c0, c1 in tiles:
+        r = min(range(world), key=lambda x: (load[x], x))
+        load[r] += pairs
+        out[r].append((r0, r1, c0, c1))
+    return out
+
+
+def tile_pairs(t) -> int:
+    """Number of pairs a tile (r0, r1, c0, c1) holds (a <= b on the diagonal)."""
+    r0, r1, c0, c1 = t
+    return (r1 - r0) * (r1 - r0 + 1) // 2 if (r0, r1) == (c0, c1) else (r1 - r0) * (c1 - c0)
+
+
+def gather_rows(local, group=None):
+    """All-gathers row blocks of unequal length (rank order): local [k_r, m] -> [sum k_r, m]."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    k = torch.tensor([local.shape[0]], dtype=torch.int64, device=local.device)
+    ks = [torch.empty_like(k) for _ in range(world)]
+    dist.all_gather(ks, k, group=group)
+    sizes = [int(x.item()) for x in ks]
+    kmax = max(sizes) if sizes else 0
+    pad = torch.zeros((kmax, local.shape[1]), dtype=local.dtype, device=local.device)
+    pad[:local.shape[0]] = local
+    parts = [torch.empty_like(pad) for _ in range(world)]
+    dist.all_gather(parts, pad, group=group)
+    return torch.cat([p[:sz] for p, sz in zip(parts, sizes)])
+
+
+def estimate_jp_sharded(local_sigs, group=None, count_block=None, gather=gather_rows, handle=None):
+    """Equal-component counts of all signature pairs over the ranks of `group`.
+
+    local_sigs: this rank's signature rows [k_r, m] (int64 view of uint64); the full table is the
+    ranks' rows in rank order.  Every rank all-gathers the table, then counts the pairs of its own
+    tiles (pair_tiles) with count_block(A, B) -> [len A, len B] counts (default: the handle's
+    pmh_estimate_jp_block).  Returns (n, [(r0, r1, c0, c1, counts)]); diagonal tiles hold the full
+    square block (its lower triangle repeats the upper)."""
+    import torch.distributed as dist
+    full = gather(local_sigs, group)
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    if count_block is None:
+        count_block = handle.estimate_jp_block
+    out = []
+    for r0, r1, c0, c1 in pair_tiles(full.shape[0], world)[rank]:
+        out.append((r0, r1, c0, c1, count_block(full[r0:r1].contiguous(), full[c0:c1].contiguous())))
+    return full.shape[0], out
+
+
 def balance(costs_per_rank) -> float:
     """max / mean of the ranks' costs (1.0 = perfect balance)."""
     c = np.asarray(costs_per_rank, dtype=np.float64)
@@ -94,4 +175,4 @@ def balance(costs_per_rank) -> float:
 
 
 __all__ = ["harmonic", "set_costs", "partition_sets", "partition_elements", "rank_slice", "gather_partials",
-           "sketch_set_sharded", "balance"]
+           "sketch_set_sharded", "pair_tiles", "tile_pairs", "gather_rows", "estimate_jp_sharded", "balance"]

@@ -142,3 +142,30 @@ def test_c4_full_allpairs_sampled_rows(H):
         assert np.array_equal(got[r_i], ref)
     # the family structure spans the range: within-family counts are high, across families ~0
     assert got[:, :].max() == 1024
+
+
+def test_block_counts_match_oracle_and_tile_the_matrix(H):
+    # one block of the pair matrix between two tables (strided output), and the 2-D tiles of the
+    # multi-GPU split computed on one GPU and put together: the full all-pairs matrix
+    import oracle
+    from paper_1911_00675_gb300 import shard
+    rng = np.random.default_rng(40)
+    base = rng.integers(0, 2**62, size=(6, 300), dtype=np.uint64)
+    sig = base[rng.integers(0, 6, size=333)].copy()
+    noise = rng.random(sig.shape) < 0.3
+    sig[noise] = rng.integers(0, 2**62, size=int(noise.sum()), dtype=np.uint64)
+    ref = oracle.count_allpairs(sig).astype(np.int64)
+    d = torch.from_numpy(sig.view(np.int64).copy()).cuda()
+    out = torch.full((70, 141), -1, dtype=torch.int16, device="cuda")
+    H.estimate_jp_block(d[5:75].contiguous(), d[190:330].contiguous(), counts=out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.int64)
+    assert np.array_equal(got[:, :140], ref[5:75, 190:330]) and (got[:, 140] == -1).all()
+    full = np.full((333, 333), -1, dtype=np.int64)
+    for rank_tiles in shard.pair_tiles(333, 3):
+        for r0, r1, c0, c1 in rank_tiles:
+            c = H.estimate_jp_block(d[r0:r1].contiguous(), d[c0:c1].contiguous())
+            torch.cuda.synchronize()
+            full[r0:r1, c0:c1] = c.cpu().numpy().astype(np.int64)
+    iu = np.triu_indices(333)
+    assert np.array_equal(full[iu], ref[iu])

@@ -32,6 +32,23 @@ def _lexmin(Q, Z):
     return Q[order, cols], Z[order, cols]
 
 
+def _pair_sigs():
+    """130 signatures of m = 24 with many equal components (rows drawn from a few base rows)."""
+    rng = np.random.default_rng(31)
+    base = rng.integers(0, 2**62, size=(5, 24), dtype=np.uint64)
+    sig = base[rng.integers(0, 5, size=130)].copy()
+    noise = rng.random(sig.shape) < 0.5
+    sig[noise] = rng.integers(0, 2**62, size=int(noise.sum()), dtype=np.uint64)
+    return sig
+
+
+def _count_block(a, b):
+    """Test-side counting: equal components of every row pair (the estimator's numerator)."""
+    a = a.numpy().view(np.uint64)
+    b = b.numpy().view(np.uint64)
+    return (a[:, None, :] == b[None, :, :]).sum(axis=2)
+
+
 def _rank_main(rank, world, port, out_dir):
     import torch.distributed as dist
 
@@ -56,6 +73,13 @@ def _rank_main(rank, world, port, out_dir):
         eb = shard.partition_elements(len(ids), world)
         q, z, _ = oracle.sketch("2", ids[eb[rank]:eb[rank + 1]], w[eb[rank]:eb[rank + 1]], 128, seed=5)
         Q, Z = shard.gather_partials(torch.from_numpy(q), torch.from_numpy(z.view(np.int64)))
+        # (3) all-pairs counts: rows split unevenly over the ranks, gathered, 2-D tiles per rank
+        sig_all = _pair_sigs()
+        cut = [0, 57, len(sig_all)]
+        local = torch.from_numpy(sig_all[cut[rank]:cut[rank + 1]].view(np.int64).copy())
+        n, tiles = shard.estimate_jp_sharded(local, count_block=_count_block)
+        flat = [np.array([r0, r1, c0, c1] + list(cnt.reshape(-1)), dtype=np.int64) for r0, r1, c0, c1, cnt in tiles]
+        np.save(os.path.join(out_dir, f"tiles{rank}.npy"), np.array(flat, dtype=object), allow_pickle=True)
         if rank == 0:
             np.save(os.path.join(out_dir, "batch.npy"), got.numpy())
             np.save(os.path.join(out_dir, "Q.npy"), Q.numpy())
@@ -124,3 +148,37 @@ def test_partition_elements_and_slices():
     assert (s0, s1, e0, e1) == (2, 4, 2, 10) and list(sub) == [0, 5, 8]
     with pytest.raises(ValueError):
         shard.partition_elements(5, 0)
+
+
+def test_pair_tiles_cover_the_upper_triangle_once():
+    for n, world in ((130, 2), (1000, 3), (7, 8), (64, 1), (0, 2)):
+        tiles = shard.pair_tiles(n, world)
+        assert len(tiles) == world
+        cover = np.zeros((n, n), dtype=int)
+        loads = []
+        for lst in tiles:
+            loads.append(sum(shard.tile_pairs(t) for t in lst))
+            for r0, r1, c0, c1 in lst:
+                assert r0 <= c0
+                blk = np.ones((r1 - r0, c1 - c0), dtype=int)
+                if (r0, r1) == (c0, c1):
+                    blk = np.triu(blk)
+                cover[r0:r1, c0:c1] += blk
+        assert np.array_equal(cover, np.triu(np.ones((n, n), dtype=int)))
+        if n >= 100 and world > 1:
+            assert max(loads) <= 1.6 * (n * (n + 1) // 2) / world     # balanced within one tile
+
+
+def test_allpairs_tiles_assemble_to_whole_matrix(gloo_run):
+    sig = _pair_sigs()
+    n = len(sig)
+    full = np.full((n, n), -1, dtype=np.int64)
+    for r in range(2):
+        for row in np.load(gloo_run / f"tiles{r}.npy", allow_pickle=True):
+            r0, r1, c0, c1 = (int(x) for x in row[:4])
+            cnt = np.asarray(row[4:], dtype=np.int64).reshape(r1 - r0, c1 - c0)
+            full[r0:r1, c0:c1] = np.where(full[r0:r1, c0:c1] < 0, cnt, full[r0:r1, c0:c1])
+    import oracle
+    ref = oracle.count_allpairs(sig).astype(np.int64)
+    iu = np.triu_indices(n)
+    assert np.array_equal(full[iu], ref[iu])
