@@ -310,7 +310,7 @@ pmh_status pmh_last_launches(pmh_handle h, int32_t *launches);
  * The paper's algorithms generate each element's points in increasing order
  * and stop once a point exceeds the running maximum of the signature
  * (Sec. "ProbMinHash1", stop rule).  The GPU kernels first generate only the
- * points below a threshold T (round 1: T = m (ln m + t_c) / sum of weights,
+ * points below a threshold T (first threshold round: T = m (ln m + t_c) / sum of weights,
  * which leaves a given component empty with probability about e^-t_c / m);
  * while a component is still empty they repeat with T x 4, and after `rounds`
  * finite rounds with T = infinity (the paper's unbounded loop).

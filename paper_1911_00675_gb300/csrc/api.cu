@@ -935,22 +935,28 @@ extern "C" pmh_status pmh_pminhash_batch(pmh_handle h, const uint64_t *ids, cons
 
 // ------------------------------------------------------------------ status reduction
 // Per-code item counts (codes outside 0..6 in slot 7) and the minimum of
-// (index << 8 | code) over the items that are not PMH_OK.
+// (index << 8 | code) over the items that are not PMH_OK.  Each thread counts
+// in registers, warps add their counts with one reduction per code, and each
+// warp adds to the global totals once per code (a shared or global atomic per
+// item would serialise on the one code nearly every item has).
 static __global__ void status_reduce_kernel(const int32_t *__restrict__ st, int64_t n, unsigned long long *out) {
-    __shared__ unsigned long long cnt[8];
-    if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
-    __syncthreads();
+    unsigned int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     unsigned long long first = ~0ull;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t c = st[i];
         const int slot = (c >= 0 && c <= 6) ? c : 7;
-        atomicAdd(&cnt[slot], 1ull);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cnt[j] += (slot == j) ? 1u : 0u;
         if (c != PMH_OK) first = min(first, ((unsigned long long)i << 8) | (unsigned long long)(slot == 7 ? 255 : c));
     }
     for (int o = 16; o; o >>= 1) first = min(first, __shfl_xor_sync(0xFFFFFFFFu, first, o));
-    if ((threadIdx.x & 31) == 0 && first != ~0ull) atomicMin(&out[8], first);
-    __syncthreads();
-    if (threadIdx.x < 8 && cnt[threadIdx.x]) atomicAdd(&out[threadIdx.x], cnt[threadIdx.x]);
+    const int lane = threadIdx.x & 31;
+    if (lane == 0 && first != ~0ull) atomicMin(&out[8], first);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const unsigned int t = __reduce_add_sync(0xFFFFFFFFu, cnt[j]);
+        if (lane == 0 && t) atomicAdd(&out[j], (unsigned long long)t);
+    }
 }
 
 extern "C" pmh_status pmh_sync_status(pmh_handle h, const int32_t *set_status, int64_t n, int64_t *counts,

@@ -10,12 +10,15 @@
 //
 // GPU design: one 256-thread block per set (blocks take sets from a counter);
 // each thread owns the components k = tid, tid + 256, ..., keeps their current
-// holder in shared memory (exact FP64 value, id, FP32 value), and walks the
-// set's elements in tiles of 256 staged in shared memory (key, FP32 scaled
-// 1/w, FP64 1/w, id).  Candidates are screened in FP32 (error within kEta of
-// the exact value, as in the ProbMinHash kernels); a candidate that may be
-// smaller than the holder is evaluated exactly in FP64 and compared
-// lexicographically, so the output equals the all-FP64 computation.
+// holder in shared memory (its FP32 value, its index in the set, and its exact
+// FP64 value once computed), and walks the set's elements in tiles of 256
+// staged in shared memory (key, FP32 scaled 1/w, FP64 1/w, id, index).
+// Candidates are compared in FP32 (within kEta of the exact values): one
+// clearly below the holder replaces it, one clearly above is dropped, and only
+// the rare candidate within the error margin of the holder is compared exactly
+// in FP64 (lexicographically with the id).  The output therefore equals the
+// all-FP64 computation, while FP64 work stays proportional to the near ties
+// (plus one exact value per component when out_q is asked for).
 #include "batch_common.cuh"
 
 using namespace pmh;
@@ -24,6 +27,7 @@ namespace {
 
 constexpr int kPmBlock = 256;
 constexpr int kPmTile = 256;
+constexpr uint32_t kNoHolder = 0xFFFFFFFFu;
 
 // One staged element.  winv32 = 2^sigma / w in FP32 (0: empty slot).  exact: the
 // scaled weight is below the FP32 range, so the element's values are always
@@ -33,8 +37,18 @@ struct __align__(16) PmElem {
     uint64_t id;
     double w_inv;
     float winv32;
+    uint32_t idx;      // index in the set
     int exact;
 };
+
+__device__ __forceinline__ double pm_exact(uint64_t key, double w_inv, uint64_t ctr) {
+    return __dmul_rn(w_inv, exp1_64(mix64(key + ctr)));
+}
+// Exact value of component k's current holder (element `idx` of the set at b).
+__device__ __forceinline__ double pm_holder_exact(const uint64_t *ids, const double *weights, int64_t b, uint32_t idx,
+                                                  uint64_t mixed_seed, uint64_t ctr) {
+    return pm_exact(mix64(ids[b + idx] ^ mixed_seed), __drcp_rn(weights[b + idx]), ctr);
+}
 
 __global__ void __launch_bounds__(kPmBlock) pminhash_kernel(const uint64_t *__restrict__ ids,
                                                             const double *__restrict__ weights,
@@ -43,12 +57,13 @@ __global__ void __launch_bounds__(kPmBlock) pminhash_kernel(const uint64_t *__re
                                                             uint64_t *__restrict__ out_ids, double *__restrict__ out_q,
                                                             int32_t *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem[];
-    double *bq = (double *)smem;
-    uint64_t *bz = (uint64_t *)(bq + m);
-    float *b32 = (float *)(bz + m);
-    PmElem *tile = (PmElem *)(smem + (((size_t)m * 20 + 15) & ~(size_t)15));
+    double *bx = (double *)smem;                 // holder's exact value (NaN: not computed yet)
+    uint32_t *bi = (uint32_t *)(bx + m);         // holder's index in the set (kNoHolder: none)
+    float *b32 = (float *)(bi + m);              // holder's FP32 value; sign bit set: an exact-only holder
+    PmElem *tile = (PmElem *)(smem + (((size_t)m * 16 + 15) & ~(size_t)15));
     __shared__ long long s_set;
-    __shared__ int s_sigma, s_bad, s_maxexp;
+    __shared__ int s_bad, s_maxexp;
+    const double kNaN = __longlong_as_double(0x7FF8000000000000ll);
     for (;;) {
         if (threadIdx.x == 0) s_set = (long long)atomicAdd(next_set, 1u);
         __syncthreads();
@@ -57,8 +72,8 @@ __global__ void __launch_bounds__(kPmBlock) pminhash_kernel(const uint64_t *__re
         const int64_t b = offsets[s], e = offsets[s + 1];
         if (threadIdx.x == 0) { s_bad = 0; s_maxexp = 0; }
         for (uint32_t k = threadIdx.x; k < m; k += kPmBlock) {
-            bq[k] = __longlong_as_double(0x7FF0000000000000ll);
-            bz[k] = 0;
+            bx[k] = kNaN;
+            bi[k] = kNoHolder;
             b32[k] = __int_as_float(0x7F800000);
         }
         __syncthreads();
@@ -98,6 +113,7 @@ __global__ void __launch_bounds__(kPmBlock) pminhash_kernel(const uint64_t *__re
                         el.id = ids[j];
                         el.key = mix64(el.id ^ mixed_seed);
                         el.w_inv = __drcp_rn(w);
+                        el.idx = (uint32_t)(j - b);
                         el.exact = ws_scaled(w, sigma) == 0.0f;
                         el.winv32 = el.exact ? 1.0f : winv_scaled(w, sigma);
                     }
@@ -107,38 +123,53 @@ __global__ void __launch_bounds__(kPmBlock) pminhash_kernel(const uint64_t *__re
             __syncthreads();
             const int cnt = (int)min((int64_t)kPmTile, e - t0);
             for (uint32_t k = threadIdx.x; k < m; k += kPmBlock) {
-                double best = bq[k];
-                uint64_t bid = bz[k];
-                float best32 = b32[k];
+                double hx = bx[k];
+                uint32_t hi = bi[k];
+                float h32 = b32[k];
                 const uint64_t ctr = ((uint64_t)k + 1) * kPhi;
                 for (int q = 0; q < cnt; ++q) {
                     const PmElem el = tile[q];
                     if (el.winv32 == 0.0f) continue;
                     const uint64_t word = mix64(el.key + ctr);
                     const float x32 = __fmul_rn(el.winv32, exp1_32(word));
-                    // may be below the holder: both FP32 values are within kEta of the exact scaled
-                    // ones, so x_c <= x_h implies x32_c (1 - eta) <= x32_h (1 + eta); 4 eta also
-                    // covers the rounding of the product
-                    if (el.exact || __fmul_rn(x32, 1.0f - 4.0f * kEta) <= best32) {
+                    // both FP32 values lie within kEta of the exact scaled ones; 4 kEta also covers
+                    // the products' rounding.  An exact-only element or holder is compared in FP64.
+                    const bool exact_path = el.exact || __float_as_int(h32) < 0;
+                    if (!exact_path && x32 < __fmul_rn(h32, 1.0f - 4.0f * kEta)) {
+                        h32 = x32;             // clearly below the holder (or no holder yet)
+                        hi = el.idx;
+                        hx = kNaN;
+                    } else if (exact_path || __fmul_rn(x32, 1.0f - 4.0f * kEta) <= h32) {
+                        // within the margin: compare the exact values, then the ids
                         const double x = __dmul_rn(el.w_inv, exp1_64(word));
-                        if (x < best || (x == best && el.id < bid)) {
-                            best = x;
-                            bid = el.id;
-                            // an exact-only holder: its scaled value rounded up (+inf beyond FP32)
-                            best32 = el.exact ? __double2float_ru(ldexp(x, sigma)) : x32;
+                        bool take = hi == kNoHolder;
+                        if (!take) {
+                            if (isnan(hx)) hx = pm_holder_exact(ids, weights, b, hi, mixed_seed, ctr);
+                            take = x < hx || (x == hx && el.id < ids[b + hi]);
+                        }
+                        if (take) {
+                            hx = x;
+                            hi = el.idx;
+                            // an exact-only holder keeps its scaled value rounded up, marked by the sign bit
+                            h32 = el.exact ? -__double2float_ru(ldexp(x, sigma)) : x32;
                         }
                     }
                 }
-                bq[k] = best;
-                bz[k] = bid;
-                b32[k] = best32;
+                bx[k] = hx;
+                bi[k] = hi;
+                b32[k] = h32;
             }
             __syncthreads();
         }
         for (uint32_t k = threadIdx.x; k < m; k += kPmBlock) {
-            const bool ok = !set_bad && !isinf(bq[k]);
-            out_ids[s * m + k] = ok ? bz[k] : 0;
-            if (out_q) out_q[s * m + k] = ok ? bq[k] : __longlong_as_double(0x7FF0000000000000ll);
+            const uint32_t hi = bi[k];
+            const bool ok = !set_bad && hi != kNoHolder;
+            out_ids[s * m + k] = ok ? ids[b + hi] : 0;
+            if (out_q) {
+                double q = __longlong_as_double(0x7FF0000000000000ll);
+                if (ok) q = isnan(bx[k]) ? pm_holder_exact(ids, weights, b, hi, mixed_seed, ((uint64_t)k + 1) * kPhi) : bx[k];
+                out_q[s * m + k] = q;
+            }
         }
         if (threadIdx.x == 0 && status) status[s] = set_bad ? PMH_ERR_BAD_WEIGHT : PMH_OK;
         __syncthreads();
@@ -153,7 +184,7 @@ __global__ void __launch_bounds__(kPmBlock) pminhash_kernel(const uint64_t *__re
 cudaError_t pmh::pminhash_launch(const uint64_t *ids, const double *weights, const int64_t *offsets, int64_t num_sets,
                                  uint32_t m, uint64_t seed, uint64_t *out_ids, double *out_q, int32_t *set_status,
                                  unsigned int *set_counter, int sm_count, cudaStream_t st, bool *fits) {
-    const size_t smem = (((size_t)m * 20 + 15) & ~(size_t)15) + (size_t)kPmTile * sizeof(PmElem);
+    const size_t smem = (((size_t)m * 16 + 15) & ~(size_t)15) + (size_t)kPmTile * sizeof(PmElem);
     *fits = true;
     cudaError_t e = cudaFuncSetAttribute(pminhash_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;

@@ -783,7 +783,9 @@ __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, 
                     if (!(y < 1e9f)) est = 1 << 30;
                     else if (FAM == 1 || FAM == 2) {
                         const float mu = fmaxf(y, 0.0f);
-                        est = (int)(mu + PMH_EST_SIGMAS * (mu > 0.0f ? mu * rsqrtf(mu) : 0.0f) + 2.0f);
+                        float sd_part = 0.0f;   // the standard deviation's share, only when asked for
+                        if constexpr (PMH_EST_SIGMAS != 0.0f) sd_part = PMH_EST_SIGMAS * (mu > 0.0f ? mu * rsqrtf(mu) : 0.0f);
+                        est = (int)(mu + sd_part + 2.0f);
                     }
                     else if (FAM == 3 || c.unw) est = (int)y;
                     else est = (int)((float)m * (1.0f - __expf(-T.lambda1_32 * y)) * 1.001f) + 1;
