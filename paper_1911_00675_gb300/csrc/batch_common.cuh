@@ -212,7 +212,9 @@ static __global__ void queue_scatter(const int64_t *off, int64_t num_sets, int32
 // FP64 exponent it has seen; a weight enters as the FP32 number with its top
 // 23 mantissa bits and exponent shifted by -me (integer operations only), and
 // a larger exponent rescales acc by a power of two.  Weights below 2^-126 of
-// the running maximum (and subnormals) add nothing.
+// the running maximum (and subnormals) add nothing.  Weights in [2^-100, 2^90)
+// (nearly all in practice) skip the rescaling: they go to a plain FP32 sum
+// (two integer operations and an add), folded into the scaled one at the end.
 struct ScaledSum {
     int me = -1000;   // running maximum biased exponent (none yet)
     float acc = 0.0f;
@@ -239,10 +241,21 @@ __device__ __forceinline__ void scaled_merge(ScaledSum &s, int me2, float acc2) 
 // valid in thread 0.
 struct StatPart {
     ScaledSum sum;
+    float fsum = 0.0f;   // the weights in [2^-100, 2^90), summed as plain FP32
     unsigned int np = 0;
     int bad = 0;
 };
+// Biased FP64 exponents of the plain FP32 sum: [kFastLo, kFastHi) (2^-100 <= w < 2^90, so a
+// thread's sum of at most 2^20 of them stays finite).
+constexpr uint32_t kFastLo = 923, kFastHi = 1113;
 __device__ __forceinline__ void stat_one(StatPart &r, uint64_t x) {
+    // common case: a positive weight in the fast range enters as the FP32 number with its top 23
+    // mantissa bits (bits 29..60 of the double, exponent re-biased from 1023 to 127)
+    if ((uint32_t)(x >> 32) - (kFastLo << 20) < ((kFastHi - kFastLo) << 20)) {
+        r.fsum = __fadd_rn(r.fsum, __uint_as_float((uint32_t)(x >> 29) - (896u << 23)));
+        r.np++;
+        return;
+    }
     const int ex = (int)(x >> 52) & 0x7FF;
     const bool neg = (x >> 63) != 0;
     const bool zero = (x << 1) == 0;
@@ -285,6 +298,7 @@ __device__ __forceinline__ StatPart block_stats(const unsigned long long *wb, in
         }
     }
     if (a + 2 * np2 < e && threadIdx.x == 0) stat_one(r, __ldcs(wb + e - 1));
+    if (r.fsum != 0.0f) scaled_add(r.sum, (uint64_t)__double_as_longlong((double)r.fsum));
     for (int o = 16; o; o >>= 1) {
         const int me2 = __shfl_xor_sync(0xFFFFFFFFu, r.sum.me, o);
         const float acc2 = __shfl_xor_sync(0xFFFFFFFFu, r.sum.acc, o);

@@ -71,7 +71,7 @@ constexpr int kGridCont = 1024;         // contender records per grid item
 constexpr uint64_t kSkipBit = 1ull << 63;   // queue entry taken by grid mode
 
 struct GridState {
-    unsigned int next_chunk;
+    unsigned int next_chunk;       // next chunk (general pass) or 128-element block (aligned inputs) to claim
     unsigned int done;             // CTAs finished with the item
     unsigned int bound32;          // shared stop bound (float bits, scaled)
     int status;
@@ -610,6 +610,9 @@ __device__ __forceinline__ bool push_redo(const SketchParams &P, int item_v, int
 #endif
 #ifndef PMH_FILTER_WS
 #define PMH_FILTER_WS 1         // filter compares U against bound * w (no reciprocal for rejected elements)
+#endif
+#ifndef PMH_GRID_LEAN
+#define PMH_GRID_LEAN 1         // grid mode: the trimmed filter pass (grid_pass) for 16-byte aligned inputs
 #endif
 #ifndef PMH_EST_SIGMAS
 #define PMH_EST_SIGMAS 0.0f     // ProbMinHash1/2: deep mode when mean + this many sd of the point count (+2) reach the cap
@@ -1199,6 +1202,7 @@ __device__ void grid_finalize(Ctx<F32> &c, GridState *g, void *gsig_v, int item_
     __syncthreads();
     // a component left empty: redo the item in this CTA with growing thresholds
     int empty = 0;
+#pragma unroll 4
     for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
         if constexpr (F32) empty |= __ldcg(&((const unsigned long long *)gsig_v)[k]) == kEmptyKey;
         else empty |= isinf(__ldcg(&((const Rec64 *)gsig_v)[k].q));
@@ -1213,9 +1217,21 @@ __device__ void grid_finalize(Ctx<F32> &c, GridState *g, void *gsig_v, int item_
     if constexpr (F32) {
         // L2 loads: other CTAs wrote the global signature
         const unsigned long long *gsig = (const unsigned long long *)gsig_v;
-        for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
-            const uint64_t key = __ldcg(&gsig[k]);
-            P.out_ids[out_row * m + k] = (key == kEmptyKey || st != PMH_OK) ? 0 : P.ids[c.beg + (uint32_t)(key & 0xFFFFFFFFu)];
+        // eight components per thread in flight: the id gathers of one thread do not wait on each other
+        constexpr int kU = 8;
+        for (uint32_t k0 = threadIdx.x; k0 < m; k0 += kU * blockDim.x) {
+            uint64_t idv[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint32_t k = k0 + u * blockDim.x;
+                const uint64_t key = k < m ? __ldcg(&gsig[k]) : kEmptyKey;
+                idv[u] = (key == kEmptyKey || st != PMH_OK) ? 0 : P.ids[c.beg + (uint32_t)(key & 0xFFFFFFFFu)];
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint32_t k = k0 + u * blockDim.x;
+                if (k < m) P.out_ids[out_row * m + k] = idv[u];
+            }
         }
         if (P.out_q) {
             for (uint32_t k = tw; k < m; k += team_warps) {
@@ -1238,6 +1254,176 @@ __device__ void grid_finalize(Ctx<F32> &c, GridState *g, void *gsig_v, int item_
     }
     if (threadIdx.x == 0 && P.status) P.status[out_row] = st;
     (void)ts;
+}
+
+// Expansion of a grid-mode warp's buffered survivors to the end of their
+// sequences.  (Kept inline: out of line, with the call's register saves, the
+// grid kernel on one set of 1e8 took 0.678 ms instead of 0.614.)
+template <int FAM, bool F32, bool REJ>
+__device__ __forceinline__ bool grid_expand(Ctx<F32> &c, int n) {
+    SeqLane<F32> L;
+    L.has = false;
+    return process_survivors<FAM, F32, REJ>(c, L, n, true);
+}
+
+// Grid mode's pass over all elements of one item by this warp, which claims
+// runs of 128-element blocks from the item's counter (no barrier of the CTA
+// until the pass ends).  A huge set's elements almost all fail the filter (the
+// survivors number about m (ln m + c) per item, against 1e6 and more
+// elements), so the common path is the filter alone: every lane takes four
+// elements of a block from two 16-byte loads of ids and two of weights (ids and
+// weights 16-byte aligned; blocks start at an even element of the whole
+// input), and a block without survivors costs one vote.  A block with
+// survivors appends them to the warp's buffer (their keys and scaled weights
+// computed again there) and expands it as run_range does, except that every
+// expansion runs its sequences to the end (no lane state outlives it, so none
+// is live in the common path).
+template <int FAM, bool F32, bool REJ>
+__device__ void grid_pass(Ctx<F32> &c, GridState *gs) {
+    const SketchParams &P = *c.p;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = blockDim.x >> 5;
+    TeamShared *ts = c.ts;
+    WarpShared *ws = c.ws;
+    const bool rej = REJ && c.rej;
+    const float te_lo = (FAM >= 3 && !c.unw && !rej) ? P.tab.te_lo : 1.0f;
+    const float u1 = rej ? P.tab.rej_u1_32 : 2.0f;
+    const uint64_t mseed = P.mixed_seed;
+    const int sigma = c.sigma;
+    const bool unw = c.unw;
+    const float ws1 = ws_scaled(1.0, sigma);   // binary weights: every element counts 1
+    const bool counting = P.counters != nullptr;
+    if (lane == 0) { ws->sb_n = 0; ws->dq_n = 0; }
+    __syncwarp();
+    int n = 0;
+    const uint64_t g_lo = (uint64_t)c.beg, g_hi = (uint64_t)c.beg + c.n;
+    const uint64_t g0 = g_lo & ~1ull;
+    const uint32_t nblk = (uint32_t)((g_hi - g0 + 127) / 128);
+    const ulonglong2 *ids2 = (const ulonglong2 *)P.ids;
+    const ulonglong2 *w2 = (const ulonglong2 *)P.weights;
+    // claims of kb blocks: about eight per warp of the launch, at most 16 blocks (2048 elements;
+    // claims shrinking towards the end measured no faster on one set of 1e8)
+    const uint32_t warps_all = gridDim.x * nwarps;
+    const uint32_t kb = max(1u, min(16u, nblk / (8u * warps_all)));
+    uint32_t b = 0, bend = 0, step = 0;
+    for (;;) {
+        if (b >= bend) {
+            unsigned cl = 0;
+            if (lane == 0) cl = atomicAdd(&gs->next_chunk, kb);
+            cl = __shfl_sync(kFull, cl, 0);
+            b = cl;
+            bend = cl < nblk ? min(cl + kb, nblk) : cl;
+        }
+        const bool fin = b >= nblk;
+        const uint64_t gb = g0 + (uint64_t)b * 128;
+        ulonglong2 wp[2], ip[2];   // this lane's pairs: elements gb + 64 h + 2 lane + {0, 1}
+        unsigned sm = 0;           // bit j: element j of this lane (j = 2 h + s) survives
+        if (!fin) {
+            // every 16 blocks the bound published by the other CTAs of the item (read here,
+            // adopted after the filter, so that the load's latency hides behind it)
+            const bool adopt = c.gbound32 && (step & 15) == 0 && lane == 0;
+            unsigned gb32 = 0;
+            unsigned long long gb64 = 0;
+            if (adopt) {
+                gb32 = (unsigned)ld_volatile((const int *)c.gbound32);
+                if constexpr (!F32) gb64 = ld_volatile((const uint64_t *)c.gbound64);
+            }
+            const float b32 = ld_volatile(&ts->bound32);
+            // the item's elements relative to the block: [rlo, rhi) within [0, 128]
+            const uint32_t rlo = gb < g_lo ? (uint32_t)(g_lo - gb) : 0u;
+            const uint32_t rhi = g_hi - gb < 128 ? (uint32_t)(g_hi - gb) : 128u;
+            // pairs p0 and p0 + 32; a pair whose second element lies past the item's last
+            // element is read as its first element alone
+            const uint64_t p0 = (gb >> 1) + lane;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint64_t pe = 2 * (p0 + 32 * h);
+                wp[h] = ip[h] = make_ulonglong2(0ull, 0ull);
+                if (pe + 1 < g_hi) { wp[h] = __ldcs(w2 + (pe >> 1)); ip[h] = __ldcs(ids2 + (pe >> 1)); }
+                else if (pe < g_hi) { wp[h].x = __ldcs(&w2[pe >> 1].x); ip[h].x = __ldcs(&ids2[pe >> 1].x); }
+            }
+            unsigned nvalid = 0, nsurv = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t r = 64 * (j >> 1) + 2 * lane + (j & 1);   // element gb + r
+                const uint64_t wb = (j & 1) ? wp[j >> 1].y : wp[j >> 1].x;
+                const double w = __longlong_as_double((long long)wb);
+                const bool valid = r >= rlo && r < rhi && weight_positive(w);
+                bool surv = false;
+                if (valid) {
+                    const uint64_t key = mix64(((j & 1) ? ip[j >> 1].y : ip[j >> 1].x) ^ mseed);
+                    const float u = unif_lo(value_word(key, 1));
+                    const float ulo = __fmul_rn(u, te_lo);
+                    surv = !(__fmul_rn(ulo, 1.0f - 16.0f * 0x1p-24f) > __fmul_rn(b32, unw ? ws1 : ws_scaled(w, sigma)));
+                    if constexpr (REJ) surv = surv || !(u < u1);
+                }
+                sm |= (unsigned)surv << j;
+                if (counting) {
+                    nvalid += popc_ballot(valid);
+                    nsurv += popc_ballot(surv);
+                }
+            }
+            if (counting) {
+                count(c, PMH_CNT_ELEMENTS, nvalid);
+                count(c, PMH_CNT_PREFILTERED, nvalid - nsurv);
+            }
+            if (adopt) {
+                atomic_min_pos_float(&ts->bound32, __uint_as_float(gb32));
+                if constexpr (!F32) atomic_min_pos_double(&ts->bound64, __longlong_as_double((long long)gb64));
+            }
+        }
+        // rare path: this block has survivors, or the pass ends with some buffered
+        if (fin ? n > 0 : __any_sync(kFull, sm != 0)) {
+            bool pending = !fin;   // this block's survivors are not in the buffer yet
+            bool any_win = false;
+            for (;;) {
+                if (pending) {
+                    unsigned msk[4];
+                    int cnt = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        msk[j] = __ballot_sync(kFull, (sm >> j) & 1u);
+                        cnt += __popc(msk[j]);
+                    }
+                    if (n + cnt <= kSurvCap) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            if ((sm >> j) & 1u) {
+                                const int pos = n + __popc(msk[j] & ((1u << lane) - 1u));
+                                const uint64_t g = gb + 64 * (j >> 1) + 2 * lane + (j & 1);
+                                const double w = __longlong_as_double((long long)((j & 1) ? wp[j >> 1].y : wp[j >> 1].x));
+                                ws->sb_e[32 + pos] = (uint32_t)(g - (uint64_t)c.beg);
+                                ws->sb_key[pos] = mix64(((j & 1) ? ip[j >> 1].y : ip[j >> 1].x) ^ mseed);
+                                ws->sb_winv[pos] = unw ? ws1 : ws_scaled(w, sigma);
+                            }
+                            n += __popc(msk[j]);
+                        }
+                        pending = false;
+                        __syncwarp();
+                    }
+                }
+                // expand when the buffer holds a batch, cannot take this block, or the pass ends
+                if (!pending && !(fin ? n > 0 : n >= kSurvBatch)) break;
+                any_win |= grid_expand<FAM, F32, REJ>(c, n);
+                n = 0;
+            }
+            if (any_win) {
+                const int uf = __shfl_sync(kFull, lane == 0 ? ld_volatile(&ts->unfilled) : 1, 0);
+                if (uf == 0) {
+                    refresh_bound<F32>(c);
+                    if (c.gbound32 && lane == 0) {   // publish this CTA's q_max bound
+                        atomicMin((int *)c.gbound32, __float_as_int(ld_volatile(&ts->bound32)));
+                        if constexpr (!F32) atomicMin(c.gbound64, (unsigned long long)__double_as_longlong(ld_volatile(&ts->bound64)));
+                    }
+                }
+            }
+        }
+        if (fin) break;
+        ++b;
+        ++step;
+    }
+    if (lane == 0) ws->sb_n = 0;
+    __syncwarp();
 }
 
 // One CTA's share of a grid item: chunks of the item's elements with a local
@@ -1282,9 +1468,16 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
     c.gbound32 = &g->bound32;
     c.gbound64 = &g->bound64;
     if (live) {
+        // the trimmed filter needs 16-byte aligned ids and weights (else run_range's, chunk by chunk)
+        const bool lean = PMH_GRID_LEAN && ((((uintptr_t)P.ids) | ((uintptr_t)P.weights)) & 15u) == 0;
+        const long long t_pass = clock64();
         uint64_t chunk = (uint64_t)c.n / (4ull * gridDim.x);
         chunk = chunk < kGridChunkMin ? kGridChunkMin : (chunk > kGridChunk ? kGridChunk : chunk);
-        for (;;) {
+        if (lean) {
+            grid_pass<FAM, F32, REJ>(c, g);
+            __syncthreads();
+        }
+        for (; !lean;) {
             if (leader) {
                 const unsigned int idx = atomicAdd(&g->next_chunk, 1u);
                 ts->item_idx = (int)idx;
@@ -1298,6 +1491,7 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
             run_range<FAM, F32, 8, REJ>(c, (uint32_t)lo, hi);
             __syncthreads();
         }
+        count(c, PMH_CNT_CYC_FIRST, (unsigned long long)(clock64() - t_pass));
         // merge the local signature into the item's global one
         for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
             if constexpr (F32) {
@@ -1327,21 +1521,27 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
     __syncthreads();
     if (last) {
         __threadfence();
+        const long long t_f = clock64();
         grid_finalize<FAM, F32, REJ>(c, g, gsig_v, item_v, set);
+        count(c, PMH_CNT_CYC_FINISH, (unsigned long long)(clock64() - t_f));
     }
     c.gbound32 = nullptr;
     c.gbound64 = nullptr;
 }
 
 // Persistent grid-mode kernel of one family: every CTA takes part in every
-// grid item of that family, in list order.  Registers are budgeted for four
-// 8-warp CTAs per SM (32 warps): the filter that dominates a huge set is
-// latency bound, so warps count more than the few spills.
-#ifndef PMH_GRID_MINB
-#define PMH_GRID_MINB 4
+// grid item of that family, in list order.  Registers are budgeted for three
+// 8-warp CTAs per SM in FP32 (80 registers) and two in FP64 (128): the filter
+// that dominates a huge set issues fewer instructions with fewer spills, and
+// the FP64 expansion needs the registers.
+#ifndef PMH_GRID_MINB32
+#define PMH_GRID_MINB32 3
+#endif
+#ifndef PMH_GRID_MINB64
+#define PMH_GRID_MINB64 2
 #endif
 template <bool F32, int FAM, bool REJ = false>
-__global__ void __launch_bounds__(256, PMH_GRID_MINB) grid_kernel(const __grid_constant__ SketchParams p) {
+__global__ void __launch_bounds__(256, F32 ? PMH_GRID_MINB32 : PMH_GRID_MINB64) grid_kernel(const __grid_constant__ SketchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool kPerm = (FAM == 2 || FAM == 4);
     constexpr int NW = 8;

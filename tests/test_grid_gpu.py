@@ -12,7 +12,7 @@ import pytest
 import torch
 
 from paper_1911_00675_gb300 import workloads as W
-from parity_util import VARS, assert_near_tie_rate, check_sets, run
+from parity_util import VARS, assert_near_tie_rate, check_sets, run, to_dev
 
 pytestmark = pytest.mark.gpu
 GRID_MIN = 40_000
@@ -120,6 +120,30 @@ def test_grid_bad_and_zero_weight_sets(grid):
         assert (z[:, 1] == 0).all() and np.isinf(q[:, 1]).all()       # empty signature
         for vi, v in enumerate(["1", "4"]):
             check_sets(bb, v, z[vi], q[vi], [2, 3], seed=3)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+def test_grid_inputs_off_the_16_byte_grid(grid, precision):
+    # 16-byte aligned ids and weights take the trimmed grid-mode filter (two elements per load),
+    # inputs at an 8-byte offset the general one: the same signatures, q and statuses; grid sets
+    # that start at an odd element, a ragged end and every variant family
+    b = W.random_batch(39, [GRID_MIN + 3, 5, 2 * GRID_MIN + 1, GRID_MIN + 64], 512, "lognormal")
+    ids, w, off = to_dev(b)
+    ids_u = torch.empty(ids.numel() + 1, dtype=ids.dtype, device=ids.device)[1:]
+    w_u = torch.empty(w.numel() + 1, dtype=w.dtype, device=w.device)[1:]
+    ids_u.copy_(ids)
+    w_u.copy_(w)
+    assert ids.data_ptr() % 16 == 0 and w.data_ptr() % 16 == 0
+    assert ids_u.data_ptr() % 16 == 8 and w_u.data_ptr() % 16 == 8
+    za, qa, sa = grid.sketch_batch(ids, w, off, b.m, VARS, precision, 6, with_q=True)
+    zb, qb, sb = grid.sketch_batch(ids_u, w_u, off, b.m, VARS, precision, 6, with_q=True)
+    torch.cuda.synchronize()
+    assert int(sa.abs().sum()) == 0
+    assert torch.equal(za, zb) and torch.equal(qa, qb) and torch.equal(sa, sb)
+    from paper_1911_00675_gb300 import pmh
+    z, q = pmh.to_u64(za), qa.cpu().numpy()
+    for vi, v in enumerate(VARS):
+        check_sets(b, v, z[vi], q[vi], [0, 2, 3], seed=6)
 
 
 def test_launch_count_reported(H):
