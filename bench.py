@@ -51,12 +51,13 @@ OPS_PAIR_COMPONENT = 3  # equal-component count: two 32-bit compares and one add
 # 8-bit codes, per pair of 64-bit words (8 fields): xor (2), per 32-bit half three fold steps of
 # shift + or (6) and and-not + popcount (2), two adds (2)
 OPS_BBIT_WORD = 2 + 2 * (6 + 2) + 2
-# DRAM bytes (read + write) of the four family sketch kernels per element-variant, from the ncu
-# capture summarised in profiles/sketch_kernel_c2_2000sets_full.md; the traffic grows in
-# proportion to the elements (one pass over ids and weights per family).
-TRAFFIC_BYTES_PER_ELEMENT_VARIANT = 13.95
+# DRAM bytes (read + write) of the four family sketch kernels and their redo kernels per
+# element-variant, from the ncu capture summarised in profiles/sketch_kernel_fp32_c2_2000sets.md
+# (1,387.6 MB for 99,379,884 element-variants); the traffic grows in proportion to the elements
+# (one pass over ids and weights per family).
+TRAFFIC_BYTES_PER_ELEMENT_VARIANT = 13.96
 TRAFFIC_BASIS = ("ncu dram bytes per element-variant on a 2,000-set c2-shaped batch (kernel source of commit "
-                 "305e05b) x this step's work")
+                 "75980f0) x this step's work")
 
 
 def parse():
