@@ -1266,6 +1266,19 @@ __device__ __forceinline__ bool grid_expand(Ctx<F32> &c, int n) {
     return process_survivors<FAM, F32, REJ>(c, L, n, true);
 }
 
+// One lane's pairs of a grid-mode block starting at element gb of the whole input: pairs
+// (gb >> 1) + lane and + 32; a pair whose second element lies at or past g_hi is read as its
+// first element alone, and one wholly past it as zeros.
+__device__ __forceinline__ void grid_load_pairs(const ulonglong2 *w2, const ulonglong2 *ids2, uint64_t gb, uint64_t g_hi,
+                                                int lane, ulonglong2 &w0, ulonglong2 &w1, ulonglong2 &i0, ulonglong2 &i1) {
+    const uint64_t pe = gb + 2 * (uint64_t)lane;
+    w0 = w1 = i0 = i1 = make_ulonglong2(0ull, 0ull);
+    if (pe + 1 < g_hi) { w0 = __ldcs(w2 + (pe >> 1)); i0 = __ldcs(ids2 + (pe >> 1)); }
+    else if (pe < g_hi) { w0.x = __ldcs(&w2[pe >> 1].x); i0.x = __ldcs(&ids2[pe >> 1].x); }
+    if (pe + 65 < g_hi) { w1 = __ldcs(w2 + (pe >> 1) + 32); i1 = __ldcs(ids2 + (pe >> 1) + 32); }
+    else if (pe + 64 < g_hi) { w1.x = __ldcs(&w2[(pe >> 1) + 32].x); i1.x = __ldcs(&ids2[(pe >> 1) + 32].x); }
+}
+
 // Grid mode's pass over all elements of one item by this warp, which claims
 // runs of 128-element blocks from the item's counter (no barrier of the CTA
 // until the pass ends).  A huge set's elements almost all fail the filter (the
@@ -1305,15 +1318,16 @@ __device__ void grid_pass(Ctx<F32> &c, GridState *gs) {
     // claims shrinking towards the end measured no faster on one set of 1e8)
     const uint32_t warps_all = gridDim.x * nwarps;
     const uint32_t kb = max(1u, min(16u, nblk / (8u * warps_all)));
+    auto claim = [&](uint32_t &x, uint32_t &xend) {
+        unsigned cl = 0;
+        if (lane == 0) cl = atomicAdd(&gs->next_chunk, kb);
+        cl = __shfl_sync(kFull, cl, 0);
+        x = cl;
+        xend = cl < nblk ? min(cl + kb, nblk) : cl;
+    };
     uint32_t b = 0, bend = 0, step = 0;
     for (;;) {
-        if (b >= bend) {
-            unsigned cl = 0;
-            if (lane == 0) cl = atomicAdd(&gs->next_chunk, kb);
-            cl = __shfl_sync(kFull, cl, 0);
-            b = cl;
-            bend = cl < nblk ? min(cl + kb, nblk) : cl;
-        }
+        if (b >= bend) claim(b, bend);
         const bool fin = b >= nblk;
         const uint64_t gb = g0 + (uint64_t)b * 128;
         ulonglong2 wp[2], ip[2];   // this lane's pairs: elements gb + 64 h + 2 lane + {0, 1}
@@ -1332,16 +1346,7 @@ __device__ void grid_pass(Ctx<F32> &c, GridState *gs) {
             // the item's elements relative to the block: [rlo, rhi) within [0, 128]
             const uint32_t rlo = gb < g_lo ? (uint32_t)(g_lo - gb) : 0u;
             const uint32_t rhi = g_hi - gb < 128 ? (uint32_t)(g_hi - gb) : 128u;
-            // pairs p0 and p0 + 32; a pair whose second element lies past the item's last
-            // element is read as its first element alone
-            const uint64_t p0 = (gb >> 1) + lane;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint64_t pe = 2 * (p0 + 32 * h);
-                wp[h] = ip[h] = make_ulonglong2(0ull, 0ull);
-                if (pe + 1 < g_hi) { wp[h] = __ldcs(w2 + (pe >> 1)); ip[h] = __ldcs(ids2 + (pe >> 1)); }
-                else if (pe < g_hi) { wp[h].x = __ldcs(&w2[pe >> 1].x); ip[h].x = __ldcs(&ids2[pe >> 1].x); }
-            }
+            grid_load_pairs(w2, ids2, gb, g_hi, lane, wp[0], wp[1], ip[0], ip[1]);
             unsigned nvalid = 0, nsurv = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
