@@ -56,6 +56,11 @@ OPS_BBIT_WORD = 2 + 2 * (6 + 2) + 2
 # (1,387.6 MB for 99,379,884 element-variants); the traffic grows in proportion to the elements
 # (one pass over ids and weights per family).
 TRAFFIC_BYTES_PER_ELEMENT_VARIANT = 13.96
+# Pipe use of the same four family kernels in that capture (per kernel, min-max over the families):
+# what binds them beside the op model above.
+NCU_SKETCH = {"issue_active_pct": [54.9, 62.7], "alu_pipe_pct": [41.3, 50.6], "fma_pipe_pct": [15.8, 19.5],
+              "dram_throughput_pct": [1.7, 3.3], "active_lanes_per_inst": [25.1, 28.1],
+              "warp_inst_per_element_variant": 21.3, "source": "profiles/sketch_kernel_fp32_c2_2000sets.md"}
 TRAFFIC_BASIS = ("ncu dram bytes per element-variant on a 2,000-set c2-shaped batch (kernel source of commit "
                  "75980f0) x this step's work")
 
@@ -660,7 +665,8 @@ def main():
                 "kernel_ms": k_avg, "kernel_ms_basis": "library CUDA events around the sketch kernels of each "
                                                          "profiled call (the second timed pass)",
                 "ops_per_launch": per_launch_ops,
-                "peak_basis": f"{n_sms} SMs x {LANES_PER_SM_CLK} lane-ops/clk x {sm_mhz:.0f} MHz (median under load)"}
+                "peak_basis": f"{n_sms} SMs x {LANES_PER_SM_CLK} lane-ops/clk x {sm_mhz:.0f} MHz (median under load)",
+                "ncu": NCU_SKETCH}
 
     # ---------------- queue build + set statistics: one read of offsets (x3) and weights
     peaks = measured_peaks()

@@ -146,6 +146,26 @@ def test_grid_inputs_off_the_16_byte_grid(grid, precision):
         check_sets(b, v, z[vi], q[vi], [0, 2, 3], seed=6)
 
 
+def test_grid_counters_count_every_element_once(grid):
+    # the grid pass counts each element with w > 0 once per variant (a zero weight not at all),
+    # and the elements it rejected without a logarithm among them
+    from paper_1911_00675_gb300 import pmh
+    b = W.random_batch(40, [GRID_MIN + 11, 2 * GRID_MIN + 3], 256, "lognormal")
+    w = b.weights.copy()
+    w[b.offsets[0] + 5] = 0.0
+    w[b.offsets[1] + 7] = 0.0
+    bb = W.Batch(b.ids, w, b.offsets, b.m)
+    cnt = torch.zeros(len(pmh.COUNTERS), dtype=torch.int64, device="cuda")
+    z, q, st = run(grid, bb, ["1", "3a"], 1, seed=2, counters=cnt)
+    _status_ok(st)
+    c = dict(zip(pmh.COUNTERS, cnt.cpu().tolist()))
+    npos = int((w > 0).sum())
+    assert c["rounds"] > 0 or c["elements"] == 2 * npos
+    assert 0 < c["prefiltered"] < c["elements"] and c["points32"] > 0
+    for vi, v in enumerate(["1", "3a"]):
+        check_sets(bb, v, z[vi], q[vi], [0, 1], seed=2)
+
+
 def test_launch_count_reported(H):
     b = W.random_batch(37, [10, 20], 64, "uniform")
     H.set_thresholds(grid_min=0)
