@@ -589,7 +589,7 @@ def main():
         for _ in range(2):
             e2e_step()
         barrier()
-        ksteps = max(3, args.steps // 2)
+        ksteps = max(3, args.steps)
         t0 = time.perf_counter()
         spans, walls = [], []
         for _ in range(ksteps):
