@@ -82,7 +82,9 @@ enum {
     PMH_CNT_ROUNDS = 5,       /* threshold rounds beyond the first */
     PMH_CNT_DEEP = 6,         /* elements processed warp-cooperatively */
     PMH_CNT_PREFILTERED = 7,  /* elements rejected without evaluating a logarithm */
-    /* SM clock cycles spent per phase, summed over warps (timers read by lane 0) */
+    /* SM clock cycles spent per phase, summed over warps (timers read by lane 0); recorded only
+     * by a library built with -DPMH_CYCLE_COUNTERS=1 (their clock reads cost about 6 % of the
+     * sketch kernels' time), else left unchanged */
     PMH_CNT_CYC_PASS0 = 8,    /* item setup: empty signature, threshold */
     PMH_CNT_CYC_FIRST = 9,    /* threshold rounds: filter, survivors, deep mode, team barrier at their end */
     PMH_CNT_CYC_DEEP = 10,    /* warp-cooperative expansion of long sequences (part of CYC_SURV) */

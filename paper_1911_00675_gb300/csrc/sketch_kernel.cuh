@@ -218,6 +218,27 @@ __device__ __forceinline__ void count(Ctx<F32> &c, int idx, unsigned long long v
     if (c.p->counters && (threadIdx.x & 31) == 0) c.ws->cnt[idx] += v;
 }
 __device__ __forceinline__ unsigned popc_ballot(bool b) { return __popc(__ballot_sync(kFull, b)); }
+// Per-phase cycle counters (PMH_CNT_CYC_*): a diagnostic, compiled in only with
+// PMH_CYCLE_COUNTERS=1.  The clock reads and the 64-bit stamps they keep live
+// cost about 6 % of the sketch kernels' time on c2 (more register spills).
+#ifndef PMH_CYCLE_COUNTERS
+#define PMH_CYCLE_COUNTERS 0
+#endif
+__device__ __forceinline__ long long cyc_now() {
+#if PMH_CYCLE_COUNTERS
+    return clock64();
+#else
+    return 0;
+#endif
+}
+template <bool F32>
+__device__ __forceinline__ void count_cyc(Ctx<F32> &c, int idx, long long t0) {
+#if PMH_CYCLE_COUNTERS
+    count(c, idx, (unsigned long long)(clock64() - t0));
+#else
+    (void)c; (void)idx; (void)t0;
+#endif
+}
 
 // ------------------------------------------------------------ offers
 template <bool F32> struct Offer;
@@ -285,7 +306,7 @@ template <bool F32>
 __device__ void refresh_bound(Ctx<F32> &c) {
     const int lane = threadIdx.x & 31;
     const uint32_t m = c.p->m;
-    const long long t0 = clock64();
+    const long long t0 = cyc_now();
     if constexpr (F32) {
         const uint64_t *sig = (const uint64_t *)c.sig;
         uint32_t mx = 0;
@@ -302,7 +323,7 @@ __device__ void refresh_bound(Ctx<F32> &c) {
             atomic_min_pos_float(&c.ts->bound32, __double2float_ru(ldexp(mx, c.sigma)));
         }
     }
-    count(c, PMH_CNT_CYC_REFRESH, (unsigned long long)(clock64() - t0));
+    count_cyc(c, PMH_CNT_CYC_REFRESH, t0);
 }
 
 // ------------------------------------------------------------ Fisher-Yates group
@@ -652,7 +673,7 @@ struct SeqLane {
 // on entry).  fin: the last call of the pass (every sequence ends in it).
 template <int FAM, bool F32, bool REJ>
 __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, int n, bool fin) {
-    const long long t_sv = clock64();
+    const long long t_sv = cyc_now();
     const SketchParams &P = *c.p;
     const Tables &T = P.tab;
     const uint32_t m = P.m;
@@ -819,14 +840,14 @@ __device__ __forceinline__ bool process_survivors(Ctx<F32> &c, SeqLane<F32> &L, 
     // ---- deep mode for the long sequences (ProbMinHash2/4: once no lane holds a write list)
     const int total_deep = min(ws->dq_n, 32 + kSurvCap);
     if (total_deep && (!kPerm || !__any_sync(kFull, L.has))) {
-        const long long td = clock64();
+        const long long td = cyc_now();
         for (int j = 0; j < total_deep; ++j) deep<FAM, F32, false, REJ>(c, ws->sb_e[j], 0);
-        count(c, PMH_CNT_CYC_DEEP, (unsigned long long)(clock64() - td));
+        count_cyc(c, PMH_CNT_CYC_DEEP, td);
         __syncwarp();
         if (lane == 0) ws->dq_n = 0;
         __syncwarp();
     }
-    count(c, PMH_CNT_CYC_SURV, (unsigned long long)(clock64() - t_sv));
+    count_cyc(c, PMH_CNT_CYC_SURV, t_sv);
     return __any_sync(kFull, won);
 }
 
@@ -1010,7 +1031,7 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
     WarpShared *ws = c.ws;
     const bool leader = (tt == 0);
     const int64_t out_row = (int64_t)item_v * P.num_sets + set;
-    long long t_ph = clock64();
+    long long t_ph = cyc_now();
     count(c, PMH_CNT_ITEMS, tw == 0);
 
     // ---- init: empty signature; T = m (ln m + c) / sum(w) = t_s * 2^-sigma, t_s in [1, 2)
@@ -1050,8 +1071,8 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
         if (leader && P.status) P.status[out_row] = st0.bad ? PMH_ERR_BAD_WEIGHT : PMH_OK;
         return;
     }
-    count(c, PMH_CNT_CYC_PASS0, (unsigned long long)(clock64() - t_ph));
-    t_ph = clock64();
+    count_cyc(c, PMH_CNT_CYC_PASS0, t_ph);
+    t_ph = cyc_now();
 
     // ---- rounds
     for (int round = 0; round <= P.rounds; ++round) {
@@ -1068,11 +1089,11 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
         if (round > 0) count(c, PMH_CNT_ROUNDS, leader);
         team_sync<TW>();
         run_range<FAM, F32, TW, REJ>(c, 0, c.n);
-        const long long t_bar = clock64();
+        const long long t_bar = cyc_now();
         team_sync<TW>();
-        count(c, PMH_CNT_CYC_BARRIER, (unsigned long long)(clock64() - t_bar));
-        count(c, PMH_CNT_CYC_FIRST, (unsigned long long)(clock64() - t_ph));
-        t_ph = clock64();
+        count_cyc(c, PMH_CNT_CYC_BARRIER, t_bar);
+        count_cyc(c, PMH_CNT_CYC_FIRST, t_ph);
+        t_ph = cyc_now();
         if (ld_volatile(&ts->unfilled) == 0 || ld_volatile(&ts->status) != PMH_OK) break;
         team_sync<TW>();
     }
@@ -1087,7 +1108,7 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
         team_sync<TW>();
         if (ld_volatile(&ts->redo)) {
             count(c, PMH_CNT_REDO, leader);
-            count(c, PMH_CNT_CYC_FINISH, (unsigned long long)(clock64() - t_ph));
+            count_cyc(c, PMH_CNT_CYC_FINISH, t_ph);
             return;   // the FP64 kernel writes this item's outputs
         }
         if (tw == 0 && ld_volatile(&ts->cont_n) > 0) {
@@ -1124,7 +1145,7 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
         }
     }
     if (leader && P.status) P.status[out_row] = st;
-    count(c, PMH_CNT_CYC_FINISH, (unsigned long long)(clock64() - t_ph));
+    count_cyc(c, PMH_CNT_CYC_FINISH, t_ph);
 }
 
 // ------------------------------------------------------------ grid mode
@@ -1475,7 +1496,7 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
     if (live) {
         // the trimmed filter needs 16-byte aligned ids and weights (else run_range's, chunk by chunk)
         const bool lean = PMH_GRID_LEAN && ((((uintptr_t)P.ids) | ((uintptr_t)P.weights)) & 15u) == 0;
-        const long long t_pass = clock64();
+        const long long t_pass = cyc_now();
         uint64_t chunk = (uint64_t)c.n / (4ull * gridDim.x);
         chunk = chunk < kGridChunkMin ? kGridChunkMin : (chunk > kGridChunk ? kGridChunk : chunk);
         if (lean) {
@@ -1496,7 +1517,7 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
             run_range<FAM, F32, 8, REJ>(c, (uint32_t)lo, hi);
             __syncthreads();
         }
-        count(c, PMH_CNT_CYC_FIRST, (unsigned long long)(clock64() - t_pass));
+        count_cyc(c, PMH_CNT_CYC_FIRST, t_pass);
         // merge the local signature into the item's global one
         for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
             if constexpr (F32) {
@@ -1526,9 +1547,9 @@ __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int it
     __syncthreads();
     if (last) {
         __threadfence();
-        const long long t_f = clock64();
+        const long long t_f = cyc_now();
         grid_finalize<FAM, F32, REJ>(c, g, gsig_v, item_v, set);
-        count(c, PMH_CNT_CYC_FINISH, (unsigned long long)(clock64() - t_f));
+        count_cyc(c, PMH_CNT_CYC_FINISH, t_f);
     }
     c.gbound32 = nullptr;
     c.gbound64 = nullptr;
@@ -1632,11 +1653,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) sketch_kernel(const __grid_cons
     __syncwarp();
     const int tt = (warp % TW) * 32 + lane;   // thread index within the team
     const bool team_leader = tt == 0;
-    const long long t_warp = clock64();
+    const long long t_warp = cyc_now();
     // the FP64 redo launch reads its queue's length (the FP32 kernels' redo count) from the device
     const int64_t qlen = p.queue_len_dev ? min(p.queue_len, (int64_t)ld_volatile((const int *)p.queue_len_dev)) : p.queue_len;
     for (;;) {
-        const long long t_item = clock64();
+        const long long t_item = cyc_now();
         if (team_leader) ts->item_idx = (int)atomicAdd(p.head, 1u);
         team_sync<TW>();
         const int64_t qi = ts->item_idx;
@@ -1661,9 +1682,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) sketch_kernel(const __grid_cons
         c.n = (uint32_t)(e - b);
         process_item<FAM, F32, TW, REJ>(c, v, set);
         team_sync<TW>();
-        count(c, PMH_CNT_CYC_ITEM, (unsigned long long)(clock64() - t_item));
+        count_cyc(c, PMH_CNT_CYC_ITEM, t_item);
     }
-    count(c, PMH_CNT_CYC_WARP, (unsigned long long)(clock64() - t_warp));
+    count_cyc(c, PMH_CNT_CYC_WARP, t_warp);
     __syncwarp();
     if (p.counters && lane < PMH_NUM_COUNTERS && c.ws->cnt[lane]) atomicAdd(&p.counters[lane], c.ws->cnt[lane]);
 }
