@@ -53,16 +53,16 @@ OPS_PAIR_COMPONENT = 3  # equal-component count: two 32-bit compares and one add
 OPS_BBIT_WORD = 2 + 2 * (6 + 2) + 2
 # DRAM bytes (read + write) of the four family sketch kernels and their redo kernels per
 # element-variant, from the ncu capture summarised in profiles/sketch_kernel_fp32_c2_2000sets.md
-# (1,387.6 MB for 99,379,884 element-variants); the traffic grows in proportion to the elements
+# (1,349.6 MB for 99,379,884 element-variants); the traffic grows in proportion to the elements
 # (one pass over ids and weights per family).
-TRAFFIC_BYTES_PER_ELEMENT_VARIANT = 13.96
+TRAFFIC_BYTES_PER_ELEMENT_VARIANT = 13.58
 # Pipe use of the same four family kernels in that capture (per kernel, min-max over the families):
 # what binds them beside the op model above.
-NCU_SKETCH = {"issue_active_pct": [54.9, 62.7], "alu_pipe_pct": [41.3, 50.6], "fma_pipe_pct": [15.8, 19.5],
-              "dram_throughput_pct": [1.7, 3.3], "active_lanes_per_inst": [25.1, 28.1],
-              "warp_inst_per_element_variant": 21.3, "source": "profiles/sketch_kernel_fp32_c2_2000sets.md"}
+NCU_SKETCH = {"issue_active_pct": [54.9, 61.6], "alu_pipe_pct": [42.9, 50.0], "fma_pipe_pct": [17.4, 18.8],
+              "dram_throughput_pct": [1.7, 3.7], "active_lanes_per_inst": [24.9, 28.0],
+              "warp_inst_per_element_variant": 20.0, "source": "profiles/sketch_kernel_fp32_c2_2000sets.md"}
 TRAFFIC_BASIS = ("ncu dram bytes per element-variant on a 2,000-set c2-shaped batch (kernel source of commit "
-                 "75980f0) x this step's work")
+                 "8a0d5f2) x this step's work")
 
 
 def parse():
