@@ -60,9 +60,10 @@ struct __align__(16) Rec64 {
 };
 
 // Grid mode: items of sets with at least SketchParams::grid_min elements are
-// processed by every CTA of a launch (chunks of kGridChunkMin..kGridChunk
-// elements, about four per CTA), each CTA with its own shared signature,
-// merged into a global one per item.
+// processed by every CTA of a launch, each CTA with its own shared signature,
+// merged into a global one per item.  With 16-byte aligned inputs every warp
+// claims runs of 128-element blocks (grid_pass); otherwise the CTAs take chunks
+// of kGridChunkMin..kGridChunk elements, about four per CTA (run_range).
 constexpr int64_t kGridMinDefault = 1ll << 20;
 constexpr uint32_t kGridChunk = 1u << 16;
 constexpr uint32_t kGridChunkMin = 1u << 11;
@@ -1452,8 +1453,8 @@ __device__ void grid_pass(Ctx<F32> &c, GridState *gs) {
     __syncwarp();
 }
 
-// One CTA's share of a grid item: chunks of the item's elements with a local
-// signature, then the merge into the global signature; the last CTA to
+// One CTA's share of a grid item: its warps' part of the filter pass with a
+// local signature, then the merge into the global signature; the last CTA to
 // finish finalises the item.
 template <int FAM, bool F32, bool REJ>
 __device__ void grid_participate(Ctx<F32> &c, GridState *g, void *gsig_v, int item_v, int64_t set) {
