@@ -426,7 +426,7 @@ pmh_status pmh_check_texp(const uint64_t *words, int64_t n, float c, float inv, 
  *   counts    device uint16[num_sigs * num_sigs].
  * Exact integer counts; J_P estimate = counts / m.  Errors: PMH_ERR_INVALID_ARG
  * (NULL pointers, num_sigs < 0), PMH_ERR_UNSUPPORTED (m > 65535, more than
- * 65535 tiles of 64 rows), PMH_ERR_CUDA.
+ * 65535 tiles of 128 rows), PMH_ERR_CUDA.
  * pmh_estimate_allpairs is the same call under its earlier name.
  */
 pmh_status pmh_estimate_jp(pmh_handle h, const uint64_t *sigs, int64_t num_sigs, uint32_t m, int32_t upper_only,
@@ -442,7 +442,7 @@ pmh_status pmh_estimate_allpairs(pmh_handle h, const uint64_t *sigs, int64_t num
  *   sig_a, sig_b device uint64[num_a * m], [num_b * m] row-major (may alias).
  *   counts    device uint16, num_a rows of ld_counts >= num_b entries.
  * Errors: PMH_ERR_INVALID_ARG (NULL pointers, negative sizes, ld_counts <
- * num_b), PMH_ERR_UNSUPPORTED (m > 65535, more than 65535 tiles of 64 rows
+ * num_b), PMH_ERR_UNSUPPORTED (m > 65535, more than 65535 tiles of 128 rows
  * of sig_a), PMH_ERR_CUDA.
  */
 pmh_status pmh_estimate_jp_block(pmh_handle h, const uint64_t *sig_a, int64_t num_a, const uint64_t *sig_b,

@@ -775,29 +775,30 @@ extern "C" pmh_status pmh_check_exp1(const uint64_t *words, int64_t n, float *ou
 
 // ------------------------------------------------------------------ estimation
 // Equal-component counts of every pair (a, b) of rows of two signature tables,
-// Eq. jaccard_estimator: out[a * ldo + b].  64x64 tile of pairs per CTA, 16
-// components per shared-memory stage, 4x4 pairs per thread (rows ty + 16i,
-// columns tx + 16j: conflict-free shared reads).  With upper_only (one table
-// against itself) only b >= a is written.
-constexpr int kTile = 64, kKc = 16;
+// Eq. jaccard_estimator: out[a * ldo + b].  128x128 tile of pairs per CTA, 16
+// components per shared-memory stage, 8x8 pairs per thread (rows ty + 16i,
+// columns tx + 16j: conflict-free shared reads, 16 shared loads per 64 pairs).
+// With upper_only (one table against itself) only b >= a is written.
+constexpr int kTile = 64, kKc = 16;   // the b-bit kernel's tile
+constexpr int kApTile = 128, kApR = kApTile / 16;
 
-__global__ void __launch_bounds__(256) allpairs_kernel(const uint64_t *__restrict__ sa, int64_t na,
-                                                       const uint64_t *__restrict__ sb, int64_t nb, uint32_t m,
-                                                       int upper_only, uint16_t *__restrict__ out, int64_t ldo) {
-    __shared__ uint64_t As[kKc][kTile + 1];
-    __shared__ uint64_t Bs[kKc][kTile + 1];
+__global__ void __launch_bounds__(256, 2) allpairs_kernel(const uint64_t *__restrict__ sa, int64_t na,
+                                                          const uint64_t *__restrict__ sb, int64_t nb, uint32_t m,
+                                                          int upper_only, uint16_t *__restrict__ out, int64_t ldo) {
+    __shared__ uint64_t As[kKc][kApTile + 1];
+    __shared__ uint64_t Bs[kKc][kApTile + 1];
     const int64_t ta = blockIdx.y, tb = blockIdx.x;
     if (upper_only && ta > tb) return;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int64_t a0 = ta * kTile, b0 = tb * kTile;
-    uint32_t cnt[4][4];
+    const int64_t a0 = ta * kApTile, b0 = tb * kApTile;
+    uint32_t cnt[kApR][kApR];
 #pragma unroll
-    for (int i = 0; i < 4; i++)
+    for (int i = 0; i < kApR; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) cnt[i][j] = 0;
+        for (int j = 0; j < kApR; j++) cnt[i][j] = 0;
     for (uint32_t kc = 0; kc < m; kc += kKc) {
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < kApTile * kKc / 256; q++) {
             const int idx = threadIdx.x + 256 * q;
             const int r = idx >> 4, kk = idx & 15;
             const uint32_t k = kc + kk;
@@ -807,26 +808,26 @@ __global__ void __launch_bounds__(256) allpairs_kernel(const uint64_t *__restric
             Bs[kk][r] = (rb < nb && k < m) ? sb[rb * m + k] : 0xFFFFFFFFFFFFFFFEull;
         }
         __syncthreads();
-#pragma unroll
+#pragma unroll 4
         for (int kk = 0; kk < kKc; kk++) {
-            uint64_t a[4], b[4];
+            uint64_t a[kApR], b[kApR];
 #pragma unroll
-            for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < kApR; i++) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < kApR; j++) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; i++)
+            for (int i = 0; i < kApR; i++)
 #pragma unroll
-                for (int j = 0; j < 4; j++) cnt[i][j] += (a[i] == b[j]);
+                for (int j = 0; j < kApR; j++) cnt[i][j] += (a[i] == b[j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
+    for (int i = 0; i < kApR; i++) {
         const int64_t a = a0 + ty + 16 * i;
         if (a >= na) continue;
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < kApR; j++) {
             const int64_t b = b0 + tx + 16 * j;
             if (b >= nb || (upper_only && a > b)) continue;
             out[a * ldo + b] = (uint16_t)cnt[i][j];
@@ -879,7 +880,7 @@ extern "C" pmh_status pmh_estimate_jp(pmh_handle h, const uint64_t *sigs, int64_
     if (m < 1 || m > 65535) return fail(h, PMH_ERR_UNSUPPORTED, "m = %u outside [1, 65535]", m);
     if (num_sigs == 0) return PMH_OK;
     if (!sigs || !counts) return fail(h, PMH_ERR_INVALID_ARG, "NULL sigs/counts");
-    const int64_t tiles = (num_sigs + kTile - 1) / kTile;
+    const int64_t tiles = (num_sigs + kApTile - 1) / kApTile;
     if (tiles > 65535) return fail(h, PMH_ERR_UNSUPPORTED, "num_sigs too large for one launch");
     CUDA_TRY(h, cudaSetDevice(h->device));
     dim3 grid((unsigned)tiles, (unsigned)tiles);
@@ -899,7 +900,7 @@ extern "C" pmh_status pmh_estimate_jp_block(pmh_handle h, const uint64_t *sig_a,
     if (num_a == 0 || num_b == 0) return PMH_OK;
     if (!sig_a || !sig_b || !counts) return fail(h, PMH_ERR_INVALID_ARG, "NULL sig_a/sig_b/counts");
     if (ld_counts < num_b) return fail(h, PMH_ERR_INVALID_ARG, "ld_counts < num_b");
-    const int64_t ta = (num_a + kTile - 1) / kTile, tb = (num_b + kTile - 1) / kTile;
+    const int64_t ta = (num_a + kApTile - 1) / kApTile, tb = (num_b + kApTile - 1) / kApTile;
     if (ta > 65535 || tb > 2147483647ll) return fail(h, PMH_ERR_UNSUPPORTED, "tables too large for one launch");
     CUDA_TRY(h, cudaSetDevice(h->device));
     dim3 grid((unsigned)tb, (unsigned)ta);
