@@ -454,6 +454,16 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ reference arm
+def workload_config(batch, world):
+    """The workload both arms run: the same keys and values in the GPU line and the reference line."""
+    n_elem, S = batch.num_elements, batch.num_sets
+    return {"workload": f"c2: {S} sets, n log-uniform [1,1e5], Uniform(0,1] weights, m=1024, "
+                        "variants 1,1a,2,3,3a,4 in one persistent launch",
+            "m": batch.m, "num_sets": S, "elements_per_rank": n_elem, "variants": VARIANTS,
+            "parallelism": f"weak x{world}",
+            "l2": f"inputs {(16 * n_elem + 8 * S) / 1e9:.2f} GB per step > 129 MB L2"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -473,8 +483,8 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"c2: {batch.num_sets} sets, n log-uniform [1,1e5], Uniform(0,1] weights, m=1024, "
-                               "variants 1,1a,2,3,3a,4", "m": 1024, "num_sets": batch.num_sets},
+        "config": workload_config(batch, world),
+        "precision": "fp64 (the oracle)",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"random (set, variant) tasks of the workload for {per_step:.0f} s per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -699,12 +709,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t32, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"c2: {S} sets, n log-uniform [1,1e5], Uniform(0,1] weights, m=1024, "
-                                   "variants 1,1a,2,3,3a,4 in one persistent launch",
-                       "m": m, "num_sets": S, "elements_per_rank": n_elem, "variants": VARIANTS,
-                       "precision": "fp32 candidates + fp64 recheck", "parallelism": f"weak x{world}",
-                       "team_shapes": shapes_headline,
-                       "l2": f"inputs {(16 * n_elem + 8 * S) / 1e9:.2f} GB per step > 129 MB L2"},
+            "config": workload_config(batch, world),
+            "precision": "fp32 candidates + fp64 recheck", "team_shapes": shapes_headline,
             "timing": "CUDA events around the timed steps on the launching stream; each step replays the "
                       "library's cached CUDA graph",
             "ms_per_step_profiled": t32_profiled,
