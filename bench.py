@@ -46,6 +46,9 @@ OPS_POINT = 70          # every generated point: value word (20), label word (20
                         # stop compare (4), offer to the component (3)
 OPS_SURVIVOR = -10      # per survivor: its point-1 value word was counted with its element (-20), and its
                         # scaled 1/w is one reciprocal (+10)
+OPS_LISTED = 30         # every prefilter list entry a variant visits: the key and scaled w come with the entry
+                        # (decode 4), value word of point 1 (20), 23-bit uniform (3), products and compare (3);
+                        # the elements the prefilter pass hashed count OPS_ELEMENT once for all variants
 LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes issue one instruction per clock
 OPS_PAIR_COMPONENT = 3  # equal-component count: two 32-bit compares and one add per component pair
 # 8-bit codes, per pair of 64-bit words (8 fields): xor (2), per 32-bit half three fold steps of
@@ -80,6 +83,8 @@ def parse():
                     help="pin the sketch kernels' team shape (0 warp, 1 cta8, 2 quad, 3 pair, 4 quad8, 5 quad8l), "
                          "one value for every family or four comma-separated values for ProbMinHash1..4; "
                          "-1 = autotuned")
+    ap.add_argument("--prefilter", type=float, default=None,
+                    help="prefilter list factor of the library (pmh_set_prefilter; 0 = off; default: the library's)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the per-kernel measurements beside the headline (huge set, all-pairs counts)")
     return ap.parse_args()
@@ -532,6 +537,8 @@ def main():
     st32 = torch.empty((len(VARIANTS), S), dtype=torch.int32, device=dev)
     st64 = torch.empty_like(st32)
     h = pmh.Handle(local)
+    if args.prefilter is not None:
+        h.set_prefilter(args.prefilter)
     shapes_pinned = [int(x) for x in args.team_shape.split(",")]
     if len(shapes_pinned) == 1 and shapes_pinned[0] >= 0:
         h.set_team_shape(0, shapes_pinned[0])
@@ -665,7 +672,12 @@ def main():
     sm_mhz = clk["sm_mhz"] if clk else 2070.0
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     survivors = c["elements"] - c["prefiltered"]
-    per_launch_ops = c["elements"] * OPS_ELEMENT + c["points32"] * OPS_POINT + survivors * OPS_SURVIVOR
+    # element-variants the sketch kernels filtered from the ids and weights; those of listed sets
+    # were filtered from the lists (c["listed"]) or rejected by the prefilter pass (c["list_skipped"]),
+    # which hashed each of its elements once (c["list_hashed"])
+    filtered_full = c["elements"] - c["list_skipped"] - c["listed"]
+    per_launch_ops = (filtered_full * OPS_ELEMENT + c["listed"] * OPS_LISTED + c["list_hashed"] * OPS_ELEMENT
+                      + c["points32"] * OPS_POINT + survivors * OPS_SURVIVOR)
     achieved = per_launch_ops / (k_avg * 1e-3) / 1e12
     peak = n_sms * LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (32-bit lane ops)",

@@ -98,7 +98,10 @@ enum {
     PMH_CNT_SEQ_STEPS = 18,   /* warp steps of lane-sequential survivor expansion (32 lane slots each) */
     PMH_CNT_SEQ_POINTS = 19,  /* points evaluated lane-sequentially (part of POINTS32/POINTS64) */
     PMH_CNT_REDO = 20,        /* FP32 items whose contender log overflowed, sketched again in FP64 */
-    PMH_NUM_COUNTERS = 21
+    PMH_CNT_LISTED = 21,      /* prefilter list entries visited (part of ELEMENTS; see pmh_set_prefilter) */
+    PMH_CNT_LIST_HASHED = 22, /* elements hashed once for all variants by the prefilter pass */
+    PMH_CNT_LIST_SKIPPED = 23,/* elements the prefilter rejected for a variant (part of ELEMENTS and PREFILTERED) */
+    PMH_NUM_COUNTERS = 24
 };
 
 /* Creates a handle bound to CUDA device `device` (the device is made current
@@ -127,7 +130,7 @@ const char *pmh_last_error(pmh_handle h);
  *   ids       device uint64[N]: element ids; set s owns ids[offsets[s] .. offsets[s+1]).
  *             Ids must be distinct within a set (precondition, not checked).
  *   weights   device float64[N]: weights; w = 0 (or -0) elements are skipped.
- *   offsets   device int64[num_sets+1], offsets[0] = 0, non-decreasing; a set
+ *   offsets   device int64[num_sets+1], offsets[0] >= 0 (usually 0), non-decreasing; a set
  *             whose offsets are decreasing gets PMH_ERR_INVALID_ARG in set_status.
  *   num_sets  >= 0.
  *   m         signature size, 1 <= m <= PMH_MAX_M (m >= 2 for V3/V3A/V4).
@@ -243,7 +246,8 @@ pmh_status pmh_sketch_batch_noalloc(const uint64_t *ids, const double *weights, 
 /*
  * Profiling.  pmh_set_profiling(h, 1) makes every later pmh_sketch_batch on
  * `h` record CUDA events on its stream before the work-queue build, between
- * the queue build and the sketch kernels, and after them (each call its own
+ * the queue build (with the per-set statistics) and the sketch kernels (with
+ * the prefilter pass of pmh_set_prefilter), and after them (each call its own
  * events from a ring of 256; profiled calls are launched directly, not from
  * a CUDA graph; calls during a stream capture are not profiled).
  * pmh_last_kernel_ms waits for the most recent call to finish and returns its
@@ -328,6 +332,37 @@ pmh_status pmh_last_launches(pmh_handle h, int32_t *launches);
  * rounds outside [0, 64].
  */
 pmh_status pmh_set_thresholds(pmh_handle h, double t_c, double t_c_grid, int32_t rounds, int64_t grid_min);
+
+/*
+ * pmh_set_prefilter -- work-only option of later pmh_sketch_batch calls on
+ * `h` (no counterpart in the paper: how the first threshold round of the
+ * sketch kernels is fed).  Results never depend on it.
+ *
+ * The paper's loop evaluates every element's first point, and only some
+ * elements continue (Sec. "ProbMinHash1": most elements of a large set stop
+ * after one point).  With the prefilter on, one extra pass per call hashes the
+ * elements of every set of list_factor * m (ln m + t_c) up to 262,144
+ * elements once for all variants and keeps those whose first point can lie
+ * below the first round's threshold T in some family (the sketch kernels'
+ * own log-free test, with the smallest lower bound of any family); the first
+ * round of each weighted variant of such a set then visits only these
+ * elements.  A later round (rare) visits all elements again.  Binary-weight
+ * variants and the rejection sampler do not use the lists.
+ *
+ *   list_factor  default 2.0; <= 0 turns the prefilter off.
+ *
+ * Memory: lists of 8 bytes per element of the call (16-byte entries for up
+ * to half the elements of each set; a set with more survivors than that is
+ * filtered in full) plus 4 bytes per set, kept in the handle.  The first
+ * pmh_sketch_batch call on new (ids, weights, offsets, num_sets) arrays reads
+ * offsets[0] and offsets[num_sets] back to size them, which waits for
+ * `stream`; calls made during a stream capture before that read skip the
+ * prefilter.  Later calls on the same arrays reuse the count: if the offsets
+ * were rewritten with more elements in between, the sets that no longer fit
+ * in the lists are filtered in full (same result, more work).
+ * Errors: PMH_ERR_INVALID_ARG for NULL h or a non-finite list_factor.
+ */
+pmh_status pmh_set_prefilter(pmh_handle h, double list_factor);
 
 /*
  * pmh_set_limits -- resource caps of later pmh_sketch_batch calls on `h`

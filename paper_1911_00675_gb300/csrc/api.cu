@@ -57,6 +57,10 @@ struct Workspace {
     int64_t stats_cap = 0;
     void *grid = nullptr;
     size_t grid_bytes = 0;
+    ulonglong2 *list = nullptr;      // prefilter lists (list_cap entries) and per-set entry counts
+    int64_t list_cap = 0;
+    uint32_t *list_n = nullptr;
+    int64_t list_n_cap = 0;
 };
 
 // Buffers and streams of pmh_sketch_batch_host.
@@ -101,6 +105,10 @@ struct pmh_handle_s {
     cudaEvent_t tev[3 + 4] = {};             // autotuning: queue/sketch brackets + one per family
     unsigned long long *status_scratch = nullptr;   // pmh_sync_status: 8 counts + the first failing (index, code)
     unsigned int *pm_counter = nullptr;              // pmh_pminhash_batch: the blocks' set counter
+    // element count of the most recent batch read back (sizes the prefilter lists), keyed by its arrays
+    const void *ncache_ids = nullptr, *ncache_w = nullptr;
+    const int64_t *ncache_off = nullptr;
+    int64_t ncache_sets = -1, ncache_n = 0;
     // profiling events
     bool profiling = false;
     bool prof_recorded = false;        // the most recent call was profiled
@@ -191,6 +199,65 @@ static pmh_status ensure_stats(pmh_handle h, Workspace &w, int64_t num_sets) {
     return PMH_OK;
 }
 
+// Prefilter lists for a call of `elements` elements (offsets[num_sets] - offsets[0]) and num_sets sets.
+static pmh_status ensure_list(pmh_handle h, Workspace &w, int64_t elements, int64_t num_sets) {
+    const int64_t need = elements / 2 + 1;
+    if (need > w.list_cap) {
+        if (w.list) cudaFree(w.list);
+        w.list = nullptr;
+        w.list_cap = 0;
+        cudaError_t e = cudaMalloc(&w.list, (size_t)need * sizeof(ulonglong2));
+        if (e != cudaSuccess) return fail(h, PMH_ERR_NO_MEMORY, "prefilter lists (%lld entries): %s", (long long)need, cudaGetErrorString(e));
+        w.list_cap = need;
+        h->graph_valid = false;
+    }
+    if (num_sets > w.list_n_cap) {
+        if (w.list_n) cudaFree(w.list_n);
+        w.list_n = nullptr;
+        w.list_n_cap = 0;
+        const int64_t cap = num_sets < 1024 ? 1024 : num_sets;
+        cudaError_t e = cudaMalloc(&w.list_n, (size_t)cap * sizeof(uint32_t));
+        if (e != cudaSuccess) return fail(h, PMH_ERR_NO_MEMORY, "prefilter list counts (%lld sets): %s", (long long)cap, cudaGetErrorString(e));
+        w.list_n_cap = cap;
+        h->graph_valid = false;
+    }
+    return PMH_OK;
+}
+
+// Sets of list_min..list_max elements get prefilter lists (list_min from the first round's threshold).
+static bool list_bounds(const Thresholds &th, uint32_t m, float t_factor, int64_t *lo, int64_t *hi) {
+    if (!kListing || !(th.list_factor > 0.0) || th.rounds <= 0) return false;
+    const double lmin = std::ceil(th.list_factor * (double)m * (double)t_factor);
+    *lo = lmin < 2.0 ? 2 : (lmin > 9e18 ? INT64_MAX : (int64_t)lmin);
+    *hi = th.list_max;
+    return *lo <= *hi;
+}
+
+// The element count offsets[num_sets] - offsets[0] of a device batch: read back (waiting for `st`)
+// the first time a batch (ids, weights, offsets, num_sets) is seen, then taken from the handle.
+// -1 when it cannot be read (during a stream capture).  A stale count costs speed only: the
+// prefilter kernel lists only the sets that fit in the lists.
+static pmh_status element_count(pmh_handle h, const void *ids, const void *weights, const int64_t *offsets,
+                                int64_t num_sets, cudaStream_t st, cudaStreamCaptureStatus cs, int64_t *n) {
+    *n = -1;
+    if (h->ncache_off == offsets && h->ncache_ids == ids && h->ncache_w == weights && h->ncache_sets == num_sets) {
+        *n = h->ncache_n;
+        return PMH_OK;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return PMH_OK;
+    int64_t v[2] = {0, 0};
+    CUDA_TRY(h, cudaMemcpyAsync(&v[0], offsets, sizeof(int64_t), cudaMemcpyDefault, st));
+    CUDA_TRY(h, cudaMemcpyAsync(&v[1], offsets + num_sets, sizeof(int64_t), cudaMemcpyDefault, st));
+    CUDA_TRY(h, cudaStreamSynchronize(st));
+    h->ncache_off = offsets;
+    h->ncache_ids = ids;
+    h->ncache_w = weights;
+    h->ncache_sets = num_sets;
+    h->ncache_n = v[1] > v[0] ? v[1] - v[0] : 0;
+    *n = h->ncache_n;
+    return PMH_OK;
+}
+
 static pmh_status ensure_workspace(pmh_handle h, Workspace &w, int64_t num_sets, int64_t items, uint32_t m) {
     pmh_status rc = ensure_queue(h, w, items);
     if (!rc) rc = ensure_stats(h, w, num_sets);
@@ -212,13 +279,14 @@ static pmh_status ensure_fork(pmh_handle h) {
 // Enqueues the whole batch on `st` with workspace `w`; with `fork`, the family
 // kernels run side by side on the handle's fork streams.
 static pmh_status enqueue_sketch(pmh_handle h, Workspace &w, const SketchParams &p, const Plan &plan, int precision,
-                                 cudaStream_t st, cudaEvent_t *prof_ev, cudaEvent_t *fam_ev, bool fork = false) {
+                                 cudaStream_t st, cudaEvent_t *prof_ev, cudaEvent_t *fam_ev, bool fork,
+                                 const ListSpec &ls) {
     if (fork) {
         pmh_status rc = ensure_fork(h);
         if (rc) return rc;
     }
     cudaError_t e = enqueue_batch(p, plan, precision, h->sm_count, w.queue, w.redo, w.qmeta, w.stats, st, prof_ev, fam_ev,
-                                  fork ? &h->ff : nullptr);
+                                  fork ? &h->ff : nullptr, ls);
     if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "sketch launch: %s", cudaGetErrorString(e));
     return PMH_OK;
 }
@@ -263,6 +331,10 @@ extern "C" void pmh_destroy(pmh_handle h) {
         if (w.stats) cudaFree(w.stats);
         if (w.grid) cudaFree(w.grid);
     }
+    for (Workspace &w : h->ws) {
+        if (w.list) cudaFree(w.list);
+        if (w.list_n) cudaFree(w.list_n);
+    }
     for (void *ptr : {h->hp.ids, h->hp.w, h->hp.off, h->hp.z[0], h->hp.z[1], h->hp.q[0], h->hp.q[1], h->hp.st[0], h->hp.st[1]})
         if (ptr) cudaFree(ptr);
     for (int i = 0; i < 4; i++) if (h->hp.s[i]) cudaStreamDestroy(h->hp.s[i]);
@@ -301,6 +373,15 @@ extern "C" pmh_status pmh_set_thresholds(pmh_handle h, double t_c, double t_c_gr
     h->th.t_c_grid = t_c_grid;
     h->th.rounds = rounds;
     h->th.grid_min = grid_min;
+    h->graph_valid = false;
+    return PMH_OK;
+}
+
+extern "C" pmh_status pmh_set_prefilter(pmh_handle h, double list_factor) {
+    if (!h) return PMH_ERR_INVALID_ARG;
+    h->err.clear();
+    if (!std::isfinite(list_factor)) return fail(h, PMH_ERR_INVALID_ARG, "list_factor must be finite");
+    h->th.list_factor = list_factor;
     h->graph_valid = false;
     return PMH_OK;
 }
@@ -393,7 +474,7 @@ extern "C" pmh_status pmh_kernel_ms_history(pmh_handle h, int32_t max_calls, flo
 // and records the fastest per family.  All runs write the same results.
 static pmh_status autotune_shapes(pmh_handle h, Workspace &w, SketchParams p, uint32_t m, const int32_t *variants,
                                   int32_t num_variants, int64_t num_sets, int precision, cudaStream_t st,
-                                  int *kinds, const TuneKey *tkey) {
+                                  int *kinds, const TuneKey *tkey, const ListSpec &ls) {
     if (!h->tev[0])
         for (int i = 0; i < 7; i++) CUDA_TRY(h, cudaEventCreate(&h->tev[i]));
     float best[4] = {1e30f, 1e30f, 1e30f, 1e30f};
@@ -413,7 +494,8 @@ static pmh_status autotune_shapes(pmh_handle h, Workspace &w, SketchParams p, ui
         q.counters = nullptr;   // the trials are not the call's work
         for (int j = 0; j < plan.nfam && q.gctl; j++)
             if (plan.ggrid[j] <= 0) { q.gctl = nullptr; q.gstate = nullptr; q.gsig = nullptr; }
-        e = enqueue_batch(q, plan, precision, h->sm_count, w.queue, w.redo, w.qmeta, w.stats, st, h->tev, h->tev + 3);
+        e = enqueue_batch(q, plan, precision, h->sm_count, w.queue, w.redo, w.qmeta, w.stats, st, h->tev, h->tev + 3,
+                          nullptr, ls);
         if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(e));
         CUDA_TRY(h, cudaEventSynchronize(h->tev[2]));
         for (int j = 0; j < plan.nfam; j++) {
@@ -465,7 +547,8 @@ static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, cons
                                 const int64_t *offsets, int64_t num_sets, uint32_t m, const int32_t *variants,
                                 int32_t num_variants, int32_t precision, uint64_t seed, uint64_t *out_ids,
                                 double *out_q, int32_t *set_status, uint64_t *counters, cudaStream_t st,
-                                bool allow_graph, cudaEvent_t *fam_ev, const int *kinds_in = nullptr) {
+                                bool allow_graph, cudaEvent_t *fam_ev, const int *kinds_in = nullptr,
+                                int64_t n_hint = -1) {
     CUDA_TRY(h, cudaSetDevice(h->device));
     Workspace &w = h->ws[wsi];
     Tables tab;
@@ -481,6 +564,18 @@ static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, cons
     if (h->th.grid_min > 0) bind_grid_scratch(&p, w.grid);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (st) CUDA_TRY(h, cudaStreamIsCapturing(st, &cs));
+    // prefilter lists, sized by the call's element count
+    ListSpec ls;
+    if (list_bounds(h->th, m, p.t_factor, &ls.list_min, &ls.list_max)) {
+        int64_t n_el = n_hint;
+        if (n_el < 0 && (rc = element_count(h, ids, weights, offsets, num_sets, st, cs, &n_el))) return rc;
+        if (n_el > 0) {
+            if ((rc = ensure_list(h, w, n_el, num_sets))) return rc;
+            ls.list = w.list;
+            ls.list_n = w.list_n;
+            ls.list_cap = w.list_cap;
+        }
+    }
     // team shape per family: given by the caller (host pipeline), else forced, else tuned, else
     // (tuning off or impossible) the default rule
     int kinds[4];
@@ -502,7 +597,7 @@ static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, cons
         }
     }
     if (need_tune && h->autotune && cs == cudaStreamCaptureStatusNone) {
-        rc = autotune_shapes(h, w, p, m, variants, num_variants, num_sets, precision, st, kinds, tkey);
+        rc = autotune_shapes(h, w, p, m, variants, num_variants, num_sets, precision, st, kinds, tkey, ls);
         if (rc) return rc;
     }
     Plan plan;
@@ -514,7 +609,7 @@ static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, cons
     // takes are skipped by the ordinary kernels)
     for (int j = 0; j < plan.nfam && p.gctl; j++)
         if (plan.ggrid[j] <= 0) { p.gctl = nullptr; p.gstate = nullptr; p.gsig = nullptr; }
-    h->last_launches = launch_count(plan, p.gctl != nullptr, precision == PMH_FP32_RECHECK);
+    h->last_launches = launch_count(plan, p.gctl != nullptr, precision == PMH_FP32_RECHECK, ls.list != nullptr);
     for (int f = 0; f < 4; f++) h->last_shape[f] = -1;
     for (int j = 0; j < plan.nfam; j++) h->last_shape[plan.fam[j] - 1] = plan.shape[j].kind;
     cudaEvent_t *prof_ev = nullptr;
@@ -526,7 +621,7 @@ static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, cons
     const bool fork = h->concurrent_families && wsi == 0 && !fam_ev;
     if (fork && (rc = ensure_fork(h))) return rc;   // before any capture begins
     if (!allow_graph || wsi != 0 || fam_ev || prof_ev || !h->use_graph || cs != cudaStreamCaptureStatusNone || !st)
-        return enqueue_sketch(h, w, p, plan, precision, st, prof_ev, fam_ev, fork);
+        return enqueue_sketch(h, w, p, plan, precision, st, prof_ev, fam_ev, fork, ls);
 
     GraphKey key{};
     key.ids = ids; key.weights = weights; key.offsets = offsets; key.out_ids = out_ids; key.out_q = out_q;
@@ -539,7 +634,7 @@ static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, cons
         if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
         h->graph_valid = false;
         CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_sketch(h, w, p, plan, precision, h->cap_stream, nullptr, nullptr, fork);
+        rc = enqueue_sketch(h, w, p, plan, precision, h->cap_stream, nullptr, nullptr, fork, ls);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
         if (rc) { if (g) cudaGraphDestroy(g); return rc; }
@@ -639,8 +734,13 @@ extern "C" pmh_status pmh_sketch_batch_host(pmh_handle h, const uint64_t *ids, c
     // workspace for every chunk first: no allocation while the pipeline runs
     Tables tab;
     if ((rc = get_tables(h, m, &tab))) return rc;
-    for (Workspace &w : h->ws)
+    int64_t lmin = 0, lmax = 0, nmax = 0;
+    for (int c = 0; c < k; c++) nmax = std::max<int64_t>(nmax, offsets[b[c + 1]] - offsets[b[c]]);
+    const bool lists = list_bounds(h->th, m, (float)(std::log((double)m) + h->th.t_c), &lmin, &lmax) && nmax > 0;
+    for (Workspace &w : h->ws) {
         if ((rc = ensure_workspace(h, w, smax, smax * V, m))) return rc;
+        if (lists && (rc = ensure_list(h, w, nmax, smax))) return rc;
+    }
     HostPipe &hp = h->hp;
     if ((rc = ensure_dev(h, &hp.ids, &hp.ids_cap, (size_t)N * 8, "device ids"))) return rc;
     if ((rc = ensure_dev(h, &hp.w, &hp.w_cap, (size_t)N * 8, "device weights"))) return rc;
@@ -703,7 +803,8 @@ extern "C" pmh_status pmh_sketch_batch_host(pmh_handle h, const uint64_t *ids, c
         if (c >= 2) CUDA_TRY(h, cudaStreamWaitEvent(s_run, ev_out(c - 2), 0));   // chunk outputs are double-buffered
         rc = sketch_device(h, r, (const uint64_t *)dids, (const double *)dw, doff + s0, sc, m, variants, num_variants,
                            precision, seed, (uint64_t *)hp.z[r], out_q ? (double *)hp.q[r] : nullptr,
-                           set_status ? (int32_t *)hp.st[r] : nullptr, nullptr, s_run, false, ev_fam(c), kinds);
+                           set_status ? (int32_t *)hp.st[r] : nullptr, nullptr, s_run, false, ev_fam(c), kinds,
+                           offsets[b[c + 1]] - offsets[b[c]]);
         if (rc) {
             for (int i = 0; i < 4; i++) cudaStreamSynchronize(hp.s[i]);
             return rc;

@@ -142,10 +142,11 @@ inline uint64_t host_mix64(uint64_t z) {
 // starts, [512, 516) per-family head counters of the persistent kernels.
 // [516] counts the sets whose statistics are split over all blocks, [518, 520)
 // is the statistics kernel's set counter (u64), [520, 524) the per-family
-// lengths of the FP64 redo lists and [524, 528) the head counters of the redo
-// kernels; [528, ...) lists the split sets (u64 set indices, kBigCap of them).
+// lengths of the FP64 redo lists, [524, 528) the head counters of the redo
+// kernels and [528, 530) the prefilter kernel's set counter (u64); [530, ...)
+// lists the split sets (u64 set indices, kBigCap of them).
 constexpr int kQHist = 0, kQStart = 256, kQHead = 512, kQBigCount = 516, kQStatNext = 518, kQRedoCount = 520,
-              kQRedoHead = 524, kQBigList = 528;
+              kQRedoHead = 524, kQListNext = 528, kQBigList = 530;
 constexpr int kBigCap = 1024;
 constexpr int kQMetaWords = kQBigList + 2 * kBigCap;
 constexpr int kQMetaClearWords = kQBigList;     // words cleared per call
@@ -386,6 +387,101 @@ static __global__ void __launch_bounds__(256) set_stats_big_kernel(const int64_t
     }
 }
 
+// ------------------------------------------------------------------ prefilter lists
+#ifndef PMH_LIST_BLOCK
+#define PMH_LIST_BLOCK 512     // threads per block of the prefilter kernel
+#endif
+#ifndef PMH_LIST_UNROLL
+#define PMH_LIST_UNROLL 8      // elements per thread and step (their loads in flight together)
+#endif
+// One pass over the elements of every set of list_min..list_max elements that
+// keeps the elements whose first point can lie below the first round's bound
+// in some family: U te_lo (1 - 16 ulp) <= t_s (w 2^-sigma), the sketch kernels'
+// own filter test with the smallest lower-bound factor of any family (te_lo of
+// Exp(lambda;0,1) <= 1 of Exp(1)) and the first round's bound t_s, which the
+// running bound of every later point of that round only undercuts.  Each kept
+// element is written as (key, index | scaled weight << 32), so that the first
+// round of every weighted variant of the set visits only these entries and
+// hashes each key once instead of twice.  The sets that profit are those much
+// larger than m (ln m + c), where most elements fail the first point's test;
+// the elements are hashed here once for all variants instead of once per
+// variant.  Set s may use list[(offsets[s] - offsets[0]) / 2, + n/2) and
+// list_cap entries in all; a set whose survivors exceed n/2, or that does not
+// fit, stays unlisted (list_n = kUnlisted) and is filtered in full.
+// One block per set, the blocks taking sets from a shared counter; each thread
+// keeps kListUnroll elements' loads in flight (1,024 threads per SM at <= 64
+// registers).
+constexpr int kListBlock = PMH_LIST_BLOCK, kListUnroll = PMH_LIST_UNROLL;
+static __global__ void __launch_bounds__(kListBlock, 1024 / kListBlock) list_kernel(const SketchParams p, ulonglong2 *list, uint32_t *list_n,
+                                                          int64_t list_cap, int64_t list_min, int64_t list_max,
+                                                          unsigned int *meta) {
+    __shared__ long long s_next;
+    __shared__ unsigned int s_cnt;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long *wb = (const unsigned long long *)p.weights;
+    const int64_t off0 = p.offsets[0];
+    const float te_lo = p.tab.te_lo;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_next = (long long)atomicAdd((unsigned long long *)(meta + kQListNext), 1ull);
+            s_cnt = 0;
+        }
+        __syncthreads();
+        const int64_t s = s_next;
+        if (s >= p.num_sets) break;
+        const int64_t b = p.offsets[s], n = p.offsets[s + 1] - b;
+        const int64_t lb = (b - off0) >> 1, cap = n >> 1;
+        const SetStat st = p.stats[s];
+        float t_s;
+        int sigma;
+        first_threshold(p.m, p.t_factor, st.wsum, st.npos, &t_s, &sigma);
+        const bool ok = n >= list_min && n <= list_max && b >= off0 && !st.bad && st.npos > 0 && lb + cap <= list_cap &&
+                        !isinf(t_s);
+        if (ok) {
+            for (int64_t e0 = 0; e0 < n; e0 += kListUnroll * (int64_t)blockDim.x) {
+                uint64_t wv[kListUnroll], iv[kListUnroll];
+#pragma unroll
+                for (int u = 0; u < kListUnroll; ++u) {
+                    const int64_t e = e0 + u * (int64_t)blockDim.x + threadIdx.x;
+                    wv[u] = 0;
+                    iv[u] = 0;
+                    if (e < n) {
+                        wv[u] = __ldcs(wb + b + e);
+                        iv[u] = __ldcs((const unsigned long long *)p.ids + b + e);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kListUnroll; ++u) {
+                    const int64_t e = e0 + u * (int64_t)blockDim.x + threadIdx.x;
+                    const double w = __longlong_as_double((long long)wv[u]);
+                    bool keep = false;
+                    uint64_t key = 0;
+                    float ws = 0.0f;
+                    if (e < n && weight_positive(w)) {
+                        key = mix64(iv[u] ^ p.mixed_seed);
+                        ws = ws_scaled(w, sigma);
+                        const float ulo = __fmul_rn(unif_lo(value_word(key, 1)), te_lo);
+                        keep = !(__fmul_rn(ulo, 1.0f - 16.0f * 0x1p-24f) > __fmul_rn(t_s, ws));
+                    }
+                    const unsigned msk = __ballot_sync(0xFFFFFFFFu, keep);
+                    unsigned int wbase = 0;
+                    if (lane == 0 && msk) wbase = atomicAdd(&s_cnt, (unsigned int)__popc(msk));
+                    wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
+                    const unsigned int pos = wbase + __popc(msk & ((1u << lane) - 1u));
+                    if (keep && pos < (uint64_t)cap)
+                        list[lb + pos] = make_ulonglong2(key, (uint64_t)(uint32_t)e | ((uint64_t)__float_as_uint(ws) << 32));
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            list_n[s] = (ok && (int64_t)s_cnt <= cap) ? s_cnt : kUnlisted;
+            if (ok && p.counters) atomicAdd(&p.counters[PMH_CNT_LIST_HASHED], (unsigned long long)st.npos);
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ plan
 // Launch plan per family present: warp teams when at least 12 warps per SM
 // fit, else CTA teams.  Computed outside any stream capture (it sets kernel
@@ -498,9 +594,18 @@ struct FamilyFork {
     cudaEvent_t join[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
+// Prefilter lists of a call (list == null: none): list_cap entries, list_n of num_sets entries, for
+// the sets of list_min..list_max elements.
+struct ListSpec {
+    ulonglong2 *list = nullptr;
+    uint32_t *list_n = nullptr;
+    int64_t list_cap = 0, list_min = 0, list_max = 0;
+};
+
 inline cudaError_t enqueue_batch(SketchParams p, const Plan &plan, int precision, int sm_count, uint64_t *queue,
                                  uint64_t *redo, unsigned int *qmeta, SetStat *stats, cudaStream_t st, cudaEvent_t *ev,
-                                 cudaEvent_t *fam_ev = nullptr, const FamilyFork *ff = nullptr) {
+                                 cudaEvent_t *fam_ev = nullptr, const FamilyFork *ff = nullptr,
+                                 const ListSpec &ls = ListSpec()) {
     const int64_t items = p.num_sets * p.num_variants;
     FamOfVariant fv{};
     for (int v = 0; v < p.num_variants; v++) fv.f[v] = family_of(p.variants[v]);
@@ -520,7 +625,17 @@ inline cudaError_t enqueue_batch(SketchParams p, const Plan &plan, int precision
     set_stats_big_kernel<<<sm_count * 8, 256, 0, st>>>(p.offsets, p.weights, stats, qmeta);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     p.stats = stats;
+    // the prefilter pass counts as sketching work: it runs after the second event
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
+    p.list = nullptr;
+    p.list_n = nullptr;
+    if (kListing && ls.list && ls.list_n && p.rounds > 0) {
+        list_kernel<<<sm_count * (1024 / kListBlock), kListBlock, 0, st>>>(p, ls.list, ls.list_n, ls.list_cap, ls.list_min,
+                                                                          ls.list_max, qmeta);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        p.list = ls.list;
+        p.list_n = ls.list_n;
+    }
     const bool forked = ff && plan.nfam > 1;
     if (forked) {
         if ((e = cudaEventRecord(ff->fork, st)) != cudaSuccess) return e;
@@ -582,11 +697,15 @@ struct Thresholds {
     uint32_t cap_points = 0;   // points per element in warp-cooperative expansion (0: 64 m ln(m+1) + 4096)
     int max_cont = -1;         // contender records per team / grid item (-1: kMaxCont / kGridCont)
     bool te_rej = false;       // ProbMinHash3/3a/4: Exp(lambda;0,1) by the rejection sampler instead of inversion
+    // prefilter lists for sets of at least list_factor * m (ln m + t_c) elements (<= 0: off) and at most
+    // list_max (one block of the prefilter kernel hashes a whole set)
+    double list_factor = 2.0;   // measured on c2: 1.5 19.93, 2.0 19.86, 2.5 20.04, 3.5 20.58 ms per step
+    int64_t list_max = 262144;
 };
 
 // Kernel launches of one enqueue_batch call (fixed by the plan).
-inline int launch_count(const Plan &plan, bool grid, bool redo) {
-    int n = 5 + plan.nfam + (grid ? 1 : 0);
+inline int launch_count(const Plan &plan, bool grid, bool redo, bool listed = false) {
+    int n = 5 + plan.nfam + (grid ? 1 : 0) + (listed ? 1 : 0);
     for (int j = 0; j < plan.nfam; j++) n += ((grid && plan.ggrid[j] > 0) ? 1 : 0) + ((redo && plan.rgrid[j] > 0) ? 1 : 0);
     return n;
 }

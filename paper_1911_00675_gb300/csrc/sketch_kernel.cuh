@@ -131,7 +131,35 @@ struct SketchParams {
     void *gsig;                   // [4][kMaxGrid][m] records of 16 bytes
     float t_factor_grid;          // ln m + c for grid items (larger c: a failed round costs a full pass)
     int64_t grid_min;             // sets with at least this many elements use grid mode
+    // Prefilter lists (null: none).  list_n[s] is kUnlisted, or the number of entries of set s
+    // from list[(offsets[s] - offsets[0]) / 2]: the elements whose first point passes the first
+    // round's bound for every family (list_kernel).
+    const ulonglong2 *list;
+    const uint32_t *list_n;
 };
+
+constexpr uint32_t kUnlisted = 0xFFFFFFFFu;
+// Prefilter lists need the filter that compares U against bound * w (PMH_FILTER_WS)
+#ifndef PMH_FILTER_WS
+#define PMH_FILTER_WS 1         // filter compares U against bound * w (no reciprocal for rejected elements)
+#endif
+constexpr bool kListing = PMH_FILTER_WS != 0;
+
+// Threshold of the first round of an item: T = m t_factor / wsum = t_s 2^-sigma with t_s in
+// [1, 2), or t_s = +inf and sigma = 0 (a single unbounded round) when the sum gives no usable
+// estimate.  The sketch kernels and the prefilter take it from here alike.
+__device__ __forceinline__ void first_threshold(uint32_t m, float t_factor, double wsum, uint32_t npos, float *t_s,
+                                                int *sigma) {
+    *sigma = 0;
+    *t_s = __int_as_float(0x7F800000);
+    const double T = (double)m * (double)t_factor / wsum;
+    if (npos > 0 && T > 0.0 && T < 1e300) {
+        int ex;
+        const double fr = frexp(T, &ex);      // T = fr * 2^ex, fr in [0.5, 1)
+        *t_s = (float)(2.0 * fr);
+        *sigma = -(ex - 1);
+    }
+}
 
 struct TeamShared {
     int item_idx;
@@ -194,6 +222,7 @@ struct Ctx {
     uint16_t *perm;     // this warp's permutation array (ProbMinHash2/4), else null
     uint32_t *fy;       // this warp's Fisher-Yates write lists [kFyCap][32] (ProbMinHash2/4)
     int64_t beg;
+    int64_t off0;       // offsets[0] of the call (prefilter list positions count from it)
     uint32_t n;
     int sigma;
     unsigned int *gbound32;        // grid mode: the item's bound shared by all CTAs (float bits), else null
@@ -630,9 +659,6 @@ __device__ __forceinline__ bool push_redo(const SketchParams &P, int item_v, int
 #ifndef PMH_SEQ_KEEP
 #define PMH_SEQ_KEEP 8
 #endif
-#ifndef PMH_FILTER_WS
-#define PMH_FILTER_WS 1         // filter compares U against bound * w (no reciprocal for rejected elements)
-#endif
 #ifndef PMH_GRID_LEAN
 #define PMH_GRID_LEAN 1         // grid mode: the trimmed filter pass (grid_pass) for 16-byte aligned inputs
 #endif
@@ -867,9 +893,10 @@ __device__ __forceinline__ void team_sync() {
 
 // One pass over the elements [lo, hi) of the current item with the team's
 // current bound: filter, compacted survivors, q_max refreshes.  Every warp of
-// the team takes 64-element steps.
+// the team takes 64-element steps.  listed: [lo, hi) are entries of the
+// item's prefilter list instead, which carry the key and scaled weight.
 template <int FAM, bool F32, int TW, bool REJ>
-__device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
+__device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi, bool listed = false) {
     const SketchParams &P = *c.p;
     const int lane = threadIdx.x & 31;
     constexpr int team_warps = TW;
@@ -923,23 +950,30 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
                 }
             }
             // filter two elements per lane: the log-free lower bound of the first point.
-            // Weights and ids are loaded together (the id does not wait for the weight).
+            // Weights and ids are loaded together (the id does not wait for the weight); a
+            // list entry is (key, element index | scaled weight << 32).
             const float b32 = ld_volatile(&ts->bound32);
             bool surv[2];
             uint64_t key[2];
             uint32_t ev[2];
             float winv[2];
             bool valid[2];
-            double wv[2];
+            uint64_t wv[2];
             uint64_t idv[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint32_t e = base + 32 * h + lane;
-                wv[h] = 0.0;
+                wv[h] = 0;
                 idv[h] = 0;
                 if (e < end) {
-                    wv[h] = P.weights[c.beg + e];
-                    idv[h] = P.ids[c.beg + e];
+                    if (kListing && listed) {
+                        const ulonglong2 v = P.list[((c.beg - c.off0) >> 1) + e];
+                        idv[h] = v.x;
+                        wv[h] = v.y;
+                    } else {
+                        wv[h] = (uint64_t)__double_as_longlong(P.weights[c.beg + e]);
+                        idv[h] = P.ids[c.beg + e];
+                    }
                 }
             }
 #pragma unroll
@@ -950,21 +984,30 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
                 key[h] = 0;
                 winv[h] = 0.0f;
                 valid[h] = false;
-                if (e < end && weight_positive(wv[h])) {
+                if (kListing && listed) {
+                    valid[h] = e < end;
+                    key[h] = idv[h];
+                    ev[h] = (uint32_t)wv[h];
+                    winv[h] = __uint_as_float((uint32_t)(wv[h] >> 32));
+                } else if (e < end && weight_positive(__longlong_as_double((long long)wv[h]))) {
                     valid[h] = true;
                     key[h] = mix64(idv[h] ^ P.mixed_seed);
+#if PMH_FILTER_WS
+                    winv[h] = ws_scaled(c.unw ? 1.0 : __longlong_as_double((long long)wv[h]), c.sigma);
+#endif
+                }
+                if (valid[h]) {
 #if PMH_FILTER_WS
                     // w * 2^-sigma instead of its reciprocal: U te_lo > bound w rejects, and the
                     // reciprocal is taken only for the buffered survivors (process_survivors).
                     // Conservative: the products' roundings and the truncated mantissa are
                     // within the 16-ulp slack.
-                    winv[h] = ws_scaled(c.unw ? 1.0 : wv[h], c.sigma);
                     const float u = unif_lo(value_word(key[h], 1));
                     const float ulo = __fmul_rn(u, te_lo);
                     surv[h] = !(__fmul_rn(ulo, 1.0f - 16.0f * 0x1p-24f) > __fmul_rn(b32, winv[h]));
                     if constexpr (REJ) surv[h] = surv[h] || !(u < u1);
 #else
-                    winv[h] = winv_scaled(c.unw ? 1.0 : wv[h], c.sigma);
+                    winv[h] = winv_scaled(c.unw ? 1.0 : __longlong_as_double((long long)wv[h]), c.sigma);
                     const float u = unif_lo(value_word(key[h], 1));
                     const float xlo = winv[h] * u * te_lo;
                     surv[h] = !(xlo * (1.0f - 8.0f * 0x1p-24f) > b32);
@@ -993,6 +1036,7 @@ __device__ void run_range(Ctx<F32> &c, uint32_t lo, uint32_t hi) {
             if (P.counters) {
                 count(c, PMH_CNT_ELEMENTS, nvalid);
                 count(c, PMH_CNT_PREFILTERED, nvalid - nsurv);
+                if (listed) count(c, PMH_CNT_LISTED, nvalid);
             }
             __syncwarp();
         }
@@ -1049,15 +1093,9 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
         ts->unfilled = (int)m;
         ts->cont_n = 0;
         ts->redo = 0;
-        int sigma = 0;
-        float t_s = __int_as_float(0x7F800000);   // no usable estimate: a single unbounded round
-        const double T = (double)m * (double)P.t_factor / st0.wsum;
-        if (st0.npos > 0 && T > 0.0 && T < 1e300) {
-            int ex;
-            const double fr = frexp(T, &ex);      // T = fr * 2^ex, fr in [0.5, 1)
-            t_s = (float)(2.0 * fr);
-            sigma = -(ex - 1);
-        }
+        int sigma;
+        float t_s;
+        first_threshold(m, P.t_factor, st0.wsum, st0.npos, &t_s, &sigma);
         ts->sigma = sigma;
         ts->t_s = t_s;
     }
@@ -1075,7 +1113,15 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
     count_cyc(c, PMH_CNT_CYC_PASS0, t_ph);
     t_ph = cyc_now();
 
-    // ---- rounds
+    // ---- rounds.  A listed set's first round (whose bound is the list's) visits only its list
+    // entries; the elements the prefilter rejected count as visited and prefiltered here.
+    uint32_t listed_n = kUnlisted;
+    if (kListing && P.list_n && !c.unw && !c.rej && P.rounds > 0) listed_n = P.list_n[set];
+    if (listed_n != kUnlisted) {
+        count(c, PMH_CNT_ELEMENTS, leader ? st0.npos - listed_n : 0);
+        count(c, PMH_CNT_PREFILTERED, leader ? st0.npos - listed_n : 0);
+        count(c, PMH_CNT_LIST_SKIPPED, leader ? st0.npos - listed_n : 0);
+    }
     for (int round = 0; round <= P.rounds; ++round) {
         if (leader) {
             ts->next = 0ull;
@@ -1089,7 +1135,8 @@ __device__ void process_item(Ctx<F32> &c, int item_v, int64_t set) {
         }
         if (round > 0) count(c, PMH_CNT_ROUNDS, leader);
         team_sync<TW>();
-        run_range<FAM, F32, TW, REJ>(c, 0, c.n);
+        const bool listed = round == 0 && listed_n != kUnlisted;
+        run_range<FAM, F32, TW, REJ>(c, 0, listed ? listed_n : c.n, listed);
         const long long t_bar = cyc_now();
         team_sync<TW>();
         count_cyc(c, PMH_CNT_CYC_BARRIER, t_bar);
@@ -1596,6 +1643,7 @@ __global__ void __launch_bounds__(256, F32 ? PMH_GRID_MINB32 : PMH_GRID_MINB64) 
         const int64_t set = (int64_t)(it & ((1ull << 40) - 1));
         const int slot = (FAM - 1) * kMaxGrid + j;
         c.beg = p.offsets[set];
+        c.off0 = p.offsets[0];
         c.n = (uint32_t)(p.offsets[set + 1] - c.beg);
         grid_participate<FAM, F32, REJ>(c, &p.gstate[slot], (unsigned char *)p.gsig + (size_t)slot * p.m * 16, v, set);
         __syncthreads();
@@ -1680,6 +1728,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) sketch_kernel(const __grid_cons
             continue;
         }
         c.beg = b;
+        c.off0 = p.offsets[0];
         c.n = (uint32_t)(e - b);
         process_item<FAM, F32, TW, REJ>(c, v, set);
         team_sync<TW>();

@@ -24,11 +24,12 @@ TE_INVERSION, TE_REJECTION = 0, 1
 SHAPE_WARP, SHAPE_CTA8, SHAPE_QUAD, SHAPE_PAIR, SHAPE_QUAD8, SHAPE_QUAD8L = range(6)
 COUNTERS = ("elements", "points32", "points64", "contenders", "resolved", "rounds", "deep", "prefiltered",
             "cyc_pass0", "cyc_first", "cyc_deep", "cyc_refresh", "cyc_finish", "items", "cyc_surv", "cyc_item",
-            "cyc_warp", "cyc_barrier", "seq_steps", "seq_points", "redo")
+            "cyc_warp", "cyc_barrier", "seq_steps", "seq_points", "redo", "listed",
+            "list_hashed", "list_skipped")
 EXPORTS = ("pmh_create", "pmh_destroy", "pmh_last_error", "pmh_sketch_batch", "pmh_sketch_batch_host",
            "pmh_last_host_span_ms", "pmh_sketch_batch_noalloc",
            "pmh_set_profiling", "pmh_last_kernel_ms", "pmh_kernel_ms_history", "pmh_last_launches",
-           "pmh_set_thresholds", "pmh_set_limits", "pmh_sync_status", "pmh_set_te_sampler",
+           "pmh_set_thresholds", "pmh_set_limits", "pmh_sync_status", "pmh_set_te_sampler", "pmh_set_prefilter",
            "pmh_set_team_shape", "pmh_set_autotune", "pmh_last_team_shapes",
            "pmh_estimate_jp", "pmh_estimate_jp_block", "pmh_estimate_allpairs", "pmh_estimate_pairs", "pmh_merge", "pmh_check_exp1",
            "pmh_check_texp", "pmh_bbit_reduce", "pmh_bbit_allpairs", "pmh_pminhash_batch")
@@ -90,6 +91,8 @@ def load(path: str = LIB_PATH):
             lib.pmh_set_te_sampler.argtypes = [vp, i32]
             lib.pmh_set_limits.restype = i32
             lib.pmh_set_limits.argtypes = [vp, u32, i32]
+            lib.pmh_set_prefilter.restype = i32
+            lib.pmh_set_prefilter.argtypes = [vp, ctypes.c_double]
             lib.pmh_sync_status.restype = i32
             lib.pmh_sync_status.argtypes = [vp, vp, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), vp]
             lib.pmh_estimate_jp.restype = i32
@@ -267,6 +270,11 @@ class Handle:
         """Iteration cap of warp-cooperative expansion (0 = default) and contender records kept per
         item (-1 = default); an item whose contender log overflows is redone in FP64."""
         self._raise(load().pmh_set_limits(self._h, int(cap_points), int(max_contenders)))
+
+    def set_prefilter(self, list_factor: float = 2.0):
+        """Prefilter lists for the first round of sets of at least list_factor * m (ln m + t_c)
+        elements (<= 0: off); work only, results never depend on it."""
+        self._raise(load().pmh_set_prefilter(self._h, float(list_factor)))
 
     def set_te_sampler(self, sampler: int = TE_INVERSION):
         """Exp(lambda;0,1) of ProbMinHash3/3a/4 by inversion (default) or by the paper's rejection sampler."""
