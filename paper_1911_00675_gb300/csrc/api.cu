@@ -59,7 +59,7 @@ struct Workspace {
     size_t grid_bytes = 0;
     ulonglong2 *list = nullptr;      // prefilter lists (list_cap entries) and per-set entry counts
     int64_t list_cap = 0;
-    uint32_t *list_n = nullptr;
+    uint32_t *list_n = nullptr;      // and, behind the counts, the sets the prefilter pass takes
     int64_t list_n_cap = 0;
 };
 
@@ -216,7 +216,7 @@ static pmh_status ensure_list(pmh_handle h, Workspace &w, int64_t elements, int6
         w.list_n = nullptr;
         w.list_n_cap = 0;
         const int64_t cap = num_sets < 1024 ? 1024 : num_sets;
-        cudaError_t e = cudaMalloc(&w.list_n, (size_t)cap * sizeof(uint32_t));
+        cudaError_t e = cudaMalloc(&w.list_n, (size_t)cap * 2 * sizeof(uint32_t));
         if (e != cudaSuccess) return fail(h, PMH_ERR_NO_MEMORY, "prefilter list counts (%lld sets): %s", (long long)cap, cudaGetErrorString(e));
         w.list_n_cap = cap;
         h->graph_valid = false;
@@ -573,6 +573,7 @@ static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, cons
             if ((rc = ensure_list(h, w, n_el, num_sets))) return rc;
             ls.list = w.list;
             ls.list_n = w.list_n;
+            ls.sel = w.list_n + w.list_n_cap;
             ls.list_cap = w.list_cap;
         }
     }

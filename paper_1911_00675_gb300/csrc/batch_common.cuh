@@ -143,10 +143,11 @@ inline uint64_t host_mix64(uint64_t z) {
 // [516] counts the sets whose statistics are split over all blocks, [518, 520)
 // is the statistics kernel's set counter (u64), [520, 524) the per-family
 // lengths of the FP64 redo lists, [524, 528) the head counters of the redo
-// kernels and [528, 530) the prefilter kernel's set counter (u64); [530, ...)
-// lists the split sets (u64 set indices, kBigCap of them).
+// kernels, [528, 530) the prefilter kernel's counter (u64) and [530] the
+// number of sets it lists; [532, ...) lists the split sets (u64 set indices,
+// kBigCap of them).
 constexpr int kQHist = 0, kQStart = 256, kQHead = 512, kQBigCount = 516, kQStatNext = 518, kQRedoCount = 520,
-              kQRedoHead = 524, kQListNext = 528, kQBigList = 530;
+              kQRedoHead = 524, kQListNext = 528, kQListCount = 530, kQBigList = 532;
 constexpr int kBigCap = 1024;
 constexpr int kQMetaWords = kQBigList + 2 * kBigCap;
 constexpr int kQMetaClearWords = kQBigList;     // words cleared per call
@@ -408,99 +409,89 @@ static __global__ void __launch_bounds__(256) set_stats_big_kernel(const int64_t
 // variant.  Set s may use list[(offsets[s] - offsets[0]) / 2, + n/2) and
 // list_cap entries in all; a set whose survivors exceed n/2, or that does not
 // fit, stays unlisted (list_n = kUnlisted) and is filtered in full.
-// One block per set, the blocks taking sets 32 at a time from a shared
-// counter (warp 0 screens them by size, so that a batch of small sets costs
-// one block barrier per 32 sets); each thread keeps kListUnroll elements'
-// loads in flight (1,024 threads per SM at <= 64 registers).
+// The sets of list_min..list_max elements are gathered first (list_select:
+// one thread per set; every other set is marked unlisted), then list_kernel
+// gives one block to each gathered set, the blocks taking them from a shared
+// counter; each thread keeps kListUnroll elements' loads in flight (1,024
+// threads per SM at <= 64 registers).
 constexpr int kListBlock = PMH_LIST_BLOCK, kListUnroll = PMH_LIST_UNROLL;
-static __global__ void __launch_bounds__(kListBlock, 1024 / kListBlock) list_kernel(const SketchParams p, ulonglong2 *list, uint32_t *list_n,
-                                                          int64_t list_cap, int64_t list_min, int64_t list_max,
+static __global__ void __launch_bounds__(256) list_select(const int64_t *off, int64_t num_sets, uint32_t *sel,
+                                                          uint32_t *list_n, int64_t list_min, int64_t list_max,
                                                           unsigned int *meta) {
-    __shared__ long long s_base;
-    __shared__ unsigned int s_mask, s_cnt;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < num_sets; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = off[s + 1] - off[s];
+        if (n >= list_min && n <= list_max) sel[atomicAdd(&meta[kQListCount], 1u)] = (uint32_t)s;
+        else list_n[s] = kUnlisted;
+    }
+}
+
+static __global__ void __launch_bounds__(kListBlock, 1024 / kListBlock) list_kernel(const SketchParams p, ulonglong2 *list, uint32_t *list_n,
+                                                          const uint32_t *sel, int64_t list_cap, unsigned int *meta) {
+    __shared__ long long s_next;
+    __shared__ unsigned int s_cnt;
     const int lane = threadIdx.x & 31;
     const unsigned long long *wb = (const unsigned long long *)p.weights;
     const int64_t off0 = p.offsets[0];
     const float te_lo = p.tab.te_lo;
+    const int64_t nsel = (int64_t)ld_volatile((const int *)&meta[kQListCount]);
     for (;;) {
-        // warp 0 takes the next 32 sets and marks those outside the size range unlisted, so that
-        // the block stops only for the sets it hashes
-        if (threadIdx.x < 32) {
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd((unsigned long long *)(meta + kQListNext), 32ull);
-            base = __shfl_sync(0xFFFFFFFFu, base, 0);
-            const int64_t s = (int64_t)base + lane;
-            bool take = false;
-            if (s < p.num_sets) {
-                const int64_t n = p.offsets[s + 1] - p.offsets[s];
-                take = n >= list_min && n <= list_max;
-                if (!take) list_n[s] = kUnlisted;
-            }
-            const unsigned msk = __ballot_sync(0xFFFFFFFFu, take);
-            if (lane == 0) {
-                s_base = (long long)base;
-                s_mask = msk;
+        if (threadIdx.x == 0) {
+            s_next = (long long)atomicAdd((unsigned long long *)(meta + kQListNext), 1ull);
+            s_cnt = 0;
+        }
+        __syncthreads();
+        const int64_t j = s_next;
+        if (j >= nsel) break;
+        const int64_t s = sel[j];
+        const int64_t b = p.offsets[s], n = p.offsets[s + 1] - b;
+        const int64_t lb = (b - off0) >> 1, cap = n >> 1;
+        const SetStat st = p.stats[s];
+        float t_s;
+        int sigma;
+        first_threshold(p.m, p.t_factor, st.wsum, st.npos, &t_s, &sigma);
+        const bool ok = b >= off0 && !st.bad && st.npos > 0 && lb + cap <= list_cap && !isinf(t_s);
+        if (ok) {
+            for (int64_t e0 = 0; e0 < n; e0 += kListUnroll * (int64_t)blockDim.x) {
+                uint64_t wv[kListUnroll], iv[kListUnroll];
+#pragma unroll
+                for (int u = 0; u < kListUnroll; ++u) {
+                    const int64_t e = e0 + u * (int64_t)blockDim.x + threadIdx.x;
+                    wv[u] = 0;
+                    iv[u] = 0;
+                    if (e < n) {
+                        wv[u] = __ldcs(wb + b + e);
+                        iv[u] = __ldcs((const unsigned long long *)p.ids + b + e);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kListUnroll; ++u) {
+                    const int64_t e = e0 + u * (int64_t)blockDim.x + threadIdx.x;
+                    const double w = __longlong_as_double((long long)wv[u]);
+                    bool keep = false;
+                    uint64_t key = 0;
+                    float ws = 0.0f;
+                    if (e < n && weight_positive(w)) {
+                        key = mix64(iv[u] ^ p.mixed_seed);
+                        ws = ws_scaled(w, sigma);
+                        const float ulo = __fmul_rn(unif_lo(value_word(key, 1)), te_lo);
+                        keep = !(__fmul_rn(ulo, 1.0f - 16.0f * 0x1p-24f) > __fmul_rn(t_s, ws));
+                    }
+                    const unsigned msk = __ballot_sync(0xFFFFFFFFu, keep);
+                    unsigned int wbase = 0;
+                    if (lane == 0 && msk) wbase = atomicAdd(&s_cnt, (unsigned int)__popc(msk));
+                    wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
+                    const unsigned int pos = wbase + __popc(msk & ((1u << lane) - 1u));
+                    if (keep && pos < (uint64_t)cap)
+                        list[lb + pos] = make_ulonglong2(key, (uint64_t)(uint32_t)e | ((uint64_t)__float_as_uint(ws) << 32));
+                }
             }
         }
         __syncthreads();
-        const int64_t base = s_base;
-        unsigned mask = s_mask;
-        if (base >= p.num_sets) break;
-        while (mask) {
-            const int64_t s = base + __ffs(mask) - 1;
-            mask &= mask - 1;
-            if (threadIdx.x == 0) s_cnt = 0;
-            __syncthreads();
-            const int64_t b = p.offsets[s], n = p.offsets[s + 1] - b;
-            const int64_t lb = (b - off0) >> 1, cap = n >> 1;
-            const SetStat st = p.stats[s];
-            float t_s;
-            int sigma;
-            first_threshold(p.m, p.t_factor, st.wsum, st.npos, &t_s, &sigma);
-            const bool ok = b >= off0 && !st.bad && st.npos > 0 && lb + cap <= list_cap && !isinf(t_s);
-            if (ok) {
-                for (int64_t e0 = 0; e0 < n; e0 += kListUnroll * (int64_t)blockDim.x) {
-                    uint64_t wv[kListUnroll], iv[kListUnroll];
-#pragma unroll
-                    for (int u = 0; u < kListUnroll; ++u) {
-                        const int64_t e = e0 + u * (int64_t)blockDim.x + threadIdx.x;
-                        wv[u] = 0;
-                        iv[u] = 0;
-                        if (e < n) {
-                            wv[u] = __ldcs(wb + b + e);
-                            iv[u] = __ldcs((const unsigned long long *)p.ids + b + e);
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < kListUnroll; ++u) {
-                        const int64_t e = e0 + u * (int64_t)blockDim.x + threadIdx.x;
-                        const double w = __longlong_as_double((long long)wv[u]);
-                        bool keep = false;
-                        uint64_t key = 0;
-                        float ws = 0.0f;
-                        if (e < n && weight_positive(w)) {
-                            key = mix64(iv[u] ^ p.mixed_seed);
-                            ws = ws_scaled(w, sigma);
-                            const float ulo = __fmul_rn(unif_lo(value_word(key, 1)), te_lo);
-                            keep = !(__fmul_rn(ulo, 1.0f - 16.0f * 0x1p-24f) > __fmul_rn(t_s, ws));
-                        }
-                        const unsigned msk = __ballot_sync(0xFFFFFFFFu, keep);
-                        unsigned int wbase = 0;
-                        if (lane == 0 && msk) wbase = atomicAdd(&s_cnt, (unsigned int)__popc(msk));
-                        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
-                        const unsigned int pos = wbase + __popc(msk & ((1u << lane) - 1u));
-                        if (keep && pos < (uint64_t)cap)
-                            list[lb + pos] = make_ulonglong2(key, (uint64_t)(uint32_t)e | ((uint64_t)__float_as_uint(ws) << 32));
-                    }
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                list_n[s] = (ok && (int64_t)s_cnt <= cap) ? s_cnt : kUnlisted;
-                if (ok && p.counters) atomicAdd(&p.counters[PMH_CNT_LIST_HASHED], (unsigned long long)st.npos);
-            }
+        if (threadIdx.x == 0) {
+            list_n[s] = (ok && (int64_t)s_cnt <= cap) ? s_cnt : kUnlisted;
+            if (ok && p.counters) atomicAdd(&p.counters[PMH_CNT_LIST_HASHED], (unsigned long long)st.npos);
         }
-        __syncthreads();   // s_base and s_mask are read by every thread before warp 0 refills them
+        __syncthreads();
     }
 }
 
@@ -616,11 +607,12 @@ struct FamilyFork {
     cudaEvent_t join[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
-// Prefilter lists of a call (list == null: none): list_cap entries, list_n of num_sets entries, for
-// the sets of list_min..list_max elements.
+// Prefilter lists of a call (list == null: none): list_cap entries, list_n and sel of num_sets
+// entries, for the sets of list_min..list_max elements.
 struct ListSpec {
     ulonglong2 *list = nullptr;
     uint32_t *list_n = nullptr;
+    uint32_t *sel = nullptr;
     int64_t list_cap = 0, list_min = 0, list_max = 0;
 };
 
@@ -651,9 +643,10 @@ inline cudaError_t enqueue_batch(SketchParams p, const Plan &plan, int precision
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
     p.list = nullptr;
     p.list_n = nullptr;
-    if (kListing && ls.list && ls.list_n && p.rounds > 0) {
-        list_kernel<<<sm_count * (1024 / kListBlock), kListBlock, 0, st>>>(p, ls.list, ls.list_n, ls.list_cap, ls.list_min,
-                                                                          ls.list_max, qmeta);
+    if (kListing && ls.list && ls.list_n && ls.sel && p.rounds > 0) {
+        const int lg = (int)std::max<int64_t>(1, std::min<int64_t>((p.num_sets + 255) / 256, (int64_t)sm_count * 8));
+        list_select<<<lg, 256, 0, st>>>(p.offsets, p.num_sets, ls.sel, ls.list_n, ls.list_min, ls.list_max, qmeta);
+        list_kernel<<<sm_count * (1024 / kListBlock), kListBlock, 0, st>>>(p, ls.list, ls.list_n, ls.sel, ls.list_cap, qmeta);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         p.list = ls.list;
         p.list_n = ls.list_n;
@@ -727,7 +720,7 @@ struct Thresholds {
 
 // Kernel launches of one enqueue_batch call (fixed by the plan).
 inline int launch_count(const Plan &plan, bool grid, bool redo, bool listed = false) {
-    int n = 5 + plan.nfam + (grid ? 1 : 0) + (listed ? 1 : 0);
+    int n = 5 + plan.nfam + (grid ? 1 : 0) + (listed ? 2 : 0);
     for (int j = 0; j < plan.nfam; j++) n += ((grid && plan.ggrid[j] > 0) ? 1 : 0) + ((redo && plan.rgrid[j] > 0) ? 1 : 0);
     return n;
 }

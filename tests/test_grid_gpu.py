@@ -170,18 +170,18 @@ def test_launch_count_reported(H):
     b = W.random_batch(37, [10, 20], 64, "uniform")
     H.set_thresholds(grid_min=0)
     run(H, b, ["1", "2", "3", "4"], 1)
-    # queue (3) + statistics (2) + prefilter pass (1) + per family one sketch kernel and one FP64
-    # redo kernel
-    assert H.last_launches() == 5 + 1 + 4 + 4
+    # queue (3) + statistics (2) + prefilter pass (2: set selection, hashing) + per family one
+    # sketch kernel and one FP64 redo kernel
+    assert H.last_launches() == 5 + 2 + 4 + 4
     run(H, b, ["1", "2", "3", "4"], 0)
-    assert H.last_launches() == 5 + 1 + 4                 # FP64 calls have no redo kernels
+    assert H.last_launches() == 5 + 2 + 4                 # FP64 calls have no redo kernels
     H.set_prefilter(0.0)
     run(H, b, ["1", "2", "3", "4"], 0)
     assert H.last_launches() == 5 + 4                     # no prefilter pass
     H.set_prefilter()
     H.set_thresholds()
     run(H, b, ["1", "3a"], 1)
-    assert H.last_launches() == 5 + 1 + 2 + 2 + 1 + 2     # + grid reset + one grid kernel per family
+    assert H.last_launches() == 5 + 2 + 2 + 2 + 1 + 2     # + grid reset + one grid kernel per family
 
 
 @pytest.mark.slow
