@@ -179,7 +179,7 @@ pmh_status pmh_sync_status(pmh_handle h, const int32_t *set_status, int64_t n, i
  * weights, offsets and the outputs in host memory.
  *
  * The call splits the sets into `chunks` contiguous ranges by work (the first
- * range gets half the share of the others; chunks <= 0: automatic, 3 for
+ * range gets half the share of the others; chunks <= 0: automatic, 4 for
  * batches of 2^22 elements or more, else 1) and pipelines them on internal
  * streams: host->device copy of a range's elements; the sketch of the range,
  * alternating between two compute streams so that one range's kernels fill

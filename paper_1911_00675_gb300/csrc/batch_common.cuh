@@ -451,26 +451,30 @@ static __global__ void __launch_bounds__(kListBlock, 1024 / kListBlock) list_ker
         first_threshold(p.m, p.t_factor, st.wsum, st.npos, &t_s, &sigma);
         const bool ok = b >= off0 && !st.bad && st.npos > 0 && lb + cap <= list_cap && !isinf(t_s);
         if (ok) {
-            for (int64_t e0 = 0; e0 < n; e0 += kListUnroll * (int64_t)blockDim.x) {
+            // 32-bit offsets within the set (n <= list_max < 2^32)
+            const unsigned long long *wset = wb + b, *iset = (const unsigned long long *)p.ids + b;
+            ulonglong2 *lset = list + lb;
+            const uint32_t n32 = (uint32_t)n;
+            for (uint32_t e0 = 0; e0 < n32; e0 += kListUnroll * kListBlock) {
                 uint64_t wv[kListUnroll], iv[kListUnroll];
 #pragma unroll
                 for (int u = 0; u < kListUnroll; ++u) {
-                    const int64_t e = e0 + u * (int64_t)blockDim.x + threadIdx.x;
+                    const uint32_t e = e0 + u * kListBlock + threadIdx.x;
                     wv[u] = 0;
                     iv[u] = 0;
-                    if (e < n) {
-                        wv[u] = __ldcs(wb + b + e);
-                        iv[u] = __ldcs((const unsigned long long *)p.ids + b + e);
+                    if (e < n32) {
+                        wv[u] = __ldcs(wset + e);
+                        iv[u] = __ldcs(iset + e);
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < kListUnroll; ++u) {
-                    const int64_t e = e0 + u * (int64_t)blockDim.x + threadIdx.x;
+                    const uint32_t e = e0 + u * kListBlock + threadIdx.x;
                     const double w = __longlong_as_double((long long)wv[u]);
                     bool keep = false;
                     uint64_t key = 0;
                     float ws = 0.0f;
-                    if (e < n && weight_positive(w)) {
+                    if (e < n32 && weight_positive(w)) {
                         key = mix64(iv[u] ^ p.mixed_seed);
                         ws = ws_scaled(w, sigma);
                         const float ulo = __fmul_rn(unif_lo(value_word(key, 1)), te_lo);
@@ -482,7 +486,7 @@ static __global__ void __launch_bounds__(kListBlock, 1024 / kListBlock) list_ker
                     wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
                     const unsigned int pos = wbase + __popc(msk & ((1u << lane) - 1u));
                     if (keep && pos < (uint64_t)cap)
-                        list[lb + pos] = make_ulonglong2(key, (uint64_t)(uint32_t)e | ((uint64_t)__float_as_uint(ws) << 32));
+                        lset[pos] = make_ulonglong2(key, (uint64_t)e | ((uint64_t)__float_as_uint(ws) << 32));
                 }
             }
         }
