@@ -321,7 +321,7 @@ pmh_status pmh_last_launches(pmh_handle h, int32_t *launches);
  * while a component is still empty they repeat with T x 4, and after `rounds`
  * finite rounds with T = infinity (the paper's unbounded loop).
  *
- *   t_c       finite; default 4.
+ *   t_c       finite; default 3.
  *   t_c_grid  the same constant for grid-mode items; default 8.
  *   rounds    0..64 finite rounds; default 5.
  *   grid_min  sets with at least grid_min elements are processed by all SMs

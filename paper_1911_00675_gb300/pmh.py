@@ -262,7 +262,7 @@ class Handle:
         self._raise(load().pmh_last_team_shapes(self._h, arr))
         return list(arr)
 
-    def set_thresholds(self, t_c: float = 4.0, t_c_grid: float = 8.0, rounds: int = 5, grid_min: int = 1 << 20):
+    def set_thresholds(self, t_c: float = 3.0, t_c_grid: float = 8.0, rounds: int = 5, grid_min: int = 1 << 20):
         """Work-only tuning of later sketch_batch calls (results never depend on it)."""
         self._raise(load().pmh_set_thresholds(self._h, float(t_c), float(t_c_grid), int(rounds), int(grid_min)))
 
