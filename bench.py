@@ -54,18 +54,21 @@ OPS_PAIR_COMPONENT = 3  # equal-component count: two 32-bit compares and one add
 # 8-bit codes, per pair of 64-bit words (8 fields): xor (2), per 32-bit half three fold steps of
 # shift + or (6) and and-not + popcount (2), two adds (2)
 OPS_BBIT_WORD = 2 + 2 * (6 + 2) + 2
-# DRAM bytes (read + write) of the four family sketch kernels and their redo kernels per
-# element-variant, from the ncu capture summarised in profiles/sketch_kernel_fp32_c2_2000sets.md
-# (1,349.6 MB for 99,379,884 element-variants); the traffic grows in proportion to the elements
-# (one pass over ids and weights per family).
-TRAFFIC_BYTES_PER_ELEMENT_VARIANT = 13.58
+# DRAM bytes (read + write) of the prefilter pass, the four family sketch kernels and their redo
+# kernels per element-variant, from the ncu capture summarised in
+# profiles/sketch_kernel_fp32_c2_2000sets.md (888.2 MB for 99,379,884 element-variants); the
+# traffic grows in proportion to the elements (one pass over the ids and weights of a listed set,
+# one per family over the others).
+TRAFFIC_BYTES_PER_ELEMENT_VARIANT = 8.94
 # Pipe use of the same four family kernels in that capture (per kernel, min-max over the families):
 # what binds them beside the op model above.
-NCU_SKETCH = {"issue_active_pct": [54.9, 61.6], "alu_pipe_pct": [42.9, 50.0], "fma_pipe_pct": [17.4, 18.8],
-              "dram_throughput_pct": [1.7, 3.7], "active_lanes_per_inst": [24.9, 28.0],
-              "warp_inst_per_element_variant": 20.0, "source": "profiles/sketch_kernel_fp32_c2_2000sets.md"}
-TRAFFIC_BASIS = ("ncu dram bytes per element-variant on a 2,000-set c2-shaped batch (kernel source of commit "
-                 "8a0d5f2) x this step's work")
+NCU_SKETCH = {"issue_active_pct": [60.6, 65.9], "alu_pipe_pct": [44.9, 51.9], "fma_pipe_pct": [18.3, 19.5],
+              "dram_throughput_pct": [1.0, 2.3], "active_lanes_per_inst": [24.9, 27.9],
+              "warp_inst_per_element_variant": 17.8, "prefilter_issue_active_pct": 59.5,
+              "prefilter_alu_pipe_pct": 56.4, "source": "profiles/sketch_kernel_fp32_c2_2000sets.md, "
+                                                        "profiles/list_kernel_c2_2000sets.md"}
+TRAFFIC_BASIS = ("ncu dram bytes per element-variant on a 2,000-set c2-shaped batch (sketch kernel source of "
+                 "commit d70b279 and later, first-round constant 4) x this step's work")
 
 
 def parse():
