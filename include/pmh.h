@@ -353,11 +353,12 @@ pmh_status pmh_set_thresholds(pmh_handle h, double t_c, double t_c_grid, int32_t
  *
  * Memory: lists of 8 bytes per element of the call (16-byte entries for up
  * to half the elements of each set; a set with more survivors than that is
- * filtered in full) plus 4 bytes per set, kept in the handle.  The first
+ * filtered in full) plus 8 bytes per set, kept in the handle.  The first
  * pmh_sketch_batch call on new (ids, weights, offsets, num_sets) arrays reads
  * offsets[0] and offsets[num_sets] back to size them, which waits for
  * `stream`; calls made during a stream capture before that read skip the
- * prefilter.  Later calls on the same arrays reuse the count: if the offsets
+ * prefilter.  Later calls on the same arrays (the handle keeps the counts of
+ * its 16 most recent batches) reuse the count: if the offsets
  * were rewritten with more elements in between, the sets that no longer fit
  * in the lists are filtered in full (same result, more work).
  * Errors: PMH_ERR_INVALID_ARG for NULL h or a non-finite list_factor.

@@ -105,10 +105,12 @@ struct pmh_handle_s {
     cudaEvent_t tev[3 + 4] = {};             // autotuning: queue/sketch brackets + one per family
     unsigned long long *status_scratch = nullptr;   // pmh_sync_status: 8 counts + the first failing (index, code)
     unsigned int *pm_counter = nullptr;              // pmh_pminhash_batch: the blocks' set counter
-    // element count of the most recent batch read back (sizes the prefilter lists), keyed by its arrays
-    const void *ncache_ids = nullptr, *ncache_w = nullptr;
-    const int64_t *ncache_off = nullptr;
-    int64_t ncache_sets = -1, ncache_n = 0;
+    // element counts of recent batches read back (they size the prefilter lists), keyed by their arrays
+    struct NCount {
+        const void *ids, *w, *off;
+        int64_t sets, n;
+    };
+    std::vector<NCount> ncache;   // most recent last, at most 16
     // profiling events
     bool profiling = false;
     bool prof_recorded = false;        // the most recent call was profiled
@@ -240,21 +242,23 @@ static bool list_bounds(const Thresholds &th, uint32_t m, float t_factor, int64_
 static pmh_status element_count(pmh_handle h, const void *ids, const void *weights, const int64_t *offsets,
                                 int64_t num_sets, cudaStream_t st, cudaStreamCaptureStatus cs, int64_t *n) {
     *n = -1;
-    if (h->ncache_off == offsets && h->ncache_ids == ids && h->ncache_w == weights && h->ncache_sets == num_sets) {
-        *n = h->ncache_n;
-        return PMH_OK;
+    for (size_t i = 0; i < h->ncache.size(); i++) {
+        const pmh_handle_s::NCount c = h->ncache[i];
+        if (c.off == offsets && c.ids == ids && c.w == weights && c.sets == num_sets) {
+            h->ncache.erase(h->ncache.begin() + (std::ptrdiff_t)i);   // most recent last
+            h->ncache.push_back(c);
+            *n = c.n;
+            return PMH_OK;
+        }
     }
     if (cs != cudaStreamCaptureStatusNone) return PMH_OK;
     int64_t v[2] = {0, 0};
     CUDA_TRY(h, cudaMemcpyAsync(&v[0], offsets, sizeof(int64_t), cudaMemcpyDefault, st));
     CUDA_TRY(h, cudaMemcpyAsync(&v[1], offsets + num_sets, sizeof(int64_t), cudaMemcpyDefault, st));
     CUDA_TRY(h, cudaStreamSynchronize(st));
-    h->ncache_off = offsets;
-    h->ncache_ids = ids;
-    h->ncache_w = weights;
-    h->ncache_sets = num_sets;
-    h->ncache_n = v[1] > v[0] ? v[1] - v[0] : 0;
-    *n = h->ncache_n;
+    if (h->ncache.size() >= 16) h->ncache.erase(h->ncache.begin());
+    h->ncache.push_back({ids, weights, offsets, num_sets, v[1] > v[0] ? v[1] - v[0] : 0});
+    *n = h->ncache.back().n;
     return PMH_OK;
 }
 
