@@ -675,21 +675,28 @@ def main():
     sm_mhz = clk["sm_mhz"] if clk else 2070.0
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     survivors = c["elements"] - c["prefiltered"]
-    # element-variants the sketch kernels filtered from the ids and weights; those of listed sets
-    # were filtered from the lists (c["listed"]) or rejected by the prefilter pass (c["list_skipped"]),
-    # which hashed each of its elements once (c["list_hashed"])
+    # algorithmic work: the per-unit figures x the units one step processes (every element-variant of
+    # the batch, every point the kernels evaluated, every survivor)
+    per_launch_ops = work * OPS_ELEMENT + c["points32"] * OPS_POINT + survivors * OPS_SURVIVOR
+    # the operations this design executes for them: the prefilter pass hashes the elements of listed
+    # sets once for all variants (c["list_hashed"]); the variants then filter only the list entries
+    # (c["listed"]) and skip the rest (c["list_skipped"]); extra rounds revisit elements
     filtered_full = c["elements"] - c["list_skipped"] - c["listed"]
-    per_launch_ops = (filtered_full * OPS_ELEMENT + c["listed"] * OPS_LISTED + c["list_hashed"] * OPS_ELEMENT
-                      + c["points32"] * OPS_POINT + survivors * OPS_SURVIVOR)
+    executed_ops = (filtered_full * OPS_ELEMENT + c["listed"] * OPS_LISTED + c["list_hashed"] * OPS_ELEMENT
+                    + c["points32"] * OPS_POINT + survivors * OPS_SURVIVOR)
     achieved = per_launch_ops / (k_avg * 1e-3) / 1e12
     peak = n_sms * LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (32-bit lane ops)",
                 "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_ELEMENT_VARIANT * work,
                 "traffic_basis": TRAFFIC_BASIS,
-                "kernel": "pmh::sketch_kernel<FP32> (four family launches per step)",
-                "kernel_ms": k_avg, "kernel_ms_basis": "library CUDA events around the sketch kernels of each "
-                                                         "profiled call (the second timed pass)",
+                "kernel": "pmh::list_kernel + pmh::sketch_kernel<FP32> (prefilter pass and four family launches per step)",
+                "kernel_ms": k_avg, "kernel_ms_basis": "library CUDA events around the prefilter pass and the sketch "
+                                                         "kernels of each profiled call (the second timed pass)",
                 "ops_per_launch": per_launch_ops,
+                "ops_basis": f"{OPS_ELEMENT} per element-variant x {work} + {OPS_POINT} per point x points32 "
+                             f"{OPS_SURVIVOR:+d} per survivor",
+                "executed_ops_per_launch": executed_ops,
+                "frac_executed": executed_ops / (k_avg * 1e-3) / 1e12 / peak,
                 "peak_basis": f"{n_sms} SMs x {LANES_PER_SM_CLK} lane-ops/clk x {sm_mhz:.0f} MHz (median under load)",
                 "ncu": NCU_SKETCH}
 
