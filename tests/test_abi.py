@@ -73,3 +73,21 @@ def test_create_without_device_reports_an_error(lib):
     rc = lib.pmh_create(ctypes.byref(h), 0)
     assert rc != 0 and not h.value
     assert lib.pmh_last_error(None)
+
+
+def test_binding_counters_match_header():
+    """The binding's counter names follow the header's PMH_CNT_* indices, and cover all of them."""
+    from paper_1911_00675_gb300 import pmh
+    with open(os.path.join(ROOT, "include", "pmh.h")) as f:
+        src = f.read()
+    idx = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"PMH_CNT_([A-Z0-9_]+)\s*=\s*(\d+)", src)}
+    total = int(re.search(r"PMH_NUM_COUNTERS\s*=\s*(\d+)", src).group(1))
+    assert len(pmh.COUNTERS) == total == len(idx)
+    for name, i in idx.items():
+        assert pmh.COUNTERS[i] == name, (name, i)
+
+
+def test_prefilter_setter_checks_its_arguments(lib):
+    lib.pmh_set_prefilter.restype = ctypes.c_int32
+    lib.pmh_set_prefilter.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    assert lib.pmh_set_prefilter(None, 2.0) == 1   # PMH_ERR_INVALID_ARG: no handle
