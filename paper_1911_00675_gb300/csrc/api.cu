@@ -93,9 +93,12 @@ struct pmh_handle_s {
     int last_launches = 0;
     int last_chunks = 0;
     HostPipe hp;
-    FamilyFork ff;               // family kernels side by side (pmh_sketch_batch)
+    FamilyFork ff[2];            // family kernels side by side, per workspace
 #ifndef PMH_FAMILY_FORK
 #define PMH_FAMILY_FORK 1
+#endif
+#ifndef PMH_PIPE_FORK
+#define PMH_PIPE_FORK 1          // the host-buffer pipeline's ranges fork their family kernels too
 #endif
     bool concurrent_families = PMH_FAMILY_FORK;
     int force_shape[4] = {-1, -1, -1, -1};   // per family: TeamShape, or -1
@@ -269,28 +272,30 @@ static pmh_status ensure_workspace(pmh_handle h, Workspace &w, int64_t num_sets,
     return rc;
 }
 
-// Streams and events of the family fork, created on first use.
-static pmh_status ensure_fork(pmh_handle h) {
-    if (h->ff.fork) return PMH_OK;
+// Streams and events of workspace wsi's family fork, created on first use.
+static pmh_status ensure_fork(pmh_handle h, int wsi) {
+    FamilyFork &ff = h->ff[wsi];
+    if (ff.fork) return PMH_OK;
     for (int i = 0; i < 4; i++) {
-        CUDA_TRY(h, cudaStreamCreateWithFlags(&h->ff.s[i], cudaStreamNonBlocking));
-        CUDA_TRY(h, cudaEventCreateWithFlags(&h->ff.join[i], cudaEventDisableTiming));
+        CUDA_TRY(h, cudaStreamCreateWithFlags(&ff.s[i], cudaStreamNonBlocking));
+        CUDA_TRY(h, cudaEventCreateWithFlags(&ff.join[i], cudaEventDisableTiming));
     }
-    CUDA_TRY(h, cudaEventCreateWithFlags(&h->ff.fork, cudaEventDisableTiming));
+    CUDA_TRY(h, cudaEventCreateWithFlags(&ff.fork, cudaEventDisableTiming));
     return PMH_OK;
 }
 
-// Enqueues the whole batch on `st` with workspace `w`; with `fork`, the family
-// kernels run side by side on the handle's fork streams.
-static pmh_status enqueue_sketch(pmh_handle h, Workspace &w, const SketchParams &p, const Plan &plan, int precision,
+// Enqueues the whole batch on `st` with workspace wsi; with `fork`, the family
+// kernels run side by side on that workspace's fork streams.
+static pmh_status enqueue_sketch(pmh_handle h, int wsi, const SketchParams &p, const Plan &plan, int precision,
                                  cudaStream_t st, cudaEvent_t *prof_ev, cudaEvent_t *fam_ev, bool fork,
                                  const ListSpec &ls) {
     if (fork) {
-        pmh_status rc = ensure_fork(h);
+        pmh_status rc = ensure_fork(h, wsi);
         if (rc) return rc;
     }
+    Workspace &w = h->ws[wsi];
     cudaError_t e = enqueue_batch(p, plan, precision, h->sm_count, w.queue, w.redo, w.qmeta, w.stats, st, prof_ev, fam_ev,
-                                  fork ? &h->ff : nullptr, ls);
+                                  fork ? &h->ff[wsi] : nullptr, ls);
     if (e != cudaSuccess) return fail(h, PMH_ERR_CUDA, "sketch launch: %s", cudaGetErrorString(e));
     return PMH_OK;
 }
@@ -344,11 +349,13 @@ extern "C" void pmh_destroy(pmh_handle h) {
     for (int i = 0; i < 4; i++) if (h->hp.s[i]) cudaStreamDestroy(h->hp.s[i]);
     for (cudaEvent_t e : h->hp.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : h->hp.span) if (e) cudaEventDestroy(e);
-    for (int i = 0; i < 4; i++) {
-        if (h->ff.s[i]) cudaStreamDestroy(h->ff.s[i]);
-        if (h->ff.join[i]) cudaEventDestroy(h->ff.join[i]);
+    for (FamilyFork &ff : h->ff) {
+        for (int i = 0; i < 4; i++) {
+            if (ff.s[i]) cudaStreamDestroy(ff.s[i]);
+            if (ff.join[i]) cudaEventDestroy(ff.join[i]);
+        }
+        if (ff.fork) cudaEventDestroy(ff.fork);
     }
-    if (h->ff.fork) cudaEventDestroy(h->ff.fork);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
@@ -623,10 +630,12 @@ static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, cons
         h->prof_calls++;
     }
     h->prof_recorded = prof_ev != nullptr;
-    const bool fork = h->concurrent_families && wsi == 0 && !fam_ev;
-    if (fork && (rc = ensure_fork(h))) return rc;   // before any capture begins
+    // the family kernels side by side; the host-buffer pipeline's ranges (fam_ev: their outputs go
+    // back family by family) fork on their own workspace's streams
+    const bool fork = h->concurrent_families && (!fam_ev || PMH_PIPE_FORK);
+    if (fork && (rc = ensure_fork(h, wsi))) return rc;   // before any capture begins
     if (!allow_graph || wsi != 0 || fam_ev || prof_ev || !h->use_graph || cs != cudaStreamCaptureStatusNone || !st)
-        return enqueue_sketch(h, w, p, plan, precision, st, prof_ev, fam_ev, fork, ls);
+        return enqueue_sketch(h, wsi, p, plan, precision, st, prof_ev, fam_ev, fork, ls);
 
     GraphKey key{};
     key.ids = ids; key.weights = weights; key.offsets = offsets; key.out_ids = out_ids; key.out_q = out_q;
@@ -639,7 +648,7 @@ static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, cons
         if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
         h->graph_valid = false;
         CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_sketch(h, w, p, plan, precision, h->cap_stream, nullptr, nullptr, fork, ls);
+        rc = enqueue_sketch(h, wsi, p, plan, precision, h->cap_stream, nullptr, nullptr, fork, ls);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
         if (rc) { if (g) cudaGraphDestroy(g); return rc; }
