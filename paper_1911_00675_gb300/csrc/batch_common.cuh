@@ -402,8 +402,9 @@ static __global__ void __launch_bounds__(256) set_stats_big_kernel(const int64_t
 // Exp(lambda;0,1) <= 1 of Exp(1)) and the first round's bound t_s, which the
 // running bound of every later point of that round only undercuts.  Each kept
 // element is written as (key, index | scaled weight << 32), so that the first
-// round of every weighted variant of the set visits only these entries and
-// hashes each key once instead of twice.  The sets that profit are those much
+// round of every weighted variant of the set visits only these entries, with
+// one SplitMix64 word to compute per entry (point 1's value word) instead of
+// two per element (the key and that word).  The sets that profit are those much
 // larger than m (ln m + c), where most elements fail the first point's test;
 // the elements are hashed here once for all variants instead of once per
 // variant.  Set s may use list[(offsets[s] - offsets[0]) / 2, + n/2) and

@@ -132,8 +132,8 @@ struct SketchParams {
     float t_factor_grid;          // ln m + c for grid items (larger c: a failed round costs a full pass)
     int64_t grid_min;             // sets with at least this many elements use grid mode
     // Prefilter lists (null: none).  list_n[s] is kUnlisted, or the number of entries of set s
-    // from list[(offsets[s] - offsets[0]) / 2]: the elements whose first point passes the first
-    // round's bound for every family (list_kernel).
+    // from list[(offsets[s] - offsets[0]) / 2]: the elements whose first point can pass the first
+    // round's bound in some family, a superset of each variant's survivors (list_kernel).
     const ulonglong2 *list;
     const uint32_t *list_n;
 };
