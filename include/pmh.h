@@ -360,7 +360,8 @@ pmh_status pmh_set_thresholds(pmh_handle h, double t_c, double t_c_grid, int32_t
  * prefilter.  Later calls on the same arrays (the handle keeps the counts of
  * its 16 most recent batches) reuse the count: if the offsets
  * were rewritten with more elements in between, the sets that no longer fit
- * in the lists are filtered in full (same result, more work).
+ * in the lists are filtered in full (same result, more work).  A call that
+ * finds no device memory for the lists runs without them.
  * Errors: PMH_ERR_INVALID_ARG for NULL h or a non-finite list_factor.
  */
 pmh_status pmh_set_prefilter(pmh_handle h, double list_factor);

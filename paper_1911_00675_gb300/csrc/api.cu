@@ -581,11 +581,20 @@ static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, cons
         int64_t n_el = n_hint;
         if (n_el < 0 && (rc = element_count(h, ids, weights, offsets, num_sets, st, cs, &n_el))) return rc;
         if (n_el > 0) {
-            if ((rc = ensure_list(h, w, n_el, num_sets))) return rc;
-            ls.list = w.list;
-            ls.list_n = w.list_n;
-            ls.sel = w.list_n + w.list_n_cap;
-            ls.list_cap = w.list_cap;
+            rc = ensure_list(h, w, n_el, num_sets);
+            if (rc == PMH_ERR_NO_MEMORY) {
+                // the lists only save work: without room for them every element is filtered in full
+                (void)cudaGetLastError();
+                h->err.clear();
+                rc = PMH_OK;
+            } else if (rc) {
+                return rc;
+            } else {
+                ls.list = w.list;
+                ls.list_n = w.list_n;
+                ls.sel = w.list_n + w.list_n_cap;
+                ls.list_cap = w.list_cap;
+            }
         }
     }
     // team shape per family: given by the caller (host pipeline), else forced, else tuned, else
@@ -751,10 +760,16 @@ extern "C" pmh_status pmh_sketch_batch_host(pmh_handle h, const uint64_t *ids, c
     if ((rc = get_tables(h, m, &tab))) return rc;
     int64_t lmin = 0, lmax = 0, nmax = 0;
     for (int c = 0; c < k; c++) nmax = std::max<int64_t>(nmax, offsets[b[c + 1]] - offsets[b[c]]);
-    const bool lists = list_bounds(h->th, m, (float)(std::log((double)m) + h->th.t_c), &lmin, &lmax) && nmax > 0;
+    bool lists = list_bounds(h->th, m, (float)(std::log((double)m) + h->th.t_c), &lmin, &lmax) && nmax > 0;
     for (Workspace &w : h->ws) {
         if ((rc = ensure_workspace(h, w, smax, smax * V, m))) return rc;
-        if (lists && (rc = ensure_list(h, w, nmax, smax))) return rc;
+        if (lists && (rc = ensure_list(h, w, nmax, smax))) {
+            if (rc != PMH_ERR_NO_MEMORY) return rc;
+            (void)cudaGetLastError();   // no room for the lists: the ranges filter every element in full
+            h->err.clear();
+            rc = PMH_OK;
+            lists = false;
+        }
     }
     HostPipe &hp = h->hp;
     if ((rc = ensure_dev(h, &hp.ids, &hp.ids_cap, (size_t)N * 8, "device ids"))) return rc;
@@ -819,7 +834,7 @@ extern "C" pmh_status pmh_sketch_batch_host(pmh_handle h, const uint64_t *ids, c
         rc = sketch_device(h, r, (const uint64_t *)dids, (const double *)dw, doff + s0, sc, m, variants, num_variants,
                            precision, seed, (uint64_t *)hp.z[r], out_q ? (double *)hp.q[r] : nullptr,
                            set_status ? (int32_t *)hp.st[r] : nullptr, nullptr, s_run, false, ev_fam(c), kinds,
-                           offsets[b[c + 1]] - offsets[b[c]]);
+                           lists ? offsets[b[c + 1]] - offsets[b[c]] : 0);
         if (rc) {
             for (int i = 0; i < 4; i++) cudaStreamSynchronize(hp.s[i]);
             return rc;
