@@ -846,3 +846,26 @@ def test_pminhash_invariants():
         qb, zb = oracle.pminhash(ids[cut:], w[cut:], 64, seed=trial)
         take_b = (qb < qa) | ((qb == qa) & (zb < za))
         assert np.array_equal(np.where(take_b, zb, za), z) and np.array_equal(np.where(take_b, qb, qa), q)
+
+
+def test_sketch_batch_is_the_per_set_sketch():
+    """The oracle's CSR batch loop: each row is that set's own signature (offsets, empty sets),
+    and a set with a bad weight reports its status with zero ids and +inf q."""
+    rng = np.random.default_rng(99)
+    sizes = [5, 0, 40, 3, 17]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    ids = rng.permutation(10_000)[: off[-1]].astype(np.uint64) * np.uint64(2654435761) + np.uint64(12345)
+    w = rng.uniform(0.1, 2.0, off[-1])
+    w[off[3] + 1] = -1.0                       # set 3: a negative weight
+    for v in ("1", "2", "3a", "4"):
+        q, z, st = oracle.sketch_batch(v, ids, w, off, 16, seed=4)
+        for s in range(len(sizes)):
+            sid, sw = ids[off[s]:off[s + 1]], w[off[s]:off[s + 1]]
+            code = oracle.sketch_status(v, sid, sw, 16, seed=4)
+            assert st[s] == code
+            if code == 0:
+                qs, zs, _ = oracle.sketch(v, sid, sw, 16, seed=4)
+                assert np.array_equal(z[s], zs) and np.array_equal(q[s], qs)
+            else:
+                assert (z[s] == 0).all() and np.isinf(q[s]).all()
+        assert st[3] != 0 and st[1] == 0 and np.isinf(q[1]).all()   # bad weight; empty set
