@@ -143,11 +143,11 @@ inline uint64_t host_mix64(uint64_t z) {
 // [516] counts the sets whose statistics are split over all blocks, [518, 520)
 // is the statistics kernel's set counter (u64), [520, 524) the per-family
 // lengths of the FP64 redo lists, [524, 528) the head counters of the redo
-// kernels, [528, 530) the prefilter kernel's counter (u64) and [530] the
-// number of sets it lists; [532, ...) lists the split sets (u64 set indices,
-// kBigCap of them).
+// kernels, [528, 530) the prefilter kernel's counter (u64), [530] the number
+// of sets it lists and [531] a flag set when the offsets decrease somewhere;
+// [532, ...) lists the split sets (u64 set indices, kBigCap of them).
 constexpr int kQHist = 0, kQStart = 256, kQHead = 512, kQBigCount = 516, kQStatNext = 518, kQRedoCount = 520,
-              kQRedoHead = 524, kQListNext = 528, kQListCount = 530, kQBigList = 532;
+              kQRedoHead = 524, kQListNext = 528, kQListCount = 530, kQListBad = 531, kQBigList = 532;
 constexpr int kBigCap = 1024;
 constexpr int kQMetaWords = kQBigList + 2 * kBigCap;
 constexpr int kQMetaClearWords = kQBigList;     // words cleared per call
@@ -411,7 +411,9 @@ static __global__ void __launch_bounds__(256) set_stats_big_kernel(const int64_t
 // list_cap entries in all; a set whose survivors exceed n/2, or that does not
 // fit, stays unlisted (list_n = kUnlisted) and is filtered in full.
 // The sets of list_min..list_max elements are gathered first (list_select:
-// one thread per set; every other set is marked unlisted), then list_kernel
+// one thread per set; every other set is marked unlisted; offsets that
+// decrease anywhere, whose sets' ranges may overlap, turn the lists off for the
+// call), then list_kernel
 // gives one block to each gathered set, the blocks taking them from a shared
 // counter; each thread keeps kListUnroll elements' loads in flight (1,024
 // threads per SM at <= 64 registers).
@@ -421,6 +423,7 @@ static __global__ void __launch_bounds__(256) list_select(const int64_t *off, in
                                                           unsigned int *meta) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < num_sets; s += (int64_t)gridDim.x * blockDim.x) {
         const int64_t n = off[s + 1] - off[s];
+        if (n < 0) atomicOr(&meta[kQListBad], 1u);
         if (n >= list_min && n <= list_max) sel[atomicAdd(&meta[kQListCount], 1u)] = (uint32_t)s;
         else list_n[s] = kUnlisted;
     }
@@ -435,6 +438,7 @@ static __global__ void __launch_bounds__(kListBlock, 1024 / kListBlock) list_ker
     const int64_t off0 = p.offsets[0];
     const float te_lo = p.tab.te_lo;
     const int64_t nsel = (int64_t)ld_volatile((const int *)&meta[kQListCount]);
+    const bool disjoint = ld_volatile((const int *)&meta[kQListBad]) == 0;   // the sets' ranges do not overlap
     for (;;) {
         if (threadIdx.x == 0) {
             s_next = (long long)atomicAdd((unsigned long long *)(meta + kQListNext), 1ull);
@@ -450,7 +454,7 @@ static __global__ void __launch_bounds__(kListBlock, 1024 / kListBlock) list_ker
         float t_s;
         int sigma;
         first_threshold(p.m, p.t_factor, st.wsum, st.npos, &t_s, &sigma);
-        const bool ok = b >= off0 && !st.bad && st.npos > 0 && lb + cap <= list_cap && !isinf(t_s);
+        const bool ok = disjoint && b >= off0 && !st.bad && st.npos > 0 && lb + cap <= list_cap && !isinf(t_s);
         if (ok) {
             // 32-bit offsets within the set (n <= list_max < 2^32)
             const unsigned long long *wset = wb + b, *iset = (const unsigned long long *)p.ids + b;

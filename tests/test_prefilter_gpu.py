@@ -137,6 +137,26 @@ def test_arrays_rewritten_in_place(handles):
     assert torch.equal(q1, q0)
 
 
+def test_decreasing_offsets_turn_lists_off(handles):
+    """Offsets that decrease make sets' element ranges overlap, and with them their share of the
+    lists: no set is listed then, and every valid set gets its own signature."""
+    from paper_1911_00675_gb300 import pmh
+    on, off = handles
+    b = W.random_batch(61, [100_000], 256, "uniform")
+    ids, w, _ = to_dev(b)
+    offs = torch.tensor([0, 60_000, 20_000, 30_000, 100_000], dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(len(pmh.COUNTERS), dtype=torch.int64, device="cuda")
+    z1, q1, s1 = on.sketch_batch(ids, w, offs, 256, VARS, 1, 3, with_q=True, counters=cnt)
+    z0, q0, s0 = off.sketch_batch(ids, w, offs, 256, VARS, 1, 3, with_q=True)
+    torch.cuda.synchronize()
+    s1 = s1.cpu().numpy()
+    assert (s1[:, 1] == 1).all() and (s1[:, [0, 2, 3]] == 0).all()   # set 1: PMH_ERR_INVALID_ARG
+    assert np.array_equal(s1, s0.cpu().numpy())
+    assert int(cnt[pmh.COUNTERS.index("listed")]) == 0
+    assert np.array_equal(pmh.to_u64(z1), pmh.to_u64(z0))
+    assert torch.equal(q1, q0)
+
+
 def test_host_pipeline_with_lists(handles):
     from paper_1911_00675_gb300 import pmh
     on, off = handles
