@@ -347,7 +347,8 @@ pmh_status pmh_set_thresholds(pmh_handle h, double t_c, double t_c_grid, int32_t
  * own log-free test, with the smallest lower bound of any family); the first
  * round of each weighted variant of such a set then visits only these
  * elements.  A later round (rare) visits all elements again.  Binary-weight
- * variants and the rejection sampler do not use the lists.
+ * variants and the rejection sampler do not use the lists (a call with no
+ * other variant skips the pass).
  *
  *   list_factor  default 2.0; <= 0 turns the prefilter off.
  *

@@ -229,9 +229,16 @@ static pmh_status ensure_list(pmh_handle h, Workspace &w, int64_t elements, int6
     return PMH_OK;
 }
 
-// Sets of list_min..list_max elements get prefilter lists (list_min from the first round's threshold).
-static bool list_bounds(const Thresholds &th, uint32_t m, float t_factor, int64_t *lo, int64_t *hi) {
+// Sets of list_min..list_max elements get prefilter lists (list_min from the first round's threshold),
+// when some variant of the call reads them: a weighted one whose first point the filter bounds
+// without the rejection sampler.
+static bool list_bounds(const Thresholds &th, uint32_t m, float t_factor, const int32_t *variants, int32_t nv,
+                        int64_t *lo, int64_t *hi) {
     if (!kListing || !(th.list_factor > 0.0) || th.rounds <= 0) return false;
+    bool used = false;
+    for (int v = 0; v < nv; v++)
+        used |= !variant_unweighted(variants[v]) && !(th.te_rej && family_of(variants[v]) >= 3);
+    if (!used) return false;
     const double lmin = std::ceil(th.list_factor * (double)m * (double)t_factor);
     *lo = lmin < 2.0 ? 2 : (lmin > 9e18 ? INT64_MAX : (int64_t)lmin);
     *hi = th.list_max;
@@ -577,7 +584,7 @@ static pmh_status sketch_device(pmh_handle h, int wsi, const uint64_t *ids, cons
     if (st) CUDA_TRY(h, cudaStreamIsCapturing(st, &cs));
     // prefilter lists, sized by the call's element count
     ListSpec ls;
-    if (list_bounds(h->th, m, p.t_factor, &ls.list_min, &ls.list_max)) {
+    if (list_bounds(h->th, m, p.t_factor, variants, num_variants, &ls.list_min, &ls.list_max)) {
         int64_t n_el = n_hint;
         if (n_el < 0 && (rc = element_count(h, ids, weights, offsets, num_sets, st, cs, &n_el))) return rc;
         if (n_el > 0) {
@@ -760,7 +767,8 @@ extern "C" pmh_status pmh_sketch_batch_host(pmh_handle h, const uint64_t *ids, c
     if ((rc = get_tables(h, m, &tab))) return rc;
     int64_t lmin = 0, lmax = 0, nmax = 0;
     for (int c = 0; c < k; c++) nmax = std::max<int64_t>(nmax, offsets[b[c + 1]] - offsets[b[c]]);
-    bool lists = list_bounds(h->th, m, (float)(std::log((double)m) + h->th.t_c), &lmin, &lmax) && nmax > 0;
+    bool lists = list_bounds(h->th, m, (float)(std::log((double)m) + h->th.t_c), variants, num_variants, &lmin, &lmax) &&
+                 nmax > 0;
     for (Workspace &w : h->ws) {
         if ((rc = ensure_workspace(h, w, smax, smax * V, m))) return rc;
         if (lists && (rc = ensure_list(h, w, nmax, smax))) {
